@@ -1,0 +1,169 @@
+"""Seeded synthetic inputs shared by the tests, the oracle timing leg and the benchmark.
+
+This module draws random initial conditions and lays them out in the patch storage
+format; it holds none of the PPM method's arithmetic.  The one formula here is the
+definition of total energy density used to build an initial state from primitives,
+E = p/(gamma-1) + rho |v|^2 / 2 (Section 2.1, total energy and ideal-gas equation of
+state), applied once to the generated input, never inside a step.
+
+Storage of one patch: five float64 arrays (rho, m_x, m_y, m_z, E), each of shape
+(n_z + 2 ng, n_y + 2 ng, n_x + 2 ng) in C order, so x is the fastest index.  Ghost
+cells are left at zero; the ghost-fill step fills them.
+
+Recipes (all seeds derive from SEED_BASE + 100 * config + patch index):
+  * single grid, white noise: rho lognormal exp(sigma g - sigma^2/2) with iid unit
+    normal g, p uniform, velocity components iid N(0, (mach c0)^2 / 3) so the rms
+    Mach number is `mach` with c0 = sqrt(gamma p / 1).
+  * single grid, turbulent: each velocity component a Gaussian random field with
+    P(k) ~ k^-4 (FFT filtered white noise), scaled to rms Mach `mach`; rho lognormal
+    on an independent k^-4 field with sigma = 1.
+  * batched level: per-axis active sizes uniform in {8..64}; each patch its own
+    white-noise realisation as above.
+  * strong-shock grid: lognormal background clipped to [1e-2, 1e2], p = 1e-3,
+    seeded spheres of radius 4..24 cells with p up to 1e3, v = 0.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 1307_2265
+NG = 3
+FIELDS = ("rho", "mx", "my", "mz", "E")
+
+
+def rng_for(config: int, index: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED_BASE + 100 * config + index))
+
+
+def lognormal(g: np.ndarray, sigma: float) -> np.ndarray:
+    """Mean-one lognormal field from a unit-variance Gaussian field g."""
+    return np.exp(sigma * g - 0.5 * sigma * sigma)
+
+
+def grf_kpow(rng: np.random.Generator, shape, power: float = -4.0) -> np.ndarray:
+    """Zero-mean, unit-variance periodic Gaussian random field with P(k) ~ k^power."""
+    white = rng.standard_normal(shape)
+    fk = np.fft.rfftn(white)
+    ks = [np.fft.fftfreq(s) * s for s in shape[:-1]] + [np.fft.rfftfreq(shape[-1]) * shape[-1]]
+    grids = np.meshgrid(*ks, indexing="ij")
+    k2 = sum(g * g for g in grids)
+    k2[(0,) * len(shape)] = 1.0
+    amp = k2 ** (power / 4.0)          # sqrt(P(k)) = k^(power/2)
+    amp[(0,) * len(shape)] = 0.0
+    f = np.fft.irfftn(fk * amp, s=shape)
+    f -= f.mean()
+    return f / f.std()
+
+
+def white_noise_prims(rng, shape, sigma=0.5, mach=1.0, gamma=5.0 / 3.0, p0=1.0):
+    """(rho, vx, vy, vz, p) arrays of `shape` (z, y, x) for the white-noise recipe."""
+    rho = lognormal(rng.standard_normal(shape), sigma)
+    c0 = np.sqrt(gamma * p0 / 1.0)
+    sd = mach * c0 / np.sqrt(3.0)
+    v = [rng.standard_normal(shape) * sd for _ in range(3)]
+    p = np.full(shape, p0)
+    return rho, v[0], v[1], v[2], p
+
+
+def turbulent_prims(rng, shape, mach=3.0, sigma=1.0, gamma=5.0 / 3.0, p0=1.0):
+    rho = lognormal(grf_kpow(rng, shape), sigma)
+    c0 = np.sqrt(gamma * p0)
+    v = [grf_kpow(rng, shape) for _ in range(3)]
+    rms = np.sqrt(np.mean(v[0] ** 2 + v[1] ** 2 + v[2] ** 2))
+    v = [vi * (mach * c0 / rms) for vi in v]
+    p = np.full(shape, p0)
+    return rho, v[0], v[1], v[2], p
+
+
+def blast_prims(rng, shape, nblast=16, p_bg=1e-3, p_max=1e3, r_min=4, r_max=24):
+    rho = np.clip(lognormal(grf_kpow(rng, shape), 1.0), 1e-2, 1e2)
+    p = np.full(shape, p_bg)
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for _ in range(nblast):
+        c = rng.uniform(0, 1, 3) * np.array([nz, ny, nx])
+        r = rng.uniform(r_min, r_max)
+        pb = p_max * 10.0 ** rng.uniform(-2.0, 0.0)
+        d = [np.minimum(np.abs(a - ci), s - np.abs(a - ci)) for a, ci, s in ((z, c[0], nz), (y, c[1], ny), (x, c[2], nx))]
+        inside = d[0] ** 2 + d[1] ** 2 + d[2] ** 2 <= r * r
+        p[inside] = np.maximum(p[inside], pb)
+    zero = np.zeros(shape)
+    return rho, zero, zero.copy(), zero.copy(), p
+
+
+def prims_to_conserved(rho, vx, vy, vz, p, gamma):
+    """Initial-state construction: conserved (rho, m, E) from primitives."""
+    E = p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz)
+    return rho.copy(), rho * vx, rho * vy, rho * vz, E
+
+
+def embed(active: np.ndarray, ng: int = NG) -> np.ndarray:
+    """Place an active (z, y, x) block inside zeroed ghost storage."""
+    nz, ny, nx = active.shape
+    out = np.zeros((nz + 2 * ng, ny + 2 * ng, nx + 2 * ng))
+    out[ng:ng + nz, ng:ng + ny, ng:ng + nx] = active
+    return out
+
+
+def single_grid(n, recipe="white", config=1, gamma=5.0 / 3.0, ng=NG, **kw):
+    """Five ghost-zoned float64 fields for one periodic grid of n = (nx, ny, nz) cells."""
+    nx, ny, nz = n
+    rng = rng_for(config)
+    shape = (nz, ny, nx)
+    if recipe == "white":
+        prims = white_noise_prims(rng, shape, gamma=gamma, **kw)
+    elif recipe == "turbulent":
+        prims = turbulent_prims(rng, shape, gamma=gamma, **kw)
+    elif recipe == "blast":
+        prims = blast_prims(rng, shape, **kw)
+    else:
+        raise ValueError(recipe)
+    return [embed(f, ng) for f in prims_to_conserved(*prims, gamma)]
+
+
+def patch_sizes(npatch, config=3, lo=8, hi=64):
+    """Per-axis active sizes (nx, ny, nz), uniform integers in [lo, hi]."""
+    rng = rng_for(config, 10 ** 6)
+    return rng.integers(lo, hi + 1, size=(npatch, 3))
+
+
+def batched_level(npatch, config=3, gamma=5.0 / 3.0, lo=8, hi=64, ng=NG, sizes=None):
+    """A batch of independent white-noise patches.
+
+    Returns (sizes[npatch,3] as (nx,ny,nz), offsets[npatch], five flat float64 arrays)
+    with each patch stored contiguously per field at its offset.
+    """
+    if sizes is None:
+        sizes = patch_sizes(npatch, config, lo, hi)
+    sizes = np.asarray(sizes, dtype=np.int64)
+    vols = np.prod(sizes + 2 * ng, axis=1)
+    offsets = np.concatenate([[0], np.cumsum(vols)[:-1]]).astype(np.int64)
+    total = int(vols.sum())
+    flat = [np.zeros(total) for _ in range(5)]
+    for i, (nx, ny, nz) in enumerate(sizes):
+        rng = rng_for(config, i)
+        prims = white_noise_prims(rng, (int(nz), int(ny), int(nx)), gamma=gamma)
+        cons = prims_to_conserved(*prims, gamma)
+        for f in range(5):
+            blk = embed(cons[f], ng)
+            flat[f][offsets[i]:offsets[i] + blk.size] = blk.ravel()
+    return sizes, offsets, flat
+
+
+def patch_view(flat, off, size, ng=NG):
+    nx, ny, nz = (int(s) for s in size)
+    cnt = (nx + 2 * ng) * (ny + 2 * ng) * (nz + 2 * ng)
+    return flat[off:off + cnt].reshape(nz + 2 * ng, ny + 2 * ng, nx + 2 * ng)
+
+
+def riemann_states(rng, n, log_rho_sd=1.0, mach=1.0, log_p_sd=1.0, gamma=5.0 / 3.0):
+    """Random left/right Riemann states (rhoL, uL, pL, rhoR, uR, pR) for solver tests."""
+    rl = np.exp(rng.normal(0, log_rho_sd, n))
+    rr = np.exp(rng.normal(0, log_rho_sd, n))
+    pl = np.exp(rng.normal(0, log_p_sd, n))
+    pr = np.exp(rng.normal(0, log_p_sd, n))
+    cl = np.sqrt(gamma * pl / rl)
+    cr = np.sqrt(gamma * pr / rr)
+    ul = rng.normal(0, mach, n) * cl
+    ur = rng.normal(0, mach, n) * cr
+    return rl, ul, pl, rr, ur, pr
