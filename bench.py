@@ -1,0 +1,378 @@
+"""Benchmark of the split PPM hydro step on GB300.
+
+Workload (default): a batched AMR level of 4000 self-periodic patches with
+per-axis active sizes uniform in 8..64 (about 1.9e8 cells), 3 ghost layers,
+white-noise lognormal density (sigma 0.5), rms Mach 1, gamma 5/3, CFL 0.4.
+One step = device CFL timestep + three split PPM sweeps over every patch in
+one persistent launch per sweep (the whole hot path), FP32 arithmetic with
+FP64 conserved accumulation.  The plain FP64 batched sweep is timed on the
+same batch for comparison.  Inputs (about 13 GB) exceed L2 (129 MB).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NPATCH = 4000
+GAMMA = 5.0 / 3.0
+CFL = 0.4
+METRIC = "Mcell-updates/s on GB300: batched FP32+learned vs plain FP64, at stated L1 err"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def dist_init():
+    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def build_level(rank, npatch=NPATCH):
+    from paper_1307_2265_gb300 import synth
+    sizes = synth.patch_sizes(npatch, config=3)
+    # each rank advances its own level (weak scaling): seeds offset by rank
+    sizes, offsets, flat = synth.batched_level(npatch, config=3 + 1000 * rank, sizes=sizes)
+    return sizes, offsets, flat
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, path):
+        self.path, self.proc = path, None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, gpu_index):
+        if not self.proc:
+            return None
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        if vis.strip().isdigit():
+            gpu_index = int(vis.strip())
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9 or parts[0] != str(gpu_index):
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except OSError:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def sweep_bytes(table, flags):
+    """Algorithmic HBM bytes of one sweep per direction: each pencil reads its
+    cells once and writes its active cells once (5 float64 fields).  Periodic
+    patches read only active cells (ghost positions are wrapped images)."""
+    n = table["n"].astype(np.int64)
+    out = []
+    for d in range(3):
+        if flags:
+            cells = np.prod(n, axis=1)
+            out.append(int(np.sum(cells * 80)))
+        else:
+            raise NotImplementedError
+    return out
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import paper_1307_2265_gb300 as ez
+    dev = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(dev)
+    sizes, offsets, flat = build_level(rank, args.npatch)
+    table = ez.patch_table(sizes, offsets, [1.0 / 64] * 3, flags=ez.PATCH_PERIODIC)
+    cells = int(np.prod(sizes, axis=1).sum())
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch = ez.PatchBatch(table, flat, stream=stream)
+    host0 = [torch.from_numpy(f).pin_memory() for f in flat]
+    p32 = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32)
+    p64 = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP64)
+    bytes_per_sweep = sweep_bytes(table, True)
+
+    def one_step(params, step_idx, ev=None):
+        """CFL timestep on the device, then the three split sweeps (dt read on the
+        device).  Periodic patches need no ghost fill: the sweeps wrap."""
+        ez.timestep_cfl(batch, params, out=batch.dt_dev)
+        order = (0, 1, 2) if step_idx % 2 == 0 else (2, 1, 0)
+        for q, d in enumerate(order):
+            if ev is not None:
+                ev[q][0].record(stream)
+            ez.ppm_sweep_dev(batch, d, batch.dt_dev, 0, params)
+            if ev is not None:
+                ev[q][1].record(stream)
+
+    # warm-up
+    with torch.cuda.stream(stream):
+        for w in range(args.warmup):
+            one_step(p32, w)
+    stream.synchronize()
+    for u, h in zip(batch.U, host0):
+        u.copy_(h)
+    torch.cuda.synchronize()
+    barrier(world)
+
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ez.launch_count()
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
+    with clk:
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            t0.record(stream)
+            for s in range(args.steps):
+                one_step(p32, s, evs[s])
+            t1.record(stream)
+        t1.synchronize()
+    launches = ez.launch_count() - launches0
+    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(ms, world)
+    sweep_ms = [[e[q][0].elapsed_time(e[q][1]) for q in range(3)] for e in evs]
+    sweep_avg = float(np.mean(sweep_ms))
+    status32 = batch.read_status()
+
+    # plain FP64 batched sweep on the same level (fewer steps: ALU bound)
+    for u, h in zip(batch.U, host0):
+        u.copy_(h)
+    torch.cuda.synchronize()
+    k64 = 1
+    with torch.cuda.stream(stream):
+        one_step(p64, 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(k64):
+            one_step(p64, s + 1)
+        e1.record(stream)
+    e1.synchronize()
+    ms64 = e0.elapsed_time(e1) / k64
+
+    # end to end through the public API with host buffers: H2D of U, step, D2H of U
+    host_out = [torch.empty_like(h).pin_memory() for h in host0]
+    h2d = sum(h.numel() * 8 for h in host0)
+    torch.cuda.synchronize()
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ke = max(1, min(args.steps, 3))
+    with torch.cuda.stream(stream):
+        ee0.record(stream)
+        for s in range(ke):
+            for u, h in zip(batch.U, host0):
+                u.copy_(h, non_blocking=True)
+            one_step(p32, s)
+            for u, h in zip(batch.U, host_out):
+                h.copy_(u, non_blocking=True)
+        ee1.record(stream)
+    ee1.synchronize()
+    ms_e2e = max_over_ranks(ee0.elapsed_time(ee1) / ke, world)
+
+    # sampled parity + CPU baseline (rank 0, N=1 only): one FP32 step of the full
+    # batch from the initial state; the oracle redoes the first patches with the
+    # same dt and is timed on the host cores
+    cpu = None
+    l1 = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        for u, h in zip(batch.U, host0):
+            u.copy_(h)
+        with torch.cuda.stream(stream):
+            one_step(p32, 0)
+        stream.synchronize()
+        sample = {"dt": float(batch.dt_dev.item()), "patches": [], "l1_num": [0.0] * 5, "l1_den": [0.0] * 5}
+        for i in range(args.sample_patches):
+            sample["patches"].append([f.cpu().numpy() for f in batch.patch_fields(i)])
+        cpu = cpu_baseline_leg(flat, sizes, offsets, sample, budget_s=args.cpu_budget)
+        l1 = [n / d for n, d in zip(sample["l1_num"], sample["l1_den"])]
+
+    peak, peak_kind = measured_peak()
+    achieved = float(np.mean(bytes_per_sweep)) / (sweep_avg * 1e-3) / 1e9
+    value = cells * world * args.steps / (ms * 1e-3) / 1e6
+    res = {
+        "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc",
+        "data": "synthetic",
+        "config": {"workload": f"batched AMR level: {args.npatch} self-periodic patches, per-axis 8..64 cells, "
+                               f"3 ghost layers, white-noise lognormal rho sigma 0.5, rms Mach 1, gamma 5/3, CFL 0.4",
+                   "cells_per_step": cells, "precision": "FP32 arithmetic, FP64 accumulation", "guess": "plain",
+                   "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+        "fp64_plain": {"value": cells / (ms64 * 1e-3) / 1e6, "unit": "Mcell-updates/s", "ms_per_step": ms64},
+        "e2e": {"value": cells * world / (ms_e2e * 1e-3) / 1e6, "unit": "Mcell-updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "ppm_sweep_kernel<float>",
+                     "peak_source": peak_kind, "sweep_ms_avg": sweep_avg},
+        "gpu_launches": int(launches),
+        "status": status32,
+        "cpu_baseline": cpu,
+        "fp32_l1_rel_err_vs_oracle_one_step": l1,
+        "clocks": clk.summary(dev),
+    }
+    return res
+
+
+def run_reference(args):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same level:
+    each step advances the first patches of the batch (by index) until about
+    `budget` seconds of CPU work, one step each with the level's CFL dt."""
+    import oracle
+    from paper_1307_2265_gb300 import synth
+    sizes, offsets, flat = build_level(0, args.npatch)
+    P = oracle.Params(gamma=GAMMA)
+    dx = [1.0 / 64] * 3
+    npick = 24
+    pats = []
+    for i in range(npick):
+        v = [synth.patch_view(f, offsets[i], sizes[i]).copy() for f in flat]
+        pats.append(v)
+    cells_each = [int(np.prod(sizes[i])) for i in range(npick)]
+    rate = max(oracle.cfl_rate(U, dx, P) for U in pats)
+    dt = CFL / rate
+    t_all, cells_all = 0.0, 0
+    for w in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        done = 0
+        for U, c in zip(pats, cells_each):
+            oracle.step_periodic(U, dx, dt, w, P)
+            done += c
+        el = time.perf_counter() - t0
+        if w >= args.warmup:
+            t_all += el
+            cells_all += done
+    v = cells_all / t_all / 1e6
+    return {"metric": METRIC, "value": v, "unit": "Mcell-updates/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"sample of the batched AMR level: first {npick} of {args.npatch} patches, "
+                                   "one oracle step each per timed step"},
+            "cpu_baseline": {"value": v, "unit": "Mcell-updates/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": f"{npick} patches, {sum(cells_each)} cells per step"},
+            "e2e": {"value": v, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline_leg(flat, sizes, offsets, gpu_fields_after_one_step=None, budget_s=12.0):
+    """Oracle timed on the host cores on a bounded sample (first patches of the
+    level, one step each), plus the FP32 path's error on that sample when the
+    GPU result of the same step is given."""
+    import oracle
+    from paper_1307_2265_gb300 import synth
+    P = oracle.Params(gamma=GAMMA)
+    dx = [1.0 / 64] * 3
+    t0 = time.perf_counter()
+    cells = 0
+    i = 0
+    while time.perf_counter() - t0 < budget_s and i < len(sizes):
+        U = [synth.patch_view(f, offsets[i], sizes[i]).copy() for f in flat]
+        oracle.step_periodic(U, dx, gpu_fields_after_one_step["dt"], 0, P)
+        cells += int(np.prod(sizes[i]))
+        if gpu_fields_after_one_step is not None and i < len(gpu_fields_after_one_step["patches"]):
+            g = gpu_fields_after_one_step["patches"][i]
+            for f in range(5):
+                a = U[f][3:-3, 3:-3, 3:-3]
+                b = g[f][3:-3, 3:-3, 3:-3]
+                gpu_fields_after_one_step["l1_num"][f] += float(np.sum(np.abs(a - b)))
+                gpu_fields_after_one_step["l1_den"][f] += float(np.sum(np.abs(a)))
+        i += 1
+    el = time.perf_counter() - t0
+    return {"value": cells / el / 1e6, "unit": "Mcell-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"first {i} patches of the level, one step each ({cells} cells, {el:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--npatch", type=int, default=NPATCH)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work in the CPU leg")
+    ap.add_argument("--sample-patches", type=int, default=6)
+    args = ap.parse_args()
+    rank, world = dist_init()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    res = run_gpu(args, rank, world)
+    if rank == 0:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * enzo_ppm.h -- C ABI of the GB300 (sm_103a) directionally split PPM hydro sweep.
+ *
+ * The library advances the Euler equations of an ideal gas (paper Sec. 2.1:
+ * conserved density, momentum and total energy density; EOS e = p/(gamma-1))
+ * on a batch of ghost-zoned grid patches (Sec. 3: rectilinear patches with 3
+ * ghost layers each, solved as independent problems with Dirichlet ghost
+ * zones) by the direct-Eulerian PPM method of Sec. 4.1 (parabolic
+ * reconstruction, monotone limiter, characteristic tracing, two-shock Riemann
+ * solver with Newton iteration on p*, Sec. 4.1.2, and the conservative
+ * update), one split direction per call, with the hydro CFL rule of Sec. 9.
+ *
+ * Conventions shared by every entry point:
+ *   - All array pointers are DEVICE pointers owned by the caller.  The library
+ *     allocates nothing and frees nothing; it keeps no state between calls
+ *     except a per-device cache of launch sizes.
+ *   - Every call is asynchronous on the given stream (NULL = legacy default
+ *     stream) unless stated otherwise, and returns ENZO_OK or a negative
+ *     ENZO_ERR_* code.  No C++ exception crosses the ABI.
+ *   - Numerical events (Newton cap hits, HLL fallbacks, floors, NaN) are not
+ *     errors: kernels add them to the caller's device counters `status`
+ *     (ENZO_STATUS_WORDS unsigned 64-bit words, indexed by ENZO_ST_*).
+ *   - Field storage: five float64 arrays U[0..4] = rho, m_x, m_y, m_z, E (E is
+ *     the total energy DENSITY).  Patch p occupies, in every array, the
+ *     elements [off, off + (nx+2ng)(ny+2ng)(nz+2ng)), x fastest, then y, z.
+ */
+#ifndef ENZO_PPM_H
+#define ENZO_PPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ENZO_ABI_VERSION 1
+
+/* ---- error codes ---- */
+#define ENZO_OK 0
+#define ENZO_ERR_ARG (-1)        /* NULL pointer, bad enum, bad size, non-finite dt */
+#define ENZO_ERR_CUDA (-2)       /* a CUDA runtime call or launch failed */
+#define ENZO_ERR_RANGE (-3)      /* a patch descriptor is out of range */
+#define ENZO_ERR_WORKSPACE (-4)  /* workspace missing or smaller than required */
+#define ENZO_ERR_UNSUPPORTED (-5)/* option not available in this build */
+
+/* ---- precision modes ---- */
+#define ENZO_FP64 0  /* every step in FP64, no FMA contraction (parity path) */
+#define ENZO_FP32 1  /* FP32 reconstruction, tracing and Riemann; FP64 conserved
+                        accumulation, and FP64 E - KE in high-Mach cells */
+
+/* ---- Newton starting guess for p* ---- */
+#define ENZO_GUESS_PLAIN 0  /* acoustic two-shock guess */
+#define ENZO_GUESS_MLP 1    /* learned guess (enzo_mlp_*), plain guess as fallback */
+
+/* ---- patch flags ---- */
+#define ENZO_PATCH_PERIODIC 1 /* the patch is its own periodic neighbour: sweeps read
+                                 ghost positions from the wrapped active cells and
+                                 leave stored ghost cells untouched */
+
+/* ---- status counters (indices into the caller's uint64 status array) ---- */
+enum {
+    ENZO_ST_INTERFACES = 0,   /* Riemann problems solved */
+    ENZO_ST_NEWTON_ITERS = 1, /* Newton updates, summed */
+    ENZO_ST_NEWTON_NONCONV = 2,/* interfaces whose Newton hit the cap */
+    ENZO_ST_HLL_CELLS = 3,    /* cells that went to rho <= 0 and were re-fluxed with HLL */
+    ENZO_ST_NEG_AFTER = 4,    /* cells still at rho <= 0 after the fallback */
+    ENZO_ST_RHO_FLOOR = 5,    /* cell densities raised to rho_floor */
+    ENZO_ST_P_FLOOR = 6,      /* cell pressures raised to p_floor */
+    ENZO_ST_NAN = 7,          /* updated cells holding NaN */
+    ENZO_ST_BAD_PATCH = 8,    /* descriptors rejected on the device (skipped) */
+    ENZO_ST_FP64_EKE = 9,     /* FP32 mode: cells whose E - KE was redone in FP64 */
+    ENZO_ST_GUESS_RESTARTS = 10, /* learned guess abandoned for the plain guess */
+    ENZO_ST_GUESS_CALLS = 11, /* interfaces given a learned guess */
+    ENZO_STATUS_WORDS = 16
+};
+
+/* One grid patch (Sec. 3).  n: active cells per axis (>= 1); ng: ghost layers
+ * stored on each side (must be 3, the PPM stencil's need, Sec. 3); off: element
+ * offset of the patch's first stored cell in every field array; dx: cell widths;
+ * level: refinement level (informational); flags: ENZO_PATCH_*. */
+typedef struct {
+    int32_t n[3];
+    int32_t ng;
+    int64_t off;
+    double dx[3];
+    int32_t level;
+    int32_t flags;
+} enzo_patch;
+
+/* A batch of patches that share one timestep (a level, Sec. 3 and Sec. 9). */
+typedef struct {
+    int32_t npatch;               /* number of descriptors (>= 0) */
+    int32_t reserved;
+    const enzo_patch *patches;    /* DEVICE array [npatch] */
+    int64_t field_len;            /* elements in each U[f]; descriptors reaching
+                                     past it are rejected (ENZO_ST_BAD_PATCH) */
+    double *U[5];                 /* DEVICE fields rho, m_x, m_y, m_z, E */
+    void *workspace;              /* DEVICE scratch, >= enzo_workspace_size(npatch) bytes,
+                                     16-byte aligned; contents need no initialisation */
+    size_t ws_bytes;
+    unsigned long long *status;   /* DEVICE counters [ENZO_STATUS_WORDS]; added to */
+    void *stream;                 /* cudaStream_t */
+} enzo_patch_batch;
+
+/* Method parameters (Sec. 4.1, 4.1.2, 9). */
+typedef struct {
+    double gamma;       /* ratio of specific heats, > 1 */
+    double cfl;         /* kappa_hydro of Sec. 9, in (0, 1] */
+    int32_t precision;  /* ENZO_FP64 | ENZO_FP32 */
+    int32_t guess;      /* ENZO_GUESS_PLAIN | ENZO_GUESS_MLP */
+    double newton_tol;  /* residual tolerance; <= 0 selects 1e-14 (FP64) / 1e-6 (FP32) */
+    int32_t newton_max; /* Newton update cap; <= 0 selects 20 (FP64) / 12 (FP32) */
+    int32_t fallback;   /* nonzero: HLL re-flux of cells that reach rho <= 0 (Sec. 4.1.2) */
+    double rho_floor;   /* density floor, > 0 */
+    double p_floor;     /* pressure floor, > 0 */
+    const void *mlp;    /* DEVICE weight blob from enzo_mlp_pack (ENZO_GUESS_MLP only) */
+} enzo_params;
+
+/* Bytes of device workspace a batch of npatch patches needs. */
+size_t enzo_workspace_size(int32_t npatch);
+
+/* Host-side check of descriptors before they are uploaded: sizes >= 1 and at
+ * most 4096 per axis, ng == 3, dx finite and > 0, patches inside field_len.
+ * Returns ENZO_OK, ENZO_ERR_ARG (NULL) or ENZO_ERR_RANGE; *bad_index (may be
+ * NULL) receives the first offending index or -1. */
+int enzo_validate_patches(const enzo_patch *host_patches, int32_t npatch, int64_t field_len,
+                          int32_t *bad_index);
+
+/* One split PPM sweep along axis dir (0 = x, 1 = y, 2 = z) with timestep dt
+ * (Sec. 4.1: reconstruction, limiter, tracing, two-shock Riemann, fluxes, FP64
+ * conservative update U_j += dt/dx (F_{j-1/2} - F_{j+1/2}), HLL fallback).
+ * cover_mask: bit a set means the pencils also cover the ghost layers of
+ * transverse axis a (the coverage that lets ghosts be filled once per step:
+ * first sweep of a step covers both transverse axes, the second the axis not
+ * yet swept, the third none).  Periodic patches ignore cover_mask.  Updates
+ * active cells along dir in place; reads ghost cells. */
+int enzo_ppm_sweep(const enzo_patch_batch *b, int32_t dir, double dt, int32_t cover_mask,
+                   const enzo_params *p);
+
+/* As enzo_ppm_sweep, with dt read on the device from dt_dev (one double, e.g.
+ * written by enzo_timestep_cfl), so a sequence of calls needs no host sync and
+ * can be captured in a CUDA graph. */
+int enzo_ppm_sweep_dev(const enzo_patch_batch *b, int32_t dir, const double *dt_dev,
+                       int32_t cover_mask, const enzo_params *p);
+
+/* Fill every ghost cell of every non-periodic patch from its own periodic image
+ * (Sec. 3.1, periodic boundary, edges and corners included).  Periodic patches
+ * are left alone (their sweeps wrap). */
+int enzo_ghost_fill_periodic(const enzo_patch_batch *b);
+
+/* Level timestep of Sec. 9: dt = cfl / max over active cells of all patches of
+ * sum_d (c_s + |v_d|)/dx_d, with c_s = sqrt(gamma p / rho).  The min-reduction
+ * runs on the device.  dt_out: DEVICE pointer to one double when
+ * dt_out_on_device != 0 (asynchronous, graph-capturable), else a HOST pointer
+ * (the call synchronises the stream). */
+int enzo_timestep_cfl(const enzo_patch_batch *b, const enzo_params *p, double *dt_out,
+                      int32_t dt_out_on_device);
+
+/* One full step (Sec. 3 control loop for one level, hydro only): ghost fill of
+ * non-periodic patches, then the three split sweeps in the order of step
+ * `step_index` (x,y,z when even, z,y,x when odd) with the once-per-step ghost
+ * coverage.  dt_dev: DEVICE pointer to the step's dt (e.g. written by
+ * enzo_timestep_cfl), read by the kernels, so a captured graph replays with
+ * each step's own dt. */
+int enzo_step(const enzo_patch_batch *b, const enzo_params *p, int32_t step_index,
+              const double *dt_dev);
+
+/* Riemann problems on their own (Sec. 4.1.2): n independent interfaces given
+ * as SoA DEVICE arrays of left/right primitive states.  Outputs (DEVICE,
+ * length n, each may be NULL): pstar, ustar, and the state sampled at x/t = 0
+ * (rho_face, u_face, p_face); iters gets the Newton update count, negated when
+ * the cap was hit.  pguess (may be NULL): per-interface starting guesses
+ * (values <= 0 select the plain guess).  Arrays are float64 when
+ * p->precision == ENZO_FP64 and float32 when ENZO_FP32. */
+typedef struct {
+    int64_t n;
+    const void *rhoL, *uL, *pL, *rhoR, *uR, *pR;
+    const void *pguess;
+    void *pstar, *ustar, *rho_face, *u_face, *p_face;
+    int32_t *iters;
+    void *stream;
+} enzo_riemann_states;
+
+int enzo_riemann_solve(const enzo_riemann_states *s, const enzo_params *p);
+
+/* Text for an ENZO_ERR_* code (static storage). */
+const char *enzo_strerror(int code);
+
+/* Number of kernels the library launched in this process since load. */
+unsigned long long enzo_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ENZO_PPM_H */

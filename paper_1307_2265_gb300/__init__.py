@@ -1,0 +1,250 @@
+"""Python binding of libenzo_ppm, the GB300 split PPM hydro sweep.
+
+This module only marshals arguments: every step of the method runs in the
+library's CUDA kernels.  PyTorch provides device memory and streams.  There is
+no CPU fallback; if the library cannot be built or loaded, `lib()` raises.
+
+Entry points mirror include/enzo_ppm.h: ppm_sweep, ghost_fill_periodic,
+timestep_cfl, step, riemann_solve (and read_status, strerror).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+FP64, FP32 = 0, 1
+GUESS_PLAIN, GUESS_MLP = 0, 1
+PATCH_PERIODIC = 1
+STATUS_WORDS = 16
+STATUS_NAMES = ("interfaces", "newton_iters", "newton_nonconv", "hll_cells", "neg_after",
+                "rho_floor_hits", "p_floor_hits", "nan", "bad_patch", "fp64_eke",
+                "guess_restarts", "guess_calls")
+
+PATCH_DTYPE = np.dtype([("n", "<i4", (3,)), ("ng", "<i4"), ("off", "<i8"), ("dx", "<f8", (3,)),
+                        ("level", "<i4"), ("flags", "<i4")])
+assert PATCH_DTYPE.itemsize == 56
+
+
+class EnzoError(RuntimeError):
+    pass
+
+
+class _Batch(ctypes.Structure):
+    _fields_ = [("npatch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("patches", ctypes.c_void_p), ("field_len", ctypes.c_int64),
+                ("U", ctypes.c_void_p * 5), ("workspace", ctypes.c_void_p),
+                ("ws_bytes", ctypes.c_size_t), ("status", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("guess", ctypes.c_int32),
+                ("newton_tol", ctypes.c_double), ("newton_max", ctypes.c_int32),
+                ("fallback", ctypes.c_int32), ("rho_floor", ctypes.c_double),
+                ("p_floor", ctypes.c_double), ("mlp", ctypes.c_void_p)]
+
+
+class _Riemann(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in
+                ("rhoL", "uL", "pL", "rhoR", "uR", "pR", "pguess", "pstar", "ustar",
+                 "rho_face", "u_face", "p_face", "iters", "stream")]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load (building first if stale) libenzo_ppm.so; raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+            L.enzo_workspace_size.argtypes = [i32]
+            L.enzo_workspace_size.restype = ctypes.c_size_t
+            L.enzo_validate_patches.argtypes = [vp, i32, i64, ctypes.POINTER(i32)]
+            L.enzo_ppm_sweep.argtypes = [ctypes.POINTER(_Batch), i32, d, i32, ctypes.POINTER(_Params)]
+            L.enzo_ppm_sweep_dev.argtypes = [ctypes.POINTER(_Batch), i32, vp, i32, ctypes.POINTER(_Params)]
+            L.enzo_ghost_fill_periodic.argtypes = [ctypes.POINTER(_Batch)]
+            L.enzo_timestep_cfl.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Params), vp, i32]
+            L.enzo_step.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Params), i32, vp]
+            L.enzo_riemann_solve.argtypes = [ctypes.POINTER(_Riemann), ctypes.POINTER(_Params)]
+            L.enzo_strerror.argtypes = [ctypes.c_int]
+            L.enzo_strerror.restype = ctypes.c_char_p
+            L.enzo_launch_count.argtypes = []
+            L.enzo_launch_count.restype = ctypes.c_ulonglong
+            for name in ("enzo_validate_patches", "enzo_ppm_sweep", "enzo_ppm_sweep_dev", "enzo_ghost_fill_periodic",
+                         "enzo_timestep_cfl", "enzo_step", "enzo_riemann_solve"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+        return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().enzo_strerror(code).decode()
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise EnzoError(f"{what}: {strerror(code)} ({code})")
+
+
+def launch_count() -> int:
+    return int(lib().enzo_launch_count())
+
+
+class Params:
+    """Method parameters (enzo_params)."""
+
+    def __init__(self, gamma=5.0 / 3.0, cfl=0.4, precision=FP64, guess=GUESS_PLAIN, newton_tol=0.0,
+                 newton_max=0, fallback=1, rho_floor=1e-30, p_floor=1e-30, mlp=None):
+        self.gamma, self.cfl, self.precision, self.guess = gamma, cfl, precision, guess
+        self.newton_tol, self.newton_max, self.fallback = newton_tol, newton_max, fallback
+        self.rho_floor, self.p_floor, self.mlp = rho_floor, p_floor, mlp
+
+    def c(self) -> _Params:
+        mlp_ptr = 0 if self.mlp is None else (self.mlp.data_ptr() if hasattr(self.mlp, "data_ptr") else int(self.mlp))
+        return _Params(self.gamma, self.cfl, self.precision, self.guess, self.newton_tol,
+                       self.newton_max, self.fallback, self.rho_floor, self.p_floor, mlp_ptr)
+
+
+def patch_table(sizes, offsets, dx, flags=0, ng=3, level=0) -> np.ndarray:
+    """Host descriptor table (PATCH_DTYPE) for patches of active sizes (nx,ny,nz)."""
+    sizes = np.asarray(sizes, dtype=np.int64).reshape(-1, 3)
+    t = np.zeros(len(sizes), dtype=PATCH_DTYPE)
+    t["n"] = sizes
+    t["ng"] = ng
+    t["off"] = np.asarray(offsets, dtype=np.int64)
+    t["dx"] = np.broadcast_to(np.asarray(dx, dtype=np.float64), (len(sizes), 3))
+    t["level"] = level
+    t["flags"] = flags
+    return t
+
+
+class PatchBatch:
+    """A batch of patches sharing one timestep, with device fields, descriptors,
+    workspace and status counters held in torch tensors on one CUDA device."""
+
+    def __init__(self, table: np.ndarray, fields, device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.table = np.ascontiguousarray(table, dtype=PATCH_DTYPE)
+        if isinstance(fields[0], torch.Tensor):
+            self.U = [f.to(self.device, torch.float64).contiguous() for f in fields]
+        else:
+            self.U = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.float64)).to(self.device) for f in fields]
+        self.field_len = int(self.U[0].numel())
+        assert all(int(u.numel()) == self.field_len for u in self.U)
+        bad = ctypes.c_int32(-1)
+        _check(lib().enzo_validate_patches(self.table.ctypes.data, len(self.table), self.field_len,
+                                           ctypes.byref(bad)), f"patch {bad.value}")
+        raw = np.frombuffer(self.table.tobytes(), dtype=np.uint8).copy()
+        self.patches = torch.from_numpy(raw).to(self.device)
+        ws = int(lib().enzo_workspace_size(len(self.table)))
+        self.workspace = torch.zeros(ws // 8 + 32, dtype=torch.float64, device=self.device)
+        self.status = torch.zeros(STATUS_WORDS, dtype=torch.int64, device=self.device)
+        self.dt_dev = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.stream = stream
+        self._ws_bytes = ws
+
+    def c(self) -> _Batch:
+        b = _Batch()
+        b.npatch = len(self.table)
+        b.patches = self.patches.data_ptr()
+        b.field_len = self.field_len
+        for i in range(5):
+            b.U[i] = self.U[i].data_ptr()
+        b.workspace = self.workspace.data_ptr()
+        b.ws_bytes = self._ws_bytes
+        b.status = self.status.data_ptr()
+        s = self.stream if self.stream is not None else self.torch.cuda.current_stream(self.device)
+        b.stream = s.cuda_stream
+        return b
+
+    def read_status(self) -> dict:
+        v = self.status.cpu().numpy().astype(np.uint64)
+        return {n: int(v[i]) for i, n in enumerate(STATUS_NAMES)}
+
+    def reset_status(self):
+        self.status.zero_()
+
+    def patch_fields(self, i):
+        """Device views (z, y, x) of patch i's five stored fields."""
+        nx, ny, nz = (int(v) for v in self.table["n"][i])
+        g = int(self.table["ng"][i])
+        off = int(self.table["off"][i])
+        cnt = (nx + 2 * g) * (ny + 2 * g) * (nz + 2 * g)
+        return [u[off:off + cnt].view(nz + 2 * g, ny + 2 * g, nx + 2 * g) for u in self.U]
+
+
+def ppm_sweep(batch: PatchBatch, direction: int, dt: float, cover_mask: int, params: Params):
+    b, p = batch.c(), params.c()
+    _check(lib().enzo_ppm_sweep(ctypes.byref(b), direction, dt, cover_mask, ctypes.byref(p)), "enzo_ppm_sweep")
+
+
+def ppm_sweep_dev(batch: PatchBatch, direction: int, dt_dev, cover_mask: int, params: Params):
+    """Sweep with dt read on the device from the 1-element float64 tensor dt_dev."""
+    b, p = batch.c(), params.c()
+    _check(lib().enzo_ppm_sweep_dev(ctypes.byref(b), direction, dt_dev.data_ptr(), cover_mask, ctypes.byref(p)),
+           "enzo_ppm_sweep_dev")
+
+
+def ghost_fill_periodic(batch: PatchBatch):
+    b = batch.c()
+    _check(lib().enzo_ghost_fill_periodic(ctypes.byref(b)), "enzo_ghost_fill_periodic")
+
+
+def timestep_cfl(batch: PatchBatch, params: Params, out=None):
+    """Level dt (Sec. 9).  With `out` (a 1-element float64 CUDA tensor) the result
+    stays on the device; otherwise it is returned as a Python float."""
+    b, p = batch.c(), params.c()
+    if out is not None:
+        _check(lib().enzo_timestep_cfl(ctypes.byref(b), ctypes.byref(p), out.data_ptr(), 1), "enzo_timestep_cfl")
+        return out
+    host = ctypes.c_double(0.0)
+    _check(lib().enzo_timestep_cfl(ctypes.byref(b), ctypes.byref(p), ctypes.addressof(host), 0), "enzo_timestep_cfl")
+    return host.value
+
+
+def step(batch: PatchBatch, params: Params, step_index: int, dt_dev):
+    """Ghost fill + three split sweeps in the order of step_index; dt read on the device."""
+    b, p = batch.c(), params.c()
+    _check(lib().enzo_step(ctypes.byref(b), ctypes.byref(p), step_index, dt_dev.data_ptr()), "enzo_step")
+
+
+def riemann_solve(rl, ul, pl, rr, ur, pr, params: Params, pguess=None, stream=None):
+    """Batched Riemann problems on device tensors (float64 for FP64, float32 for FP32)."""
+    import torch
+    n = rl.numel()
+    dt = torch.float64 if params.precision == FP64 else torch.float32
+    ins = [t.contiguous() for t in (rl, ul, pl, rr, ur, pr)]
+    assert all(t.dtype == dt and t.is_cuda for t in ins)
+    outs = [torch.empty(n, dtype=dt, device=rl.device) for _ in range(5)]
+    iters = torch.empty(n, dtype=torch.int32, device=rl.device)
+    s = _Riemann()
+    s.n = n
+    s.rhoL, s.uL, s.pL, s.rhoR, s.uR, s.pR = (t.data_ptr() for t in ins)
+    s.pguess = 0 if pguess is None else pguess.contiguous().data_ptr()
+    s.pstar, s.ustar, s.rho_face, s.u_face, s.p_face = (t.data_ptr() for t in outs)
+    s.iters = iters.data_ptr()
+    st = stream if stream is not None else torch.cuda.current_stream(rl.device)
+    s.stream = st.cuda_stream
+    p = params.c()
+    _check(lib().enzo_riemann_solve(ctypes.byref(s), ctypes.byref(p)), "enzo_riemann_solve")
+    return dict(pstar=outs[0], ustar=outs[1], rho=outs[2], u=outs[3], p=outs[4], iters=iters)
+
+
+def evolve(batch: PatchBatch, params: Params, nsteps: int, step0: int = 0, use_step=True):
+    """Advance nsteps steps: device CFL dt, then enzo_step (all on the stream)."""
+    for s in range(nsteps):
+        timestep_cfl(batch, params, out=batch.dt_dev)
+        step(batch, params, step0 + s, batch.dt_dev)

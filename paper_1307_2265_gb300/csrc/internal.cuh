@@ -1,0 +1,110 @@
+// Internal declarations shared by the CUDA translation units of libenzo_ppm.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "enzo_ppm.h"
+
+namespace enzo {
+
+constexpr int kSweepThreads = 128;     // pencils per tile (one per thread)
+constexpr int kFillThreads = 256;      // stored cells per ghost-fill tile
+constexpr int kCflCells = 4096;        // active cells per CFL tile
+constexpr int kMaxN = 4096;            // per-axis active size limit
+
+// Workspace layout (bytes from the 256-aligned start).
+constexpr size_t kWsCounter = 0;       // uint32 dynamic tile counter
+constexpr size_t kWsRateBits = 8;      // uint64: bits of the max CFL rate (double >= 0)
+constexpr size_t kWsDt = 16;           // double: last dt computed on the device
+constexpr size_t kWsPrefix = 256;      // int32 prefix[npatch + 1] of tiles per patch
+
+// Per-thread counts of frequent events (32-bit, flushed once per thread);
+// rare events are added to the caller's status words when they happen.
+struct Counters {
+    unsigned iters = 0, restarts = 0, guesses = 0;
+    unsigned long long *st = nullptr;
+#ifdef __CUDACC__
+    __device__ __forceinline__ void rare(int word) const
+    {
+        if (st) atomicAdd(st + word, 1ull);
+    }
+#endif
+};
+
+// Method parameters after defaults are applied.
+struct MethodParams {
+    double gamma, rho_floor, p_floor, newton_tol;
+    int newton_max, fallback, guess;
+    const void *mlp;
+};
+
+struct SweepArgs {
+    const enzo_patch *patches;
+    int npatch;
+    int dir;
+    int cover_mask;
+    int64_t field_len;
+    double *U[5];
+    double dt;                 // used when dt_ptr == nullptr
+    const double *dt_ptr;      // device dt (enzo_step)
+    MethodParams mp;
+    const int *prefix;         // [npatch + 1]
+    unsigned *tile_counter;
+    unsigned long long *status;
+};
+
+// Tiles of a sweep along dir for one patch: ceil(pencils / kSweepThreads).
+__host__ __device__ inline void sweep_ranges(const enzo_patch &P, int dir, int cover_mask,
+                                             int lo[3], int hi[3])
+{
+    const bool wrap = (P.flags & ENZO_PATCH_PERIODIC) != 0;
+    for (int a = 0; a < 3; ++a) {
+        const bool cov = !wrap && a != dir && ((cover_mask >> a) & 1);
+        lo[a] = cov ? 0 : P.ng;
+        hi[a] = cov ? P.n[a] + 2 * P.ng : P.ng + P.n[a];
+    }
+}
+
+__host__ __device__ inline bool patch_ok(const enzo_patch &P, int64_t field_len)
+{
+    if (P.ng != 3) return false;
+    for (int a = 0; a < 3; ++a) {
+        if (P.n[a] < 1 || P.n[a] > kMaxN) return false;
+        if (!(P.dx[a] > 0.0) || !(P.dx[a] < 1e300)) return false;
+    }
+    const int64_t vol = (int64_t)(P.n[0] + 6) * (P.n[1] + 6) * (P.n[2] + 6);
+    return P.off >= 0 && P.off + vol <= field_len;
+}
+
+// Launch helpers implemented in the precision translation units.
+cudaError_t launch_sweep_fp64(const SweepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_sweep_fp32(const SweepArgs &a, int grid, cudaStream_t s);
+int sweep_grid_fp64(int device);
+int sweep_grid_fp32(int device);
+
+struct CflArgs {
+    const enzo_patch *patches;
+    int npatch;
+    int64_t field_len;
+    const double *U[5];
+    double gamma, rho_floor, p_floor;
+    const int *prefix;
+    unsigned long long *rate_bits;
+    unsigned long long *status;
+};
+cudaError_t launch_cfl_fp64(const CflArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_cfl_fp32(const CflArgs &a, int grid, cudaStream_t s);
+
+struct RiemannArgs {
+    int64_t n;
+    const void *rl, *ul, *pl, *rr, *ur, *pr, *pguess;
+    void *pstar, *ustar, *rho, *u, *p;
+    int32_t *iters;
+    MethodParams mp;
+};
+cudaError_t launch_riemann_fp64(const RiemannArgs &a, cudaStream_t s);
+cudaError_t launch_riemann_fp32(const RiemannArgs &a, cudaStream_t s);
+
+void note_launch(unsigned n = 1);
+
+}  // namespace enzo

@@ -1,0 +1,878 @@
+// Device code of the split PPM sweep, templated on the arithmetic type.
+//
+// R = double: the FP64 path.  Its translation unit is compiled with
+// --fmad=false and IEEE division/square root, and every formula keeps the
+// association written here, so results are reproducible operation by
+// operation.
+// R = float: the FP32 path (fast reciprocal/sqrt, FMA contraction allowed);
+// conserved variables stay FP64 in memory and are updated in FP64, and the
+// internal energy E - KE is recovered in FP64 where E - KE < eta * E
+// (high-Mach cells).
+//
+// Method (paper Sec. 4.1 and 4.1.2, reconstruction formulas of CW84 that the
+// paper defers to):
+//   primitives rho, u_n, p, u_t1, u_t2 from the conserved state (Sec. 2.1);
+//   limited slopes and interface values q_{j+1/2}; monotone parabola per zone
+//   (q_L, q_R, Delta q, q6); averages over the u-c, u, u+c domains of
+//   dependence; characteristic left/right states (reference wave plus beta
+//   corrections); two-shock Riemann solve with Newton iteration on p*; fluxes;
+//   U_j += dt/dx (F_{j-1/2} - F_{j+1/2}); HLL re-flux of cells whose density
+//   would drop to <= 0.
+//
+// Thread layout: one thread marches one pencil from one end to the other,
+// holding a sliding window of zones in registers: reading cell k it finishes
+// the slope of zone k-1, the interface value at (k-2)+1/2, the parabola and
+// both edge states of zone k-2, the Riemann problem at (k-3)+1/2, decides
+// whether cell k-3 needs the fallback, and writes cell k-4.  Threads of a
+// warp take neighbouring pencils, which for y and z sweeps are neighbouring
+// x positions (coalesced loads and stores).
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace enzo {
+
+template <class R>
+struct Consts {
+    R gamma, gm1, gm1inv, gp1o2g, rho_floor, p_floor, tol, step_tol, eta_eke;
+    int nmax;
+};
+
+template <class R>
+__device__ __forceinline__ Consts<R> make_consts(const MethodParams &m)
+{
+    Consts<R> k;
+    k.gamma = (R)m.gamma;
+    k.gm1 = (R)(m.gamma - 1.0);
+    k.gm1inv = (R)(1.0 / (m.gamma - 1.0));
+    k.gp1o2g = (R)((m.gamma + 1.0) / (2.0 * m.gamma));
+    k.rho_floor = (R)m.rho_floor;
+    k.p_floor = (R)m.p_floor;
+    k.tol = (R)m.newton_tol;
+    k.step_tol = sizeof(R) == 8 ? (R)0 : (R)4e-7;
+    k.eta_eke = (R)0.05;
+    k.nmax = m.newton_max;
+    return k;
+}
+
+template <class R>
+struct Zone {
+    R r, u, p, t1, t2, c;
+};
+
+__device__ __forceinline__ double div6(double x) { return x / 6.0; }
+__device__ __forceinline__ float div6(float x) { return x * (1.0f / 6.0f); }
+
+// Primitive state of one cell from its conserved values (Sec. 2.1), with floors.
+template <class R, bool COUNT>
+__device__ __forceinline__ Zone<R> prim(double rho64, double mn64, double m164, double m264,
+                                        double E64, const Consts<R> &k, Counters &cnt);
+
+template <>
+__device__ __forceinline__ Zone<double> prim<double, true>(double rho, double mn, double m1,
+                                                           double m2, double E,
+                                                           const Consts<double> &k,
+                                                           Counters &cnt)
+{
+    Zone<double> z;
+    if (!(rho >= k.rho_floor)) { rho = k.rho_floor; cnt.rare(ENZO_ST_RHO_FLOOR); }
+    double ke = 0.5 * ((mn * mn + m1 * m1) + m2 * m2) / rho;
+    double p = k.gm1 * (E - ke);
+    if (!(p >= k.p_floor)) { p = k.p_floor; cnt.rare(ENZO_ST_P_FLOOR); }
+    z.r = rho;
+    z.u = mn / rho;
+    z.p = p;
+    z.t1 = m1 / rho;
+    z.t2 = m2 / rho;
+    z.c = sqrt(k.gamma * p / rho);
+    return z;
+}
+
+template <>
+__device__ __forceinline__ Zone<double> prim<double, false>(double rho, double mn, double m1,
+                                                            double m2, double E,
+                                                            const Consts<double> &k,
+                                                            Counters &cnt)
+{
+    Counters quiet;
+    return prim<double, true>(rho, mn, m1, m2, E, k, quiet);
+}
+
+// float <-> double conversions on the integer pipe.  On GB300 the FP64 pipe
+// retires 2 thread-operations per clock per SM (1/64 of FP32), and F2F
+// conversions run on it, so the FP32 path converts with bit operations:
+// d2f rounds toward zero (error below one FP32 ulp; values below the FP32
+// normal range flush to zero, values above it become infinite), f2d is exact
+// for normal and zero floats (denormals are already flushed by -ftz).
+__device__ __forceinline__ float d2f_rz(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    const unsigned bits = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return __uint_as_float(e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : bits));
+}
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u;
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned m = b & 0x7fffffu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+    unsigned lo = m << 29;
+    hi = e == 0u ? sign : (e == 255u ? (sign | 0x7ff00000u | (m >> 3)) : hi);
+    lo = e == 0u ? 0u : lo;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+template <bool COUNT>
+__device__ __forceinline__ Zone<float> prim_f(double rho64, double mn64, double m164,
+                                              double m264, double E64, const Consts<float> &k,
+                                              Counters &cnt)
+{
+    Zone<float> z;
+    float rho = d2f_rz(rho64);
+    if (!(rho >= k.rho_floor)) { rho = k.rho_floor; rho64 = f2d_exact(rho); if (COUNT) cnt.rare(ENZO_ST_RHO_FLOOR); }
+    const float inv = 1.0f / rho;
+    const float mn = d2f_rz(mn64), m1 = d2f_rz(m164), m2 = d2f_rz(m264), E = d2f_rz(E64);
+    const float ke = 0.5f * ((mn * mn + m1 * m1) + m2 * m2) * inv;
+    float e = E - ke;
+    if (e < k.eta_eke * E) {
+        // high-Mach cell: the internal energy is a small difference of two
+        // large numbers, so it is recovered in FP64
+        const double ke64 = 0.5 * ((mn64 * mn64 + m164 * m164) + m264 * m264) / rho64;
+        e = (float)(E64 - ke64);
+        if (COUNT) cnt.rare(ENZO_ST_FP64_EKE);
+    }
+    float p = k.gm1 * e;
+    if (!(p >= k.p_floor)) { p = k.p_floor; if (COUNT) cnt.rare(ENZO_ST_P_FLOOR); }
+    z.r = rho;
+    z.u = mn * inv;
+    z.p = p;
+    z.t1 = m1 * inv;
+    z.t2 = m2 * inv;
+    z.c = sqrtf(k.gamma * p * inv);
+    return z;
+}
+
+template <>
+__device__ __forceinline__ Zone<float> prim<float, true>(double rho, double mn, double m1,
+                                                         double m2, double E,
+                                                         const Consts<float> &k, Counters &cnt)
+{
+    return prim_f<true>(rho, mn, m1, m2, E, k, cnt);
+}
+
+template <>
+__device__ __forceinline__ Zone<float> prim<float, false>(double rho, double mn, double m1,
+                                                          double m2, double E,
+                                                          const Consts<float> &k, Counters &cnt)
+{
+    return prim_f<false>(rho, mn, m1, m2, E, k, cnt);
+}
+
+template <class R>
+__device__ __forceinline__ R zv(const Zone<R> &z, int v)
+{
+    return v == 0 ? z.r : v == 1 ? z.u : v == 2 ? z.p : v == 3 ? z.t1 : z.t2;
+}
+
+// Limited slope of zone j (CW84 1.7-1.8).
+template <class R>
+__device__ __forceinline__ R limited_slope(R qm, R q0, R qp)
+{
+    const R dl = q0 - qm;
+    const R dr = qp - q0;
+    const R dc = (R)0.5 * (qp - qm);
+    R r = (R)0;
+    if (dl * dr > (R)0) {
+        const R a = fabs(dc), b = (R)2 * fabs(dl), e = (R)2 * fabs(dr);
+        R m = a < b ? a : b;
+        m = m < e ? m : e;
+        r = dc >= (R)0 ? m : -m;
+    }
+    return r;
+}
+
+// Monotone parabola of a zone (CW84 1.10): edges ql, qr in, (qL, Delta q, q6) out.
+template <class R>
+__device__ __forceinline__ void parabola(R qs, R ql, R qr, R &oL, R &oR, R &d, R &q6)
+{
+    if ((qr - qs) * (qs - ql) <= (R)0) {
+        ql = qs;
+        qr = qs;
+    } else {
+        const R dd = qr - ql;
+        const R qq6 = (R)6 * (qs - (R)0.5 * (ql + qr));
+        if (dd * qq6 > dd * dd) ql = (R)3 * qs - (R)2 * qr;
+        else if (-(dd * dd) > dd * qq6) qr = (R)3 * qs - (R)2 * ql;
+    }
+    oL = ql;
+    oR = qr;
+    d = qr - ql;
+    q6 = (R)6 * (qs - (R)0.5 * (ql + qr));
+}
+
+// Averages of the zone parabola over the fraction sig of the zone adjacent to
+// its right / left edge (CW84 1.12).
+template <class R>
+__device__ __forceinline__ R avg_right(R qR, R d, R q6, R sig)
+{
+    return qR - ((R)0.5 * sig) * (d - ((R)1 - sig * (R)(2.0 / 3.0)) * q6);
+}
+template <class R>
+__device__ __forceinline__ R avg_left(R qL, R d, R q6, R sig)
+{
+    return qL + ((R)0.5 * sig) * (d + ((R)1 - sig * (R)(2.0 / 3.0)) * q6);
+}
+
+// Characteristic state at one edge of a zone (CW84 3.6/3.7, Sec. 4.1).
+// SIDE = +1: left state of the interface at the zone's right edge (waves with
+// lambda > 0 reach it); SIDE = -1: right state at the zone's left edge.
+// Wave order: 0 = u-c, 1 = u, 2 = u+c.  The reference state is the fastest wave
+// moving toward the edge (u+c or u-c) averaged over its domain, else the edge
+// value; the others enter through beta corrections of the linearised
+// Lagrangian characteristic relations dp +- C du = 0, dp + C^2 d(1/rho) = 0.
+template <class R, int SIDE>
+__device__ __forceinline__ void trace(const R qL[5], const R qR[5], const R d[5], const R q6[5],
+                                      R u, R c, R dtdx, const Consts<R> &k, R out[5])
+{
+    const R lam0 = u - c, lam1 = u, lam2 = u + c;
+    const bool r0 = SIDE > 0 ? lam0 > (R)0 : lam0 < (R)0;
+    const bool r1 = SIDE > 0 ? lam1 > (R)0 : lam1 < (R)0;
+    const bool r2 = SIDE > 0 ? lam2 > (R)0 : lam2 < (R)0;
+    const R s0 = SIDE > 0 ? lam0 * dtdx : -lam0 * dtdx;
+    const R s1 = SIDE > 0 ? lam1 * dtdx : -lam1 * dtdx;
+    const R s2 = SIDE > 0 ? lam2 * dtdx : -lam2 * dtdx;
+#define ENZO_I(SIG, V) (SIDE > 0 ? avg_right<R>(qR[V], d[V], q6[V], SIG) : avg_left<R>(qL[V], d[V], q6[V], SIG))
+    const bool rref = SIDE > 0 ? r2 : r0;
+    const R sref = SIDE > 0 ? s2 : s0;
+    const R *edge = SIDE > 0 ? qR : qL;
+    R rho_ref, u_ref, p_ref;
+    if (rref) {
+        rho_ref = ENZO_I(sref, 0);
+        u_ref = ENZO_I(sref, 1);
+        p_ref = ENZO_I(sref, 2);
+    } else {
+        rho_ref = edge[0];
+        u_ref = edge[1];
+        p_ref = edge[2];
+    }
+    if (!(rho_ref > k.rho_floor)) rho_ref = k.rho_floor;
+    if (!(p_ref > k.p_floor)) p_ref = k.p_floor;
+    const R C = sqrt(k.gamma * p_ref * rho_ref);
+    R bp = (R)0, bm = (R)0, b0 = (R)0;
+    if (r2) bp = -((R)0.5 / C) * ((u_ref - ENZO_I(s2, 1)) + (p_ref - ENZO_I(s2, 2)) / C);
+    if (r0) bm = ((R)0.5 / C) * ((u_ref - ENZO_I(s0, 1)) - (p_ref - ENZO_I(s0, 2)) / C);
+    if (r1) b0 = (p_ref - ENZO_I(s1, 2)) / (C * C) + (R)1 / rho_ref - (R)1 / ENZO_I(s1, 0);
+    R p = p_ref + (C * C) * (bp + bm);
+    const R un = u_ref + C * (bp - bm);
+    const R tau = (R)1 / rho_ref - ((bp + bm) + b0);
+    R rho = (R)1 / tau;
+    if (!(rho > k.rho_floor)) rho = k.rho_floor;
+    if (!(p > k.p_floor)) p = k.p_floor;
+    out[0] = rho;
+    out[1] = un;
+    out[2] = p;
+    out[3] = r1 ? ENZO_I(s1, 3) : edge[3];
+    out[4] = r1 ? ENZO_I(s1, 4) : edge[4];
+#undef ENZO_I
+}
+
+// Lagrangian shock speed W and |dp/du| of the shock curve Z = 2W^3/(W^2+C^2).
+template <class R>
+__device__ __forceinline__ void shock_side(R ps, R p, R C, const Consts<R> &k, R &W, R &Z)
+{
+    R rad = (R)1 + k.gp1o2g * (ps / p - (R)1);
+    if (rad < (R)1e-6) rad = (R)1e-6;
+    W = C * sqrt(rad);
+    Z = (R)2 * W * W * W / (W * W + C * C);
+}
+
+template <class R>
+__device__ __forceinline__ R plain_guess(R rl, R ul, R pl, R rr, R ur, R pr, const Consts<R> &k)
+{
+    const R CL = sqrt(k.gamma * pl * rl);
+    const R CR = sqrt(k.gamma * pr * rr);
+    const R p0 = (CR * pl + CL * pr + CL * CR * (ul - ur)) / (CL + CR);
+    return p0 > k.p_floor ? p0 : k.p_floor;
+}
+
+// Newton iteration on f(p*) = u*_R - u*_L = 0 (two-shock, Sec. 4.1.2).  Stops
+// when |f| <= tol (|u_L| + |u_R| + c_L + c_R), when the update no longer moves
+// p*, or (FP32 only) when the update is below a few ulp of p*.
+template <class R>
+__device__ __forceinline__ int newton(R rl, R ul, R pl, R rr, R ur, R pr, R p0,
+                                      const Consts<R> &k, R &pstar, bool &conv)
+{
+    const R CL = sqrt(k.gamma * pl * rl);
+    const R CR = sqrt(k.gamma * pr * rr);
+    const R uscale = (fabs(ul) + fabs(ur)) + (sqrt(k.gamma * pl / rl) + sqrt(k.gamma * pr / rr));
+    R ps = p0 > k.p_floor ? p0 : k.p_floor;
+    conv = false;
+    int it;
+    for (it = 0; it < k.nmax; ++it) {
+        R WL, ZL, WR, ZR;
+        shock_side(ps, pl, CL, k, WL, ZL);
+        shock_side(ps, pr, CR, k, WR, ZR);
+        const R usL = ul - (ps - pl) / WL;
+        const R usR = ur + (ps - pr) / WR;
+        const R f = usR - usL;
+        if (fabs(f) <= k.tol * uscale) { conv = true; break; }
+        R pn = ps - ZL * ZR * f / (ZL + ZR);
+        if (!(pn > k.p_floor)) pn = k.p_floor;
+        if (pn == ps) { conv = true; break; }
+        if (sizeof(R) == 4 && fabs(pn - ps) <= k.step_tol * pn) { ps = pn; conv = true; ++it; break; }
+        ps = pn;
+    }
+    pstar = ps;
+    return it;
+}
+
+template <class R>
+struct RiemannOut {
+    R rho, u, p, ustar, pstar;
+    int iters;
+    bool conv;
+};
+
+// Two-shock solve and sampling of the self-similar solution at x/t = 0.
+template <class R>
+__device__ __forceinline__ RiemannOut<R> riemann(R rl, R ul, R pl, R rr, R ur, R pr, R pguess,
+                                                 const Consts<R> &k, Counters &cnt)
+{
+    RiemannOut<R> o;
+    R ps;
+    bool conv;
+    int it;
+    if (pguess > (R)0) {
+        it = newton(rl, ul, pl, rr, ur, pr, pguess, k, ps, conv);
+        if (!conv) {
+            cnt.restarts++;
+            it += newton(rl, ul, pl, rr, ur, pr, plain_guess(rl, ul, pl, rr, ur, pr, k), k, ps, conv);
+        }
+    } else {
+        it = newton(rl, ul, pl, rr, ur, pr, plain_guess(rl, ul, pl, rr, ur, pr, k), k, ps, conv);
+    }
+    o.iters = it;
+    o.conv = conv;
+    const R CL = sqrt(k.gamma * pl * rl);
+    const R CR = sqrt(k.gamma * pr * rr);
+    R WL, ZL, WR, ZR;
+    shock_side(ps, pl, CL, k, WL, ZL);
+    shock_side(ps, pr, CR, k, WR, ZR);
+    const R usL = ul - (ps - pl) / WL;
+    const R usR = ur + (ps - pr) / WR;
+    const R us = (ZL * usL + ZR * usR) / (ZL + ZR);
+    R rsL = (R)1 / ((R)1 / rl - (ps - pl) / (WL * WL));
+    R rsR = (R)1 / ((R)1 / rr - (ps - pr) / (WR * WR));
+    if (!(rsL > k.rho_floor)) rsL = k.rho_floor;
+    if (!(rsR > k.rho_floor)) rsR = k.rho_floor;
+    o.ustar = us;
+    o.pstar = ps;
+    R rho, u, p;
+    if (sizeof(R) == 4) {
+        // FP32: the same sampling rule without divergent branches.  sg = +1
+        // samples the left side (contact moving right), -1 the right side; w is
+        // the weight of the star state (0 outside the wave, 1 inside, linear in
+        // the head/tail speed fraction across a transonic rarefaction).
+        const bool left = us >= (R)0;
+        const R sg = left ? (R)1 : (R)-1;
+        const R r_s = left ? rl : rr, u_s = left ? ul : ur, p_s = left ? pl : pr;
+        const R W_s = left ? WL : WR, rs_s = left ? rsL : rsR;
+        const R Sshock = u_s - sg * W_s / r_s;
+        const R c_s = sqrt(k.gamma * p_s / r_s);
+        const R c_st = sqrt(k.gamma * ps / rs_s);
+        const R Sh = u_s - sg * c_s;
+        const R St = us - sg * c_st;
+        const R fr = -Sh / (St - Sh);
+        const R w_rare = sg * Sh >= (R)0 ? (R)0 : (sg * St <= (R)0 ? (R)1 : fr);
+        const R w_shock = sg * Sshock >= (R)0 ? (R)0 : (R)1;
+        const R w = ps > p_s ? w_shock : w_rare;
+        rho = r_s + w * (rs_s - r_s);
+        u = u_s + w * (us - u_s);
+        p = p_s + w * (ps - p_s);
+        o.rho = rho;
+        o.u = u;
+        o.p = p;
+        return o;
+    }
+    if (us >= (R)0) {
+        if (ps > pl) {
+            const R S = ul - WL / rl;
+            if (S >= (R)0) { rho = rl; u = ul; p = pl; }
+            else { rho = rsL; u = us; p = ps; }
+        } else {
+            const R cl = sqrt(k.gamma * pl / rl);
+            const R cs = sqrt(k.gamma * ps / rsL);
+            const R Sh = ul - cl;
+            const R St = us - cs;
+            if (Sh >= (R)0) { rho = rl; u = ul; p = pl; }
+            else if (St <= (R)0) { rho = rsL; u = us; p = ps; }
+            else {
+                const R f = -Sh / (St - Sh);
+                rho = rl + f * (rsL - rl);
+                u = ul + f * (us - ul);
+                p = pl + f * (ps - pl);
+            }
+        }
+    } else {
+        if (ps > pr) {
+            const R S = ur + WR / rr;
+            if (S <= (R)0) { rho = rr; u = ur; p = pr; }
+            else { rho = rsR; u = us; p = ps; }
+        } else {
+            const R cr = sqrt(k.gamma * pr / rr);
+            const R cs = sqrt(k.gamma * ps / rsR);
+            const R Sh = ur + cr;
+            const R St = us + cs;
+            if (Sh <= (R)0) { rho = rr; u = ur; p = pr; }
+            else if (St >= (R)0) { rho = rsR; u = us; p = ps; }
+            else {
+                const R f = Sh / (Sh - St);
+                rho = rr + f * (rsR - rr);
+                u = ur + f * (us - ur);
+                p = pr + f * (ps - pr);
+            }
+        }
+    }
+    o.rho = rho;
+    o.u = u;
+    o.p = p;
+    return o;
+}
+
+// Physical flux of the split 1-D equations (Sec. 4.1): mass, normal momentum,
+// transverse momenta, total energy.
+template <class R>
+__device__ __forceinline__ void phys_flux(R rho, R u, R p, R t1, R t2, const Consts<R> &k, R F[5])
+{
+    const R mflux = rho * u;
+    F[0] = mflux;
+    F[1] = mflux * u + p;
+    F[2] = mflux * t1;
+    F[3] = mflux * t2;
+    const R eint = p * k.gm1inv;
+    const R ke = (R)0.5 * rho * ((u * u + t1 * t1) + t2 * t2);
+    F[4] = u * ((eint + ke) + p);
+}
+
+// HLL flux with Davis wave-speed bounds from first-order zone states (fallback).
+template <class R>
+__device__ __forceinline__ void hll_flux(const Zone<R> &L, const Zone<R> &Rz, const Consts<R> &k,
+                                         R F[5])
+{
+    const R cl = sqrt(k.gamma * L.p / L.r), cr = sqrt(k.gamma * Rz.p / Rz.r);
+    const R SL = L.u - cl < Rz.u - cr ? L.u - cl : Rz.u - cr;
+    const R SR = L.u + cl > Rz.u + cr ? L.u + cl : Rz.u + cr;
+    R FL[5], FR[5];
+    phys_flux(L.r, L.u, L.p, L.t1, L.t2, k, FL);
+    phys_flux(Rz.r, Rz.u, Rz.p, Rz.t1, Rz.t2, k, FR);
+    if (SL >= (R)0) {
+        _Pragma("unroll") for (int c = 0; c < 5; ++c) F[c] = FL[c];
+        return;
+    }
+    if (SR <= (R)0) {
+        _Pragma("unroll") for (int c = 0; c < 5; ++c) F[c] = FR[c];
+        return;
+    }
+    const R UL[5] = {L.r, L.r * L.u, L.r * L.t1, L.r * L.t2,
+                     L.p * k.gm1inv + (R)0.5 * L.r * ((L.u * L.u + L.t1 * L.t1) + L.t2 * L.t2)};
+    const R UR[5] = {Rz.r, Rz.r * Rz.u, Rz.r * Rz.t1, Rz.r * Rz.t2,
+                     Rz.p * k.gm1inv + (R)0.5 * Rz.r * ((Rz.u * Rz.u + Rz.t1 * Rz.t1) + Rz.t2 * Rz.t2)};
+    _Pragma("unroll") for (int c = 0; c < 5; ++c)
+        F[c] = (SR * FL[c] - SL * FR[c] + SL * SR * (UR[c] - UL[c])) / (SR - SL);
+}
+
+// Pencil addressing: storage index of pencil position s (0 .. L-1).
+struct Pencil {
+    int64_t base, sd;
+    int L, ng, n;
+    __device__ __forceinline__ int64_t at(int s) const { return base + (int64_t)s * sd; }
+};
+
+// Face contribution to the FP64 conservative update.  FP64 path: the flux
+// itself (the update is U + dt/dx (F_m - F_p), as in the oracle).  FP32 path:
+// G = dt/dx * F rounded once in FP32 and widened exactly to FP64; a cell then
+// gets (U + G_m) - G_p in FP64, so each face's contribution enters its two
+// cells with opposite signs exactly and the totals change only by FP64 rounding.
+template <class R>
+struct Face {
+    double g[5];
+};
+
+__device__ __forceinline__ double cell_update(double U, double dtdx64, double Fm, double Fp)
+{
+    return U + dtdx64 * (Fm - Fp);
+}
+
+template <class R, bool WRAP, int DIR>
+struct Marcher {
+    static constexpr int A1 = DIR == 0 ? 1 : 0;
+    static constexpr int A2 = DIR == 2 ? 1 : 2;
+    const SweepArgs &a;
+    Pencil pc;
+    Consts<R> k;
+    Zone<R> c0, c1, c2;   // WRAP: initial state of the first three active cells
+
+    __device__ __forceinline__ const double *F(int f) const { return a.U[f]; }
+
+    // Zone at pencil position s, before any update of this sweep.
+    template <bool COUNT>
+    __device__ __forceinline__ Zone<R> zone(int s, Counters &cnt)
+    {
+        int64_t idx;
+        if (WRAP) {
+            const int j = s - pc.ng;
+            if (j >= pc.n) {
+                // trailing ghost: image of active cell (j - n) mod n, which this
+                // pencil may already have updated, so its initial state is kept
+                const int t = (j - pc.n) % pc.n;
+                return t == 0 ? c0 : (t == 1 ? c1 : c2);
+            }
+            const int jj = j < 0 ? (pc.n - ((-j) % pc.n)) % pc.n : j;
+            idx = pc.at(pc.ng + jj);
+        } else {
+            idx = pc.at(s);
+        }
+        return prim<R, COUNT>(a.U[0][idx], a.U[1 + DIR][idx], a.U[1 + A1][idx], a.U[1 + A2][idx],
+                              a.U[4][idx], k, cnt);
+    }
+
+    // Density of cell s at the start of the sweep (raw, no floor).
+    __device__ __forceinline__ double rho_old(int s) const { return a.U[0][pc.at(s)]; }
+
+    // Write the final state of active cell s given its two face terms.
+    __device__ __forceinline__ void update(int s, const R Fm[5], const R Fp[5], double dtdx64,
+                                           const double Gm[5], const double Gp[5], bool fb,
+                                           Counters &cnt)
+    {
+        const int64_t idx = pc.at(s);
+        double u[5];
+        const int map[5] = {0, 1 + DIR, 1 + A1, 1 + A2, 4};
+        _Pragma("unroll") for (int v = 0; v < 5; ++v)
+        {
+            const double U = a.U[map[v]][idx];
+            if (sizeof(R) == 8) u[v] = cell_update(U, dtdx64, (double)Fm[v], (double)Fp[v]);
+            else u[v] = (U + Gm[v]) - Gp[v];
+        }
+        if (fb && !(u[0] > 0.0)) cnt.rare(ENZO_ST_NEG_AFTER);
+        if (u[0] != u[0] || u[4] != u[4]) cnt.rare(ENZO_ST_NAN);
+        _Pragma("unroll") for (int v = 0; v < 5; ++v) const_cast<double *>(a.U[map[v]])[idx] = u[v];
+    }
+
+    __device__ __forceinline__ void widen(const R Fv[5], R dtdx, double G[5]) const
+    {
+        if (sizeof(R) == 4) {
+            _Pragma("unroll") for (int v = 0; v < 5; ++v) G[v] = f2d_exact((float)(dtdx * Fv[v]));
+        }
+    }
+
+    __device__ void run(R dtdx, double dtdx64, const MethodParams &mp, Counters &cnt)
+    {
+        const int L = pc.L;
+        const bool fb = mp.fallback != 0;
+        Zone<R> zm2, zm1, z0;                 // zones k-2, k-1, k
+        R dprev[5], qfprev[5], sLprev[5];
+        R Fgprev[5], Fuprev2[5];
+        double Gprev2[5];                     // FP32 path: widened face term of Fuprev2
+        R rho3 = (R)0, rho2 = (R)0, rho1 = (R)0, rho0 = (R)0;   // FP32: raw densities of cells k-3..k
+        bool badprev = false;
+        _Pragma("unroll") for (int v = 0; v < 5; ++v)
+        {
+            dprev[v] = qfprev[v] = sLprev[v] = Fgprev[v] = Fuprev2[v] = (R)0;
+            Gprev2[v] = 0.0;
+        }
+        z0 = zm1 = zm2 = Zone<R>{};
+        for (int kk = 0; kk < L; ++kk) {
+            zm2 = zm1;
+            zm1 = z0;
+            z0 = zone<true>(kk, cnt);
+            if (WRAP) {
+                const int j = kk - pc.ng;
+                if (j == 0) c0 = z0;
+                else if (j == 1) c1 = z0;
+                else if (j == 2) c2 = z0;
+            }
+            if (sizeof(R) == 4) {
+                rho3 = rho2;
+                rho2 = rho1;
+                rho1 = rho0;
+                rho0 = z0.r;
+            }
+            if (kk < 2) continue;
+            R dcur[5];
+            _Pragma("unroll") for (int v = 0; v < 5; ++v) dcur[v] = limited_slope<R>(zv(zm2, v), zv(zm1, v), zv(z0, v));
+            if (kk >= 3) {
+                R qfcur[5];
+                _Pragma("unroll") for (int v = 0; v < 5; ++v)
+                    qfcur[v] = (R)0.5 * (zv(zm2, v) + zv(zm1, v)) - div6(dcur[v] - dprev[v]);
+                if (kk >= 4) {
+                    // parabola of zone kk-2 (its edges: qfprev on the left, qfcur on the right)
+                    R pL[5], pR[5], pd[5], p6[5];
+                    _Pragma("unroll") for (int v = 0; v < 5; ++v) parabola<R>(zv(zm2, v), qfprev[v], qfcur[v], pL[v], pR[v], pd[v], p6[v]);
+                    R sR[5], sLnew[5];
+                    trace<R, -1>(pL, pR, pd, p6, zm2.u, zm2.c, dtdx, k, sR);
+                    trace<R, +1>(pL, pR, pd, p6, zm2.u, zm2.c, dtdx, k, sLnew);
+                    if (kk >= 5) {
+                        // Riemann problem at interface (kk-3)+1/2
+                        const RiemannOut<R> o = riemann<R>(sLprev[0], sLprev[1], sLprev[2], sR[0], sR[1], sR[2],
+                                                           (R)-1, k, cnt);
+                        cnt.iters += (unsigned)o.iters;
+                        if (!o.conv) cnt.rare(ENZO_ST_NEWTON_NONCONV);
+                        const R t1 = o.ustar >= (R)0 ? sLprev[3] : sR[3];
+                        const R t2 = o.ustar >= (R)0 ? sLprev[4] : sR[4];
+                        R Fg[5];
+                        phys_flux<R>(o.rho, o.u, o.p, t1, t2, k, Fg);
+                        if (kk >= 6) {
+                            // cell c = kk-3: does the Godunov update leave rho > 0?
+                            const int c = kk - 3;
+                            bool bad = false;
+                            if (fb) {
+                                if (sizeof(R) == 8) {
+                                    bad = !(cell_update(rho_old(c), dtdx64, (double)Fgprev[0], (double)Fg[0]) > 0.0);
+                                } else {
+                                    // FP32 screen; cells near zero are decided in FP64
+                                    const R rt = rho3 + dtdx * (Fgprev[0] - Fg[0]);
+                                    if (!(rt > (R)1e-3 * rho3)) {
+                                        const double g0 = f2d_exact((float)(dtdx * Fgprev[0]));
+                                        const double g1 = f2d_exact((float)(dtdx * Fg[0]));
+                                        bad = !((rho_old(c) + g0) - g1 > 0.0);
+                                    }
+                                }
+                                if (bad) cnt.rare(ENZO_ST_HLL_CELLS);
+                            }
+                            // final flux at face (kk-4)+1/2
+                            R Fu1[5];
+                            if (badprev || bad) {
+                                Counters quiet;
+                                const Zone<R> za = zone<false>(kk - 4, quiet);
+                                const Zone<R> zb = zone<false>(kk - 3, quiet);
+                                hll_flux<R>(za, zb, k, Fu1);
+                            } else {
+                                _Pragma("unroll") for (int v = 0; v < 5; ++v) Fu1[v] = Fgprev[v];
+                            }
+                            double G1[5];
+                            widen(Fu1, dtdx, G1);
+                            if (kk >= 7) update(kk - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt);
+                            _Pragma("unroll") for (int v = 0; v < 5; ++v)
+                            {
+                                Fuprev2[v] = Fu1[v];
+                                Gprev2[v] = G1[v];
+                            }
+                            badprev = bad;
+                        }
+                        _Pragma("unroll") for (int v = 0; v < 5; ++v) Fgprev[v] = Fg[v];
+                    }
+                    _Pragma("unroll") for (int v = 0; v < 5; ++v) sLprev[v] = sLnew[v];
+                }
+                _Pragma("unroll") for (int v = 0; v < 5; ++v) qfprev[v] = qfcur[v];
+            }
+            _Pragma("unroll") for (int v = 0; v < 5; ++v) dprev[v] = dcur[v];
+        }
+        // last active cell L-4: its right face (L-4)+1/2 borders a ghost zone
+        R Fu1[5];
+        if (badprev) {
+            Counters quiet;
+            const Zone<R> za = zone<false>(L - 4, quiet);
+            const Zone<R> zb = zone<false>(L - 3, quiet);
+            hll_flux<R>(za, zb, k, Fu1);
+        } else {
+            _Pragma("unroll") for (int v = 0; v < 5; ++v) Fu1[v] = Fgprev[v];
+        }
+        double G1[5];
+        widen(Fu1, dtdx, G1);
+        update(L - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt);
+    }
+};
+
+__device__ __forceinline__ void warp_flush(unsigned long long *status, unsigned long long v, int word)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(status + word, v);
+}
+
+// Persistent sweep kernel: CTAs take (patch, 128-pencil tile) work items from a
+// device counter until the batch is exhausted.  DIR is the sweep axis.
+template <class R, int DIR>
+__global__ void __launch_bounds__(kSweepThreads, sizeof(R) == 4 ? 4 : 2)
+    ppm_sweep_kernel(const __grid_constant__ SweepArgs a)
+{
+    constexpr int A1 = DIR == 0 ? 1 : 0, A2 = DIR == 2 ? 1 : 2;
+    __shared__ int s_tile;
+    Counters cnt;
+    cnt.st = a.status;
+    const Consts<R> k = make_consts<R>(a.mp);
+    const double dt = a.dt_ptr ? *a.dt_ptr : a.dt;
+    const int total = a.prefix[a.npatch];
+    unsigned long long interfaces = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.tile_counter, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        __syncthreads();
+        if (tile >= total) break;
+        int lo = 0, hi = a.npatch;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.prefix[mid] <= tile) lo = mid; else hi = mid;
+        }
+        const enzo_patch P = a.patches[lo];
+        int rlo[3], rhi[3];
+        sweep_ranges(P, DIR, a.cover_mask, rlo, rhi);
+        const int cnt1 = rhi[A1] - rlo[A1], cnt2 = rhi[A2] - rlo[A2];
+        const int pen = (tile - a.prefix[lo]) * kSweepThreads + (int)threadIdx.x;
+        if (pen >= cnt1 * cnt2) continue;
+        const int i1 = rlo[A1] + pen % cnt1, i2 = rlo[A2] + pen / cnt1;
+        const int64_t N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng;
+        const int64_t stride[3] = {1, N0, N0 * N1};
+        Pencil pc;
+        pc.base = P.off + (int64_t)i1 * stride[A1] + (int64_t)i2 * stride[A2];
+        pc.sd = stride[DIR];
+        pc.L = P.n[DIR] + 2 * P.ng;
+        pc.ng = P.ng;
+        pc.n = P.n[DIR];
+        const double dtdx64 = dt / P.dx[DIR];
+        const R dtdx = (R)dtdx64;
+        interfaces += (unsigned long long)(P.n[DIR] + 1);
+        if (P.flags & ENZO_PATCH_PERIODIC) {
+            Marcher<R, true, DIR> m{a, pc, k};
+            m.run(dtdx, dtdx64, a.mp, cnt);
+        } else {
+            Marcher<R, false, DIR> m{a, pc, k};
+            m.run(dtdx, dtdx64, a.mp, cnt);
+        }
+    }
+    warp_flush(a.status, interfaces, ENZO_ST_INTERFACES);
+    warp_flush(a.status, cnt.iters, ENZO_ST_NEWTON_ITERS);
+    warp_flush(a.status, cnt.restarts, ENZO_ST_GUESS_RESTARTS);
+    warp_flush(a.status, cnt.guesses, ENZO_ST_GUESS_CALLS);
+}
+
+// CFL rate of Sec. 9 per active cell, max-reduced into *rate_bits.  A tile is
+// kCflTile active cells of one patch; one thread finds the tile's patch and
+// the block walks the tile's cells with 32-bit index arithmetic.
+constexpr int kCflTile = kCflCells;
+
+template <class R>
+__global__ void __launch_bounds__(256) cfl_kernel(const __grid_constant__ CflArgs a)
+{
+    __shared__ double s_max[8];
+    __shared__ int s_patch;
+    const int total = a.prefix[a.npatch];
+    double best = 0.0;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = a.npatch;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (a.prefix[mid] <= tile) lo = mid; else hi = mid;
+            }
+            s_patch = lo;
+        }
+        __syncthreads();
+        const int pi = s_patch;
+        __syncthreads();
+        const enzo_patch P = a.patches[pi];
+        const int nx = P.n[0], ny = P.n[1];
+        const int64_t ncell = (int64_t)nx * ny * P.n[2];
+        const int64_t first = (int64_t)(tile - a.prefix[pi]) * kCflTile;
+        const int64_t N0 = nx + 2 * P.ng, N1 = ny + 2 * P.ng;
+        const double idx0 = 1.0 / P.dx[0], idx1 = 1.0 / P.dx[1], idx2 = 1.0 / P.dx[2];
+        for (int t = threadIdx.x; t < kCflTile; t += blockDim.x) {
+            const int64_t cell = first + t;
+            if (cell >= ncell) break;
+            const int64_t row = cell / nx;
+            const int i = (int)(cell - row * nx);
+            const int j = (int)(row % ny);
+            const int kz = (int)(row / ny);
+            const int64_t idx = P.off + (i + P.ng) + N0 * ((j + P.ng) + N1 * (int64_t)(kz + P.ng));
+            if (sizeof(R) == 8) {
+                double rho = a.U[0][idx];
+                if (!(rho >= a.rho_floor)) rho = a.rho_floor;
+                const double mx = a.U[1][idx], my = a.U[2][idx], mz = a.U[3][idx];
+                const double ke = 0.5 * ((mx * mx + my * my) + mz * mz) / rho;
+                double p = (a.gamma - 1.0) * (a.U[4][idx] - ke);
+                if (!(p >= a.p_floor)) p = a.p_floor;
+                const double c = sqrt(a.gamma * p / rho);
+                const double r = ((c + fabs(mx / rho)) / P.dx[0] + (c + fabs(my / rho)) / P.dx[1]) +
+                                 (c + fabs(mz / rho)) / P.dx[2];
+                best = r > best ? r : best;
+            } else {
+                Counters quiet;
+                Consts<float> k;
+                k.gamma = (float)a.gamma;
+                k.gm1 = (float)(a.gamma - 1.0);
+                k.rho_floor = (float)a.rho_floor;
+                k.p_floor = (float)a.p_floor;
+                k.eta_eke = 0.05f;
+                const Zone<float> z = prim_f<false>(a.U[0][idx], a.U[1][idx], a.U[2][idx], a.U[3][idx],
+                                                    a.U[4][idx], k, quiet);
+                const float r = ((z.c + fabsf(z.u)) * (float)idx0 + (z.c + fabsf(z.t1)) * (float)idx1) +
+                                (z.c + fabsf(z.t2)) * (float)idx2;
+                best = (double)r > best ? (double)r : best;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double other = __shfl_down_sync(0xffffffffu, best, o);
+        best = other > best ? other : best;
+    }
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_max[w] > m ? s_max[w] : m;
+        if (m > 0.0) atomicMax(a.rate_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// Standalone Riemann problems (one thread per interface).
+template <class R>
+__global__ void __launch_bounds__(256) riemann_kernel(const __grid_constant__ RiemannArgs a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const Consts<R> k = make_consts<R>(a.mp);
+    const R *rl = (const R *)a.rl, *ul = (const R *)a.ul, *pl = (const R *)a.pl;
+    const R *rr = (const R *)a.rr, *ur = (const R *)a.ur, *pr = (const R *)a.pr;
+    const R g = a.pguess ? ((const R *)a.pguess)[i] : (R)-1;
+    Counters cnt;
+    const RiemannOut<R> o = riemann<R>(rl[i], ul[i], pl[i], rr[i], ur[i], pr[i], g, k, cnt);
+    if (a.pstar) ((R *)a.pstar)[i] = o.pstar;
+    if (a.ustar) ((R *)a.ustar)[i] = o.ustar;
+    if (a.rho) ((R *)a.rho)[i] = o.rho;
+    if (a.u) ((R *)a.u)[i] = o.u;
+    if (a.p) ((R *)a.p)[i] = o.p;
+    if (a.iters) a.iters[i] = o.conv ? o.iters : -o.iters;
+}
+
+template <class R>
+int sweep_grid_for(int device)
+{
+    static int cached[64] = {0};
+    if (device < 0 || device >= 64) device = 0;
+    if (cached[device]) return cached[device];
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<R, 0>, kSweepThreads, 0);
+    if (sms < 1) sms = 1;
+    if (per < 1) per = 1;
+    cached[device] = sms * per;
+    return cached[device];
+}
+
+template <class R>
+cudaError_t launch_sweep_dir(const SweepArgs &a, int grid, cudaStream_t s)
+{
+    switch (a.dir) {
+    case 0: ppm_sweep_kernel<R, 0><<<grid, kSweepThreads, 0, s>>>(a); break;
+    case 1: ppm_sweep_kernel<R, 1><<<grid, kSweepThreads, 0, s>>>(a); break;
+    default: ppm_sweep_kernel<R, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace enzo

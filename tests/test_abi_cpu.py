@@ -1,0 +1,84 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every function declared in include/*.h, and rejects bad arguments before any
+CUDA call (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1307_2265_gb300 as ez
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(enzo_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("enzo_ppm_sweep", "enzo_riemann_solve", "enzo_timestep_cfl", "enzo_step",
+                 "enzo_ghost_fill_periodic", "enzo_workspace_size", "enzo_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = ez._build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = sorted(n for n in _declared() if n not in exported)
+    assert not missing, missing
+    L = ez.lib()
+    for n in _declared():
+        assert hasattr(L, n)
+
+
+def test_null_and_bad_arguments_rejected_without_gpu():
+    L = ez.lib()
+    p = ez.Params().c()
+    assert L.enzo_ppm_sweep(None, 0, 0.1, 0, ctypes.byref(p)) == -1
+    b = ez._Batch()
+    b.npatch = -1
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -1
+    b.npatch = 0
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == 0      # empty batch: no-op
+    bad = ez.Params(gamma=1.0).c()
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(bad)) == -1
+    bad = ez.Params(precision=7).c()
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(bad)) == -1
+    b.npatch = 3
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -1      # NULL arrays
+    assert L.enzo_riemann_solve(None, ctypes.byref(p)) == -1
+    assert L.enzo_workspace_size(4000) >= 4 * 4001
+    assert ez.strerror(-3) == "patch descriptor out of range"
+
+
+def test_validate_patches_ranges():
+    L = ez.lib()
+    t = ez.patch_table([(8, 9, 10), (1, 1, 1)], [0, 14 * 15 * 16], [0.1, 0.1, 0.1])
+    total = 14 * 15 * 16 + 7 * 7 * 7
+    bad = ctypes.c_int32(0)
+    assert L.enzo_validate_patches(t.ctypes.data, 2, total, ctypes.byref(bad)) == 0 and bad.value == -1
+    assert L.enzo_validate_patches(t.ctypes.data, 2, total - 1, ctypes.byref(bad)) == -3 and bad.value == 1
+    for field, val in (("ng", 2), ("n", (0, 4, 4)), ("n", (5000, 1, 1)), ("off", -1)):
+        u = t.copy()
+        u[field][0] = val
+        assert L.enzo_validate_patches(u.ctypes.data, 2, total, ctypes.byref(bad)) == -3 and bad.value == 0
+    u = t.copy()
+    u["dx"][1] = (0.1, 0.0, 0.1)
+    assert L.enzo_validate_patches(u.ctypes.data, 2, total, ctypes.byref(bad)) == -3 and bad.value == 1
+
+
+def test_patch_struct_layout_matches_header():
+    assert ez.PATCH_DTYPE.itemsize == 56
+    assert ctypes.sizeof(ez._Batch) == 4 + 4 + 8 + 8 + 40 + 8 + 8 + 8 + 8

@@ -1,0 +1,206 @@
+"""GPU parity of the CUDA path (called through the C ABI) against the FP64 oracle.
+
+Tolerances:
+  * FP64 path: max relative difference per cell <= 1e-11 after 10 steps (the
+    kernels round every operation like the oracle, so the result is expected to
+    be bit-identical; the count of identical cells is asserted too).
+  * FP32 path: per-field L1 relative error <= max(4 x floor, 2e-6) and <= 1e-4,
+    where the floor is the L1 spread of two FP64 oracle runs whose inputs differ
+    by 2^-24 relative noise (the chaotic sensitivity of the flow itself).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1307_2265_gb300 as ez
+from gpu_helpers import (NG, active, batch_from_patches, gpu_evolve, gpu_patches, l1_rel, max_rel,
+                         oracle_evolve_batch, white_patch)
+from paper_1307_2265_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+G = 5.0 / 3.0
+
+
+def _copy(patches):
+    return [[f.copy() for f in U] for U in patches]
+
+
+def test_fp64_config1_ten_steps_matches_oracle():
+    """32^3 periodic, white-noise lognormal rho (sigma 0.5), rms Mach 1, CFL 0.4,
+    10 steps with alternating sweep order."""
+    U = synth.single_grid((32, 32, 32), "white", config=1)
+    dx = [1.0 / 32] * 3
+    P = oracle.Params()
+    ora = _copy([U])
+    dts_o = oracle_evolve_batch(ora, dx, 10, P)
+    b = batch_from_patches([U], dx)
+    dts_g = gpu_evolve(b, ez.Params(precision=ez.FP64), 10)
+    assert dts_g == dts_o
+    g = gpu_patches(b)[0]
+    assert max_rel(g, ora[0], G) <= 1e-11
+    same = sum(int(np.sum(active(a) == active(c))) for a, c in zip(g, ora[0]))
+    assert same == 5 * 32 ** 3
+    st = b.read_status()
+    assert st["nan"] == 0 and st["bad_patch"] == 0 and st["newton_nonconv"] == 0
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2])
+@pytest.mark.parametrize("cover", [0, 3, 5, 6, 7])
+def test_fp64_single_sweep_bitwise(direction, cover):
+    U = white_patch((13, 9, 7), seed=10 + direction, mach=1.5)
+    oracle.fill_periodic(U)
+    dx = [0.1, 0.07, 0.13]
+    P = oracle.Params()
+    dt = 0.4 / oracle.cfl_rate(U, dx, P)
+    ora = [f.copy() for f in U]
+    n = (13, 9, 7)
+    lo = [0 if (cover >> a) & 1 and a != direction else NG for a in range(3)]
+    hi = [n[a] + 2 * NG if (cover >> a) & 1 and a != direction else NG + n[a] for a in range(3)]
+    oracle.sweep(ora, dx, direction, dt, lo, hi, P)
+    b = batch_from_patches([U], dx)
+    ez.ppm_sweep(b, direction, dt, cover, ez.Params(precision=ez.FP64))
+    g = gpu_patches(b)[0]
+    for a, c in zip(g, ora):
+        assert np.array_equal(a, c)
+
+
+RAGGED = [(1, 1, 1), (2, 3, 1), (3, 2, 5), (8, 9, 10), (17, 5, 33), (40, 8, 8), (5, 64, 6)]
+
+
+@pytest.mark.parametrize("flags", [0, ez.PATCH_PERIODIC])
+def test_fp64_ragged_batch_matches_oracle(flags):
+    """Uneven patches (ragged tiles, 1-cell axes, multi-tile patches) in one
+    batch; with the periodic flag the sweeps wrap instead of reading ghosts."""
+    patches = [white_patch(n, seed=100 + i) for i, n in enumerate(RAGGED)]
+    dx = [0.05, 0.05, 0.05]
+    P = oracle.Params()
+    ora = _copy(patches)
+    dts_o = oracle_evolve_batch(ora, dx, 6, P)
+    b = batch_from_patches(patches, dx, flags=flags)
+    dts_g = gpu_evolve(b, ez.Params(precision=ez.FP64), 6)
+    assert dts_g == dts_o
+    for g, o in zip(gpu_patches(b), ora):
+        for a, c in zip(g, o):
+            assert np.array_equal(active(a), active(c))
+
+
+def test_fp64_fallback_matches_oracle():
+    """Violent 1-D data that triggers the HLL re-flux: same cells, same result."""
+    rng = np.random.default_rng(0)
+    shape = (1, 1, 32)
+    for _ in range(16):
+        rho = np.exp(rng.normal(0, 3, shape)); vx = rng.normal(0, 10, shape); p = np.exp(rng.normal(0, 3, shape))
+    z = np.zeros(shape)
+    U = [synth.embed(f) for f in synth.prims_to_conserved(rho, vx, z, z, p, G)]
+    dx = [1.0, 1e30, 1e30]
+    P = oracle.Params()
+    ora = [f.copy() for f in U]
+    hll = 0
+    b = batch_from_patches([U], dx)
+    params = ez.Params(precision=ez.FP64, cfl=0.8)
+    for s in range(20):
+        dt = 0.8 / oracle.cfl_rate(ora, dx, P)
+        st = oracle.step_periodic(ora, dx, dt, s, P)
+        hll += st["hll_cells"]
+        b.dt_dev.fill_(dt)
+        ez.step(b, params, s, b.dt_dev)
+    assert hll > 0
+    assert b.read_status()["hll_cells"] == hll
+    for a, c in zip(gpu_patches(b)[0], ora):
+        assert np.array_equal(active(a), active(c))
+
+
+def test_riemann_fp64_bitwise_and_fp32_close():
+    import torch
+    rng = np.random.default_rng(3)
+    st = synth.riemann_states(rng, 20000, mach=2.0)
+    P = oracle.Params()
+    o = oracle.riemann(*st, P)
+    t = [torch.from_numpy(a).cuda() for a in st]
+    g = ez.riemann_solve(*t, ez.Params(precision=ez.FP64))
+    for k in ("pstar", "ustar", "rho", "u", "p"):
+        assert np.array_equal(g[k].cpu().numpy(), o[k]), k
+    assert np.array_equal(g["iters"].cpu().numpy(), o["iters"])
+    g32 = ez.riemann_solve(*[x.float() for x in t], ez.Params(precision=ez.FP32))
+    # FP32 Newton stops at a residual of 1e-6 (|u_L|+|u_R|+c_L+c_R); through
+    # dp*/du* ~ rho c that leaves an error of ~1e-6 gamma (1 + M) in units of the
+    # side pressures, so errors are measured against p* + max(p_L, p_R)
+    scale = o["pstar"] + np.maximum(st[2], st[5])
+    rel = np.abs(g32["pstar"].cpu().numpy().astype(np.float64) - o["pstar"]) / scale
+    assert np.percentile(rel, 99) < 1e-5 and rel.max() < 3e-5
+
+
+@pytest.mark.parametrize("precision", [ez.FP64, ez.FP32])
+def test_uniform_state_preserved_bitwise_gpu(precision):
+    shape = (6, 5, 7)
+    prims = [np.full(shape, 1.3), np.full(shape, 0.7), np.full(shape, -1.1), np.full(shape, 0.2),
+             np.full(shape, 0.9)]
+    U = [synth.embed(f) for f in synth.prims_to_conserved(*prims, G)]
+    for flags in (0, ez.PATCH_PERIODIC):
+        b = batch_from_patches([U], [0.1, 0.1, 0.1], flags=flags)
+        gpu_evolve(b, ez.Params(precision=precision), 4)
+        for a, c in zip(gpu_patches(b)[0], U):
+            assert np.array_equal(active(a), active(c))
+
+
+def test_ghost_fill_and_cfl_match_oracle():
+    patches = [white_patch(n, seed=200 + i, mach=2.0) for i, n in enumerate(RAGGED)]
+    dx = [0.05, 0.03, 0.07]
+    b = batch_from_patches(patches, dx)
+    ez.ghost_fill_periodic(b)
+    P = oracle.Params()
+    for g, U in zip(gpu_patches(b), patches):
+        oracle.fill_periodic(U)
+        for a, c in zip(g, U):
+            assert np.array_equal(a, c)
+    dt = ez.timestep_cfl(b, ez.Params(precision=ez.FP64, cfl=0.4))
+    assert dt == 0.4 / max(oracle.cfl_rate(U, dx, P) for U in patches)
+
+
+def _fp32_floor(U, dx, nsteps):
+    """L1 spread of two FP64 oracle runs with 2^-24 relative input noise."""
+    P = oracle.Params()
+    base = [f.copy() for f in U]
+    oracle_evolve_batch([base], dx, nsteps, P)
+    rng = np.random.default_rng(77)
+    pert = [f * (1.0 + 2.0 ** -24 * rng.standard_normal(f.shape)) for f in U]
+    oracle_evolve_batch([pert], dx, nsteps, P)
+    return base, l1_rel(pert, base)
+
+
+def test_fp32_config1_l1_error_within_stated_tolerance():
+    U = synth.single_grid((32, 32, 32), "white", config=1)
+    dx = [1.0 / 32] * 3
+    base, floor = _fp32_floor(U, dx, 10)
+    b = batch_from_patches([U], dx)
+    gpu_evolve(b, ez.Params(precision=ez.FP32), 10)
+    err = l1_rel(gpu_patches(b)[0], base)
+    for e, f in zip(err, floor):
+        assert e <= max(4.0 * f, 2e-6) and e <= 1e-4, (err, floor)
+
+
+def test_fp32_periodic_flag_equals_ghosted():
+    """Wrap mode equals ghost fill + coverage; in FP32 the two kernel variants may
+    fuse multiply-adds differently, so agreement is to FP32 rounding (the FP64
+    variant of this equality is bitwise, see test_fp64_ragged_batch_matches_oracle)."""
+    patches = [white_patch(n, seed=300 + i) for i, n in enumerate(RAGGED)]
+    dx = [0.05, 0.05, 0.05]
+    a = batch_from_patches(_copy(patches), dx, flags=0)
+    c = batch_from_patches(_copy(patches), dx, flags=ez.PATCH_PERIODIC)
+    gpu_evolve(a, ez.Params(precision=ez.FP32), 5)
+    gpu_evolve(c, ez.Params(precision=ez.FP32), 5)
+    for ga, gc in zip(gpu_patches(a), gpu_patches(c)):
+        for x, y in zip(ga, gc):
+            assert np.max(np.abs(active(x) - active(y))) <= 1e-5 * np.max(np.abs(active(y)))
+
+
+def test_empty_batch_and_periodic_conservation_gpu():
+    b = ez.PatchBatch(ez.patch_table(np.zeros((0, 3)), [], [1, 1, 1]), [np.zeros(1)] * 5)
+    ez.ppm_sweep(b, 0, 0.1, 7, ez.Params())
+    patches = [white_patch(n, seed=400 + i) for i, n in enumerate(RAGGED)]
+    tot0 = [[active(f).sum() for f in U] for U in patches]
+    bb = batch_from_patches(patches, [0.05] * 3, flags=ez.PATCH_PERIODIC)
+    gpu_evolve(bb, ez.Params(precision=ez.FP32), 10)
+    for g, t0 in zip(gpu_patches(bb), tot0):
+        for f, t in zip(g, t0):
+            assert abs(active(f).sum() - t) <= 1e-12 * (np.abs(active(f)).sum() + abs(t))
