@@ -144,6 +144,27 @@ int enzo_ppm_sweep(const enzo_patch_batch *b, int32_t dir, double dt, int32_t co
 int enzo_ppm_sweep_dev(const enzo_patch_batch *b, int32_t dir, const double *dt_dev,
                        int32_t cover_mask, const enzo_params *p);
 
+/* Allocation-free variant of enzo_ppm_sweep (the paper has no counterpart;
+ * this is an interface convenience).  It is meant for callers that cannot
+ * allocate device memory for this library, for instance a host code that owns
+ * every device buffer through its own pool, or one whose memory budget is
+ * fixed once time stepping starts.  It performs the same sweep with the same
+ * arguments, but ignores b->workspace and b->ws_bytes (they may be NULL / 0).
+ * Its scratch (the tile table and tile counter) lives in a 128 KiB array of
+ * device memory owned by the library.  Every GPU that loads the library keeps
+ * that array until the process exits.
+ *   - At most 32000 patches per call; larger batches return ENZO_ERR_RANGE.
+ *   - The first call on a device looks up the array's device address and
+ *     caches it.  Make that first call before any stream capture.
+ *   - All calls share the array.  Each call rewrites the tile table and zeroes
+ *     the counter before use, so the previous call's contents do not matter,
+ *     but calls whose kernels overlap on the GPU (e.g. on two streams) race on
+ *     it.
+ *   - Nothing is allocated or freed; ENZO_GUESS_MLP returns ENZO_ERR_UNSUPPORTED.
+ * b->patches, b->U, b->status and b->stream are used as in enzo_ppm_sweep. */
+int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, double dt, int32_t cover_mask,
+                           const enzo_params *p);
+
 /* Fill every ghost cell of every non-periodic patch from its own periodic image
  * (Sec. 3.1, periodic boundary, edges and corners included).  Periodic patches
  * are left alone (their sweeps wrap). */

@@ -73,6 +73,7 @@ def lib():
             L.enzo_validate_patches.argtypes = [vp, i32, i64, ctypes.POINTER(i32)]
             L.enzo_ppm_sweep.argtypes = [ctypes.POINTER(_Batch), i32, d, i32, ctypes.POINTER(_Params)]
             L.enzo_ppm_sweep_dev.argtypes = [ctypes.POINTER(_Batch), i32, vp, i32, ctypes.POINTER(_Params)]
+            L.enzo_ppm_sweep_noalloc.argtypes = [ctypes.POINTER(_Batch), i32, d, i32, ctypes.POINTER(_Params)]
             L.enzo_ghost_fill_periodic.argtypes = [ctypes.POINTER(_Batch)]
             L.enzo_timestep_cfl.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Params), vp, i32]
             L.enzo_step.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Params), i32, vp]
@@ -81,7 +82,8 @@ def lib():
             L.enzo_strerror.restype = ctypes.c_char_p
             L.enzo_launch_count.argtypes = []
             L.enzo_launch_count.restype = ctypes.c_ulonglong
-            for name in ("enzo_validate_patches", "enzo_ppm_sweep", "enzo_ppm_sweep_dev", "enzo_ghost_fill_periodic",
+            for name in ("enzo_validate_patches", "enzo_ppm_sweep", "enzo_ppm_sweep_dev", "enzo_ppm_sweep_noalloc",
+                         "enzo_ghost_fill_periodic",
                          "enzo_timestep_cfl", "enzo_step", "enzo_riemann_solve"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
@@ -196,6 +198,18 @@ def ppm_sweep_dev(batch: PatchBatch, direction: int, dt_dev, cover_mask: int, pa
     b, p = batch.c(), params.c()
     _check(lib().enzo_ppm_sweep_dev(ctypes.byref(b), direction, dt_dev.data_ptr(), cover_mask, ctypes.byref(p)),
            "enzo_ppm_sweep_dev")
+
+
+def ppm_sweep_noalloc(batch: PatchBatch, direction: int, dt: float, cover_mask: int, params: Params):
+    """Same sweep as ppm_sweep, for callers that cannot allocate device memory:
+    the library keeps the scratch in its own fixed device array (at most 32000
+    patches per call; calls that overlap on the GPU race on it), so the batch's
+    workspace is not used."""
+    b, p = batch.c(), params.c()
+    b.workspace = None
+    b.ws_bytes = 0
+    _check(lib().enzo_ppm_sweep_noalloc(ctypes.byref(b), direction, dt, cover_mask, ctypes.byref(p)),
+           "enzo_ppm_sweep_noalloc")
 
 
 def ghost_fill_periodic(batch: PatchBatch):

@@ -4,6 +4,7 @@ Translation units and their flags:
   abi.cu        host entry points, work lists, ghost fill, CFL finalisation
   fp64_path.cu  FP64 sweep/CFL/Riemann: --fmad=false, IEEE div and sqrt
   fp32_path.cu  FP32 sweep/CFL/Riemann: -use_fast_math (FMA, fast rcp/sqrt)
+  noalloc.cu    sweep entry point whose scratch is a library-owned device array
   mlp.cu        learned p* guess: tcgen05 inference and training kernels
 Objects go to paper_1307_2265_gb300/_build/, the library next to this file.
 """
@@ -26,6 +27,7 @@ UNITS = {
     "abi.cu": [],
     "fp64_path.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     "fp32_path.cu": ["-use_fast_math"],
+    "noalloc.cu": [],
 }
 OPTIONAL_UNITS = {"mlp.cu": ["-use_fast_math"]}
 

@@ -165,6 +165,14 @@ static int check_batch(const enzo_patch_batch *b)
 
 static char *ws(const enzo_patch_batch *b) { return static_cast<char *>(b->workspace); }
 
+void launch_tile_prefix(const enzo_patch *patches, int npatch, int64_t field_len, int kind, int dir,
+                        int cover, int *prefix, unsigned *counter, unsigned long long *rate_bits,
+                        unsigned long long *status, cudaStream_t s)
+{
+    prefix_kernel<<<1, 1024, 0, s>>>(patches, npatch, field_len, kind, dir, cover, prefix, counter,
+                                     rate_bits, status);
+}
+
 static int launch_prefix(const enzo_patch_batch *b, int kind, int dir, int cover, bool reset_rate,
                          cudaStream_t s)
 {
