@@ -137,6 +137,22 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def measured_traffic(cells_per_sweep):
+    """DRAM bytes per sweep launch from the committed ncu capture, scaled by the
+    cells a launch processes; None when the kernel source changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        with open(os.path.join(ROOT, t["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except (OSError, KeyError, ValueError):
+        return None
+    if sha != t["source_sha256_16"]:
+        return None
+    return float(t["bytes_per_cell_sweep"]) * cells_per_sweep
+
+
 def sweep_bytes(table, flags):
     """Algorithmic HBM bytes of one sweep per direction: each pencil reads its
     cells once and writes its active cells once (5 float64 fields).  Periodic
@@ -275,7 +291,7 @@ def run_gpu(args, rank, world):
         "e2e": {"value": cells * world / (ms_e2e * 1e-3) / 1e6, "unit": "Mcell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "ppm_sweep_kernel<float>",
+                     "frac": achieved / peak, "traffic": measured_traffic(cells), "kernel": "ppm_sweep_kernel<float>",
                      "peak_source": peak_kind, "sweep_ms_avg": sweep_avg},
         "gpu_launches": int(launches),
         "status": status32,

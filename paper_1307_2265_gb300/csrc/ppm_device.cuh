@@ -696,8 +696,11 @@ __device__ __forceinline__ void warp_flush(unsigned long long *status, unsigned 
 
 // Persistent sweep kernel: CTAs take (patch, 128-pencil tile) work items from a
 // device counter until the batch is exhausted.  DIR is the sweep axis.
+#ifndef ENZO_SWEEP_MIN_BLOCKS_FP32
+#define ENZO_SWEEP_MIN_BLOCKS_FP32 4   // 128 registers per thread: 16 warps per SM
+#endif
 template <class R, int DIR>
-__global__ void __launch_bounds__(kSweepThreads, sizeof(R) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(kSweepThreads, sizeof(R) == 4 ? ENZO_SWEEP_MIN_BLOCKS_FP32 : 2)
     ppm_sweep_kernel(const __grid_constant__ SweepArgs a)
 {
     constexpr int A1 = DIR == 0 ? 1 : 0, A2 = DIR == 2 ? 1 : 2;
