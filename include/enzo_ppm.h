@@ -72,6 +72,7 @@ enum {
     ENZO_ST_FP64_EKE = 9,     /* FP32 mode: cells whose E - KE was redone in FP64 */
     ENZO_ST_GUESS_RESTARTS = 10, /* learned guess abandoned for the plain guess */
     ENZO_ST_GUESS_CALLS = 11, /* interfaces given a learned guess */
+    ENZO_ST_TIMEOUT = 12,     /* bounded waits that ran out (tensor-core kernels) */
     ENZO_STATUS_WORDS = 16
 };
 
@@ -204,6 +205,45 @@ typedef struct {
 } enzo_riemann_states;
 
 int enzo_riemann_solve(const enzo_riemann_states *s, const enzo_params *p);
+
+/* ---- learned Newton starting guess for p* (not in the paper) ----
+ * The two-shock solver of Sec. 4.1.2 iterates on p*.  An MLP 6 -> 64 -> 64 -> 1
+ * with SiLU, BF16 weights and FP32 accumulation (tcgen05 tensor cores)
+ * predicts y = ln(p* / sqrt(p_L p_R)) from the Riemann-invariant features
+ *   (ln rho_L/rho_ref, (u_L-u_bar)/c_ref, ln p_L/p_ref, same for R),
+ *   rho_ref = sqrt(rho_L rho_R), p_ref = sqrt(p_L p_R), c_ref = sqrt(gamma p_ref/rho_ref),
+ *   u_bar = (u_L+u_R)/2.
+ * Newton then starts from p_ref exp(y); if it does not converge it restarts
+ * from the plain guess, so answers stay the plain solver's to tolerance.
+ * Master parameters: ENZO_MLP_PARAMS float32 values W1[64][6], b1[64],
+ * W2[64][64], b2[64], w3[64], b3.  The device blob (ENZO_MLP_BLOB_BYTES,
+ * 16-byte aligned) holds the BF16 tensor-core tiles and FP32 vectors the
+ * kernels read; enzo_params.mlp points to it. */
+#define ENZO_MLP_PARAMS 4673
+#define ENZO_MLP_BLOB_BYTES 19456
+
+/* Convert FP32 master parameters (DEVICE) into the blob (DEVICE). */
+int enzo_mlp_pack(const float *master, void *blob, void *stream);
+
+/* y[i] = MLP(x[i][0..5]) for n samples (DEVICE, float32).  status: DEVICE
+ * counters; ENZO_ST_TIMEOUT counts tensor-core waits that ran out (then the
+ * outputs of that CTA are not written). */
+int enzo_mlp_forward(const void *blob, const float *x, float *y, int64_t n, unsigned long long *status,
+                     void *stream);
+
+/* Features x[i][0..5] of n Riemann problems given as float32 SoA states. */
+int enzo_mlp_features(const float *rhoL, const float *uL, const float *pL, const float *rhoR,
+                      const float *uR, const float *pR, double gamma, float *x, int64_t n, void *stream);
+
+/* One training step on n samples (x[n][6], target[n], DEVICE float32): the MSE
+ * loss mean((y - target)^2) goes to *loss and its gradient with respect to the
+ * master parameters to grad[ENZO_MLP_PARAMS] (both overwritten; forward and
+ * backward on tensor cores, BF16 operands, FP32 accumulation).  If lr > 0, an
+ * Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with the 1-based
+ * step) updates master, adam_m and adam_v, and the blob is re-packed. */
+int enzo_mlp_train_step(float *master, float *adam_m, float *adam_v, int32_t step, const float *x,
+                        const float *target, int64_t n, float lr, float *grad, float *loss, void *blob,
+                        unsigned long long *status, void *stream);
 
 /* Text for an ENZO_ERR_* code (static storage). */
 const char *enzo_strerror(int code);

@@ -262,3 +262,100 @@ def evolve(batch: PatchBatch, params: Params, nsteps: int, step0: int = 0, use_s
     for s in range(nsteps):
         timestep_cfl(batch, params, out=batch.dt_dev)
         step(batch, params, step0 + s, batch.dt_dev)
+
+
+# ---------------------------------------------------------------------------
+# learned Newton starting guess (enzo_mlp_*)
+# ---------------------------------------------------------------------------
+MLP_PARAMS = 4673
+MLP_BLOB_BYTES = 19456
+MLP_SLICES = {"W1": (0, (64, 6)), "b1": (384, (64,)), "W2": (448, (64, 64)), "b2": (4544, (64,)),
+              "w3": (4608, (64,)), "b3": (4672, (1,))}
+
+
+def _mlp_lib():
+    L = lib()
+    if not getattr(L, "_mlp_ready", False):
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.enzo_mlp_pack.argtypes = [vp, vp, vp]
+        L.enzo_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.enzo_mlp_features.argtypes = [vp] * 6 + [ctypes.c_double, vp, i64, vp]
+        L.enzo_mlp_train_step.argtypes = [vp, vp, vp, i32, vp, vp, i64, ctypes.c_float, vp, vp, vp, vp, vp]
+        for n in ("enzo_mlp_pack", "enzo_mlp_forward", "enzo_mlp_features", "enzo_mlp_train_step"):
+            getattr(L, n).restype = ctypes.c_int
+        L._mlp_ready = True
+    return L
+
+
+def _stream_ptr(device=None):
+    import torch
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class MLP:
+    """Learned p* guess: FP32 master weights, Adam moments and the packed BF16
+    blob on one CUDA device (all tensors owned here, kernels in libenzo_ppm)."""
+
+    def __init__(self, params=None, device="cuda", seed=0):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        if params is None:
+            rng = np.random.default_rng(seed)
+            flat = np.zeros(MLP_PARAMS)
+            flat[0:384] = rng.normal(0, np.sqrt(2 / 6), 384)
+            flat[448:4544] = rng.normal(0, np.sqrt(2 / 64), 4096)
+            flat[4608:4672] = rng.normal(0, np.sqrt(1 / 64), 64)
+        else:
+            flat = np.concatenate([np.asarray(params[k], dtype=np.float64).reshape(-1) for k in MLP_SLICES])
+        self.master = torch.tensor(flat, dtype=torch.float32, device=self.device)
+        self.m = torch.zeros_like(self.master)
+        self.v = torch.zeros_like(self.master)
+        self.grad = torch.zeros_like(self.master)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.blob = torch.zeros(MLP_BLOB_BYTES // 4, dtype=torch.float32, device=self.device)
+        self.status = torch.zeros(STATUS_WORDS, dtype=torch.int64, device=self.device)
+        self.step = 0
+        self.pack()
+
+    def pack(self):
+        _check(_mlp_lib().enzo_mlp_pack(self.master.data_ptr(), self.blob.data_ptr(), _stream_ptr(self.device)),
+               "enzo_mlp_pack")
+
+    def params(self) -> dict:
+        flat = self.master.double().cpu().numpy()
+        return {k: flat[o:o + int(np.prod(s))].reshape(s) for k, (o, s) in MLP_SLICES.items()}
+
+    def forward(self, x):
+        x = x.contiguous().float()
+        y = self.torch.empty(x.shape[0], dtype=self.torch.float32, device=self.device)
+        _check(_mlp_lib().enzo_mlp_forward(self.blob.data_ptr(), x.data_ptr(), y.data_ptr(), x.shape[0],
+                                           self.status.data_ptr(), _stream_ptr(self.device)), "enzo_mlp_forward")
+        return y
+
+    def train_step(self, x, t, lr):
+        """One Adam step (lr > 0) or a gradient-only pass (lr = 0); returns the loss tensor."""
+        x = x.contiguous().float()
+        t = t.contiguous().float()
+        if lr > 0:
+            self.step += 1
+        _check(_mlp_lib().enzo_mlp_train_step(self.master.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
+                                              max(self.step, 1), x.data_ptr(), t.data_ptr(), x.shape[0], lr,
+                                              self.grad.data_ptr(), self.loss.data_ptr(), self.blob.data_ptr(),
+                                              self.status.data_ptr(), _stream_ptr(self.device)),
+               "enzo_mlp_train_step")
+        return self.loss
+
+    def grads(self) -> dict:
+        flat = self.grad.double().cpu().numpy()
+        return {k: flat[o:o + int(np.prod(s))].reshape(s) for k, (o, s) in MLP_SLICES.items()}
+
+
+def mlp_features(rl, ul, pl, rr, ur, pr, gamma):
+    import torch
+    ins = [t.contiguous().float() for t in (rl, ul, pl, rr, ur, pr)]
+    n = ins[0].numel()
+    x = torch.empty((n, 6), dtype=torch.float32, device=ins[0].device)
+    _check(_mlp_lib().enzo_mlp_features(*[t.data_ptr() for t in ins], float(gamma), x.data_ptr(), n,
+                                        _stream_ptr(ins[0].device)), "enzo_mlp_features")
+    return x

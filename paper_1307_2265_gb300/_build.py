@@ -28,8 +28,9 @@ UNITS = {
     "fp64_path.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     "fp32_path.cu": ["-use_fast_math"],
     "noalloc.cu": [],
+    "mlp.cu": ["-use_fast_math"],
 }
-OPTIONAL_UNITS = {"mlp.cu": ["-use_fast_math"]}
+OPTIONAL_UNITS = {}
 
 
 def nvcc() -> str:
