@@ -115,7 +115,9 @@ typedef struct {
     int32_t fallback;   /* nonzero: HLL re-flux of cells that reach rho <= 0 (Sec. 4.1.2) */
     double rho_floor;   /* density floor, > 0 */
     double p_floor;     /* pressure floor, > 0 */
-    const void *mlp;    /* DEVICE weight blob from enzo_mlp_pack (ENZO_GUESS_MLP only) */
+    const void *mlp;    /* DEVICE weight blob from enzo_mlp_pack (ENZO_GUESS_MLP only;
+                           the learned guess runs in the FP32 path; FP64 returns
+                           ENZO_ERR_UNSUPPORTED) */
 } enzo_params;
 
 /* Bytes of device workspace a batch of npatch patches needs. */
@@ -144,6 +146,16 @@ int enzo_ppm_sweep(const enzo_patch_batch *b, int32_t dir, double dt, int32_t co
  * can be captured in a CUDA graph. */
 int enzo_ppm_sweep_dev(const enzo_patch_batch *b, int32_t dir, const double *dt_dev,
                        int32_t cover_mask, const enzo_params *p);
+
+/* enzo_ppm_sweep that also logs traced interface states for training the
+ * learned guess (not in the paper).  Every interface whose hash of (patch,
+ * pencil, position) is divisible by log_stride appends its left and right
+ * states (rho_L, u_L, p_L, rho_R, u_R, p_R) as float32 to log[slot][6];
+ * *log_count (DEVICE uint64, caller-zeroed) counts appended rows, and rows
+ * beyond log_cap are dropped (the count still grows). */
+int enzo_ppm_sweep_logged(const enzo_patch_batch *b, int32_t dir, double dt, int32_t cover_mask,
+                          const enzo_params *p, float *log, unsigned long long *log_count, int64_t log_cap,
+                          int32_t log_stride);
 
 /* Allocation-free variant of enzo_ppm_sweep (the paper has no counterpart;
  * this is an interface convenience).  It is meant for callers that cannot

@@ -74,6 +74,8 @@ def lib():
             L.enzo_ppm_sweep.argtypes = [ctypes.POINTER(_Batch), i32, d, i32, ctypes.POINTER(_Params)]
             L.enzo_ppm_sweep_dev.argtypes = [ctypes.POINTER(_Batch), i32, vp, i32, ctypes.POINTER(_Params)]
             L.enzo_ppm_sweep_noalloc.argtypes = [ctypes.POINTER(_Batch), i32, d, i32, ctypes.POINTER(_Params)]
+            L.enzo_ppm_sweep_logged.argtypes = [ctypes.POINTER(_Batch), i32, d, i32, ctypes.POINTER(_Params),
+                                                vp, vp, i64, i32]
             L.enzo_ghost_fill_periodic.argtypes = [ctypes.POINTER(_Batch)]
             L.enzo_timestep_cfl.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Params), vp, i32]
             L.enzo_step.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Params), i32, vp]
@@ -83,7 +85,7 @@ def lib():
             L.enzo_launch_count.argtypes = []
             L.enzo_launch_count.restype = ctypes.c_ulonglong
             for name in ("enzo_validate_patches", "enzo_ppm_sweep", "enzo_ppm_sweep_dev", "enzo_ppm_sweep_noalloc",
-                         "enzo_ghost_fill_periodic",
+                         "enzo_ghost_fill_periodic", "enzo_ppm_sweep_logged",
                          "enzo_timestep_cfl", "enzo_step", "enzo_riemann_solve"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
@@ -210,6 +212,15 @@ def ppm_sweep_noalloc(batch: PatchBatch, direction: int, dt: float, cover_mask: 
     b.ws_bytes = 0
     _check(lib().enzo_ppm_sweep_noalloc(ctypes.byref(b), direction, dt, cover_mask, ctypes.byref(p)),
            "enzo_ppm_sweep_noalloc")
+
+
+def ppm_sweep_logged(batch: PatchBatch, direction: int, dt: float, cover_mask: int, params: Params,
+                     log, log_count, stride: int):
+    """Sweep that appends sampled traced interface states to log (float32 [cap, 6])."""
+    b, p = batch.c(), params.c()
+    _check(lib().enzo_ppm_sweep_logged(ctypes.byref(b), direction, dt, cover_mask, ctypes.byref(p),
+                                       log.data_ptr(), log_count.data_ptr(), log.shape[0], stride),
+           "enzo_ppm_sweep_logged")
 
 
 def ghost_fill_periodic(batch: PatchBatch):

@@ -134,7 +134,7 @@ static int resolve(const enzo_params *p, MethodParams &m)
     if (!(p->gamma > 1.0) || !(p->gamma < 100.0)) return ENZO_ERR_ARG;
     if (p->precision != ENZO_FP64 && p->precision != ENZO_FP32) return ENZO_ERR_ARG;
     if (p->guess != ENZO_GUESS_PLAIN && p->guess != ENZO_GUESS_MLP) return ENZO_ERR_ARG;
-    if (p->guess == ENZO_GUESS_MLP && !p->mlp) return ENZO_ERR_ARG;
+    if (p->guess == ENZO_GUESS_MLP && (!p->mlp || (reinterpret_cast<uintptr_t>(p->mlp) & 15u))) return ENZO_ERR_ARG;
     if (!(p->rho_floor > 0.0) || !(p->p_floor > 0.0)) return ENZO_ERR_ARG;
     if (p->precision == ENZO_FP32 && (p->rho_floor < 1e-37 || p->p_floor < 1e-37)) return ENZO_ERR_ARG;
     const bool f64 = p->precision == ENZO_FP64;
@@ -195,7 +195,8 @@ static int device_sms()
 }
 
 static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const double *dt_dev,
-                      int cover, const MethodParams &m, int precision)
+                      int cover, const MethodParams &m, int precision, float *log = nullptr,
+                      unsigned long long *log_count = nullptr, long long log_cap = 0, int log_stride = 0)
 {
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
     int r = launch_prefix(b, kKindSweep, dir, cover, false, s);
@@ -213,10 +214,15 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
     a.prefix = reinterpret_cast<const int *>(ws(b) + kWsPrefix);
     a.tile_counter = reinterpret_cast<unsigned *>(ws(b) + kWsCounter);
     a.status = b->status;
+    a.log = log;
+    a.log_count = log_count;
+    a.log_cap = log_cap;
+    a.log_stride = log_stride;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaError_t e;
     if (precision == ENZO_FP64) e = launch_sweep_fp64(a, sweep_grid_fp64(dev), s);
+    else if (m.guess == ENZO_GUESS_MLP) e = launch_sweep_fp32_learned(a, s);
     else e = launch_sweep_fp32(a, sweep_grid_fp32(dev), s);
     note_launch();
     return e == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
@@ -270,7 +276,7 @@ int enzo_ppm_sweep(const enzo_patch_batch *b, int32_t dir, double dt, int32_t co
     if (r) return r;
     if (dir < 0 || dir > 2 || !(dt >= 0.0) || !std::isfinite(dt) || cover_mask < 0 || cover_mask > 7)
         return ENZO_ERR_ARG;
-    if (m.guess == ENZO_GUESS_MLP) return ENZO_ERR_UNSUPPORTED;
+    if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
     if (b->npatch == 0) return ENZO_OK;
     return sweep_impl(b, dir, dt, nullptr, cover_mask, m, p->precision);
 }
@@ -284,9 +290,26 @@ int enzo_ppm_sweep_dev(const enzo_patch_batch *b, int32_t dir, const double *dt_
     r = resolve(p, m);
     if (r) return r;
     if (dir < 0 || dir > 2 || !dt_dev || cover_mask < 0 || cover_mask > 7) return ENZO_ERR_ARG;
-    if (m.guess == ENZO_GUESS_MLP) return ENZO_ERR_UNSUPPORTED;
+    if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
     if (b->npatch == 0) return ENZO_OK;
     return sweep_impl(b, dir, 0.0, dt_dev, cover_mask, m, p->precision);
+}
+
+int enzo_ppm_sweep_logged(const enzo_patch_batch *b, int32_t dir, double dt, int32_t cover_mask,
+                          const enzo_params *p, float *log, unsigned long long *log_count, int64_t log_cap,
+                          int32_t log_stride)
+{
+    int r = check_batch(b);
+    if (r) return r;
+    MethodParams m;
+    r = resolve(p, m);
+    if (r) return r;
+    if (dir < 0 || dir > 2 || !(dt >= 0.0) || !std::isfinite(dt) || cover_mask < 0 || cover_mask > 7)
+        return ENZO_ERR_ARG;
+    if (!log || !log_count || log_cap < 0 || log_stride < 1) return ENZO_ERR_ARG;
+    if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
+    if (b->npatch == 0) return ENZO_OK;
+    return sweep_impl(b, dir, dt, nullptr, cover_mask, m, p->precision, log, log_count, log_cap, log_stride);
 }
 
 int enzo_ghost_fill_periodic(const enzo_patch_batch *b)
@@ -349,7 +372,7 @@ int enzo_step(const enzo_patch_batch *b, const enzo_params *p, int32_t step_inde
     r = resolve(p, m);
     if (r) return r;
     if (!dt_dev || step_index < 0) return ENZO_ERR_ARG;
-    if (m.guess == ENZO_GUESS_MLP) return ENZO_ERR_UNSUPPORTED;
+    if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
     if (b->npatch == 0) return ENZO_OK;
     r = fill_impl(b);
     if (r) return r;

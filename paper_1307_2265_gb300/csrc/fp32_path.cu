@@ -12,6 +12,40 @@ cudaError_t launch_sweep_fp32(const SweepArgs &a, int grid, cudaStream_t s)
 
 int sweep_grid_fp32(int device) { return sweep_grid_for<float>(device); }
 
+// Sweep with the learned Newton guess (tensor cores inside the sweep).  TMEM
+// holds 128 columns per CTA, so at most 4 CTAs share an SM.
+template <int DIR>
+static cudaError_t launch_learned_dir(const SweepArgs &a, cudaStream_t s)
+{
+    static int grid[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    const size_t smem = sizeof(GuessSmem) + 1024;
+    if (!grid[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(ppm_sweep_kernel<float, DIR, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<float, DIR, true>, kSweepThreads, smem);
+        if (per > 4) per = 4;
+        if (per < 1) per = 1;
+        grid[dev] = (sms > 0 ? sms : 1) * per;
+    }
+    ppm_sweep_kernel<float, DIR, true><<<grid[dev], kSweepThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_fp32_learned(const SweepArgs &a, cudaStream_t s)
+{
+    switch (a.dir) {
+    case 0: return launch_learned_dir<0>(a, s);
+    case 1: return launch_learned_dir<1>(a, s);
+    default: return launch_learned_dir<2>(a, s);
+    }
+}
+
 cudaError_t launch_cfl_fp32(const CflArgs &a, int grid, cudaStream_t s)
 {
     cfl_kernel<float><<<grid, 256, 0, s>>>(a);

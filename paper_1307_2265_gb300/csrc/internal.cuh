@@ -51,6 +51,13 @@ struct SweepArgs {
     const int *prefix;         // [npatch + 1]
     unsigned *tile_counter;
     unsigned long long *status;
+    // interface-state log (optional): every log_stride-th interface of a
+    // pencil, by a hash of (pencil, position), writes its traced left/right
+    // states (rho, u, p) x 2 as float32 into log[slot][6]
+    float *log = nullptr;
+    unsigned long long *log_count = nullptr;
+    long long log_cap = 0;
+    int log_stride = 0;
 };
 
 // Tiles of a sweep along dir for one patch: ceil(pencils / kSweepThreads).
@@ -79,6 +86,7 @@ __host__ __device__ inline bool patch_ok(const enzo_patch &P, int64_t field_len)
 // Launch helpers implemented in the precision translation units.
 cudaError_t launch_sweep_fp64(const SweepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_sweep_fp32(const SweepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_sweep_fp32_learned(const SweepArgs &a, cudaStream_t s);
 int sweep_grid_fp64(int device);
 int sweep_grid_fp32(int device);
 

@@ -29,8 +29,11 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.cuh"
+#include "mlp_layout.cuh"
+#include "tc05.cuh"
 
 namespace enzo {
 
@@ -508,6 +511,141 @@ __device__ __forceinline__ double cell_update(double U, double dtdx64, double Fm
     return U + dtdx64 * (Fm - Fp);
 }
 
+// Starting guess for Newton: the plain acoustic guess (inside riemann()).
+struct PlainGuess {
+    template <class R>
+    __device__ __forceinline__ R operator()(R, R, R, R, R, R) { return (R)-1; }
+};
+
+// Learned guess evaluated on the tensor cores for the 128 interfaces the CTA's
+// pencils reach at the same march step (one per thread = one MMA row).
+struct alignas(1024) GuessSmem {
+    unsigned char w1[64 * 16 * 2];
+    unsigned char w2[64 * 64 * 2];
+    unsigned char a1[128 * 16 * 2];
+    unsigned char a2[128 * 64 * 2];
+    float vec[4 * 64 + 4];   // b1, b2, w3, b3
+    uint64_t mbar;
+    uint32_t tmem;
+};
+
+__device__ __forceinline__ uint32_t silu_bf16x2(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(0.5f * a, 0.5f * b);
+    const uint32_t hb = *reinterpret_cast<const uint32_t *>(&h);
+    uint32_t tb;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(tb) : "r"(hb));
+    const __nv_bfloat162 o = __hfma2(h, *reinterpret_cast<const __nv_bfloat162 *>(&tb), h);
+    return *reinterpret_cast<const uint32_t *>(&o);
+}
+
+struct LearnedGuess {
+    GuessSmem *S;
+    uint32_t phase;
+    bool ok;
+    float gamma;
+
+    __device__ void setup(unsigned char *raw, const void *blob, float g)
+    {
+        S = reinterpret_cast<GuessSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+        const unsigned char *b = static_cast<const unsigned char *>(blob);
+        for (int i = threadIdx.x; i < (int)sizeof(S->w1) / 16; i += blockDim.x)
+            reinterpret_cast<uint4 *>(S->w1)[i] = reinterpret_cast<const uint4 *>(b + kBlobW1)[i];
+        for (int i = threadIdx.x; i < (int)sizeof(S->w2) / 16; i += blockDim.x)
+            reinterpret_cast<uint4 *>(S->w2)[i] = reinterpret_cast<const uint4 *>(b + kBlobW2)[i];
+        for (int i = threadIdx.x; i < 193; i += blockDim.x) S->vec[i] = reinterpret_cast<const float *>(b + kBlobF32)[i];
+        if (threadIdx.x == 0) tc::mbar_init(&S->mbar, 1);
+        if (threadIdx.x < 32) tc::tmem_alloc(&S->tmem, 128);
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        phase = 0;
+        ok = true;
+        gamma = g;
+    }
+
+    __device__ void teardown()
+    {
+        tc::fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) tc::tmem_dealloc(S->tmem, 128);
+    }
+
+    // Every thread of the CTA calls this at the same march step.
+    __device__ float operator()(float rl, float ul, float pl, float rr, float ur, float pr)
+    {
+        if (!ok) return -1.0f;
+        const int row = threadIdx.x;
+        const uint32_t lane = (uint32_t)((row & ~31) << 16);
+        float x[6];
+        mlp_features(rl, ul, pl, rr, ur, pr, gamma, x);
+#pragma unroll
+        for (int kk = 0; kk < 16; kk += 2) {
+            const __nv_bfloat162 v = __floats2bfloat162_rn(kk < 6 ? x[kk] : 0.0f, kk + 1 < 6 ? x[kk + 1] : 0.0f);
+            *reinterpret_cast<__nv_bfloat162 *>(S->a1 + tc::tile_off(row, kk, 16)) = v;
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (row == 0) {
+            tc::fence_after();
+            tc::mma_bf16(S->tmem, tc::smem_desc(tc::smem_u32(S->a1), 128, 256),
+                         tc::smem_desc(tc::smem_u32(S->w1), 128, 256), tc::idesc_bf16_f32(128, 64), false);
+            tc::commit(&S->mbar);
+        }
+        if (__syncthreads_or(!tc::mbar_wait(&S->mbar, phase))) { ok = false; return -1.0f; }
+        phase ^= 1u;
+        tc::fence_after();
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float v[16];
+            tc::tmem_ld16(S->tmem + lane + c * 16, v);
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+                const int j = c * 16 + i;
+                *reinterpret_cast<uint32_t *>(S->a2 + tc::tile_off(row, j, 64)) =
+                    silu_bf16x2(v[i] + S->vec[j], v[i + 1] + S->vec[j + 1]);
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (row == 0) {
+            tc::fence_after();
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                tc::mma_bf16(S->tmem + 64, tc::smem_desc(tc::smem_u32(S->a2) + ks * 256, 128, 1024),
+                             tc::smem_desc(tc::smem_u32(S->w2) + ks * 256, 128, 1024), tc::idesc_bf16_f32(128, 64),
+                             ks > 0);
+            tc::commit(&S->mbar);
+        }
+        if (__syncthreads_or(!tc::mbar_wait(&S->mbar, phase))) { ok = false; return -1.0f; }
+        phase ^= 1u;
+        tc::fence_after();
+        float y = S->vec[192];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float v[16];
+            tc::tmem_ld16(S->tmem + lane + 64 + c * 16, v);
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+                const int j = c * 16 + i;
+                const uint32_t hb = silu_bf16x2(v[i] + S->vec[64 + j], v[i + 1] + S->vec[64 + j + 1]);
+                const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hb));
+                y = fmaf(S->vec[128 + j], h.x, y);
+                y = fmaf(S->vec[128 + j + 1], h.y, y);
+            }
+        }
+        return sqrtf(pl * pr) * __expf(y);
+    }
+
+    template <class R>
+    __device__ __forceinline__ R operator()(R rl, R ul, R pl, R rr, R ur, R pr)
+    {
+        return (R)(*this)((float)rl, (float)ul, (float)pl, (float)rr, (float)ur, (float)pr);
+    }
+};
+
 template <class R, bool WRAP, int DIR>
 struct Marcher {
     static constexpr int A1 = DIR == 0 ? 1 : 0;
@@ -515,6 +653,8 @@ struct Marcher {
     const SweepArgs &a;
     Pencil pc;
     Consts<R> k;
+    bool active;          // false: a stand-in pencil that only keeps the CTA in step
+    unsigned log_key;     // pencil identity for the interface-state log
     Zone<R> c0, c1, c2;   // WRAP: initial state of the first three active cells
 
     __device__ __forceinline__ const double *F(int f) const { return a.U[f]; }
@@ -558,6 +698,7 @@ struct Marcher {
             if (sizeof(R) == 8) u[v] = cell_update(U, dtdx64, (double)Fm[v], (double)Fp[v]);
             else u[v] = (U + Gm[v]) - Gp[v];
         }
+        if (!active) return;
         if (fb && !(u[0] > 0.0)) cnt.rare(ENZO_ST_NEG_AFTER);
         if (u[0] != u[0] || u[4] != u[4]) cnt.rare(ENZO_ST_NAN);
         _Pragma("unroll") for (int v = 0; v < 5; ++v) const_cast<double *>(a.U[map[v]])[idx] = u[v];
@@ -570,7 +711,19 @@ struct Marcher {
         }
     }
 
-    __device__ void run(R dtdx, double dtdx64, const MethodParams &mp, Counters &cnt)
+    __device__ __forceinline__ void log_states(int kk, const R sl[5], const R sr[5])
+    {
+        const unsigned h = (log_key * 2654435761u) ^ ((unsigned)kk * 40503u);
+        if (!active || (h % (unsigned)a.log_stride) != 0u) return;
+        const unsigned long long slot = atomicAdd(a.log_count, 1ull);
+        if ((long long)slot >= a.log_cap) return;
+        float *o = a.log + 6 * slot;
+        o[0] = (float)sl[0]; o[1] = (float)sl[1]; o[2] = (float)sl[2];
+        o[3] = (float)sr[0]; o[4] = (float)sr[1]; o[5] = (float)sr[2];
+    }
+
+    template <class GS>
+    __device__ void run(R dtdx, double dtdx64, const MethodParams &mp, Counters &cnt, GS &guess)
     {
         const int L = pc.L;
         const bool fb = mp.fallback != 0;
@@ -618,10 +771,15 @@ struct Marcher {
                     trace<R, +1>(pL, pR, pd, p6, zm2.u, zm2.c, dtdx, k, sLnew);
                     if (kk >= 5) {
                         // Riemann problem at interface (kk-3)+1/2
+                        if (a.log) log_states(kk, sLprev, sR);
+                        const R p0 = guess(sLprev[0], sLprev[1], sLprev[2], sR[0], sR[1], sR[2]);
                         const RiemannOut<R> o = riemann<R>(sLprev[0], sLprev[1], sLprev[2], sR[0], sR[1], sR[2],
-                                                           (R)-1, k, cnt);
-                        cnt.iters += (unsigned)o.iters;
-                        if (!o.conv) cnt.rare(ENZO_ST_NEWTON_NONCONV);
+                                                           p0, k, cnt);
+                        if (active) {
+                            if (p0 > (R)0) cnt.guesses++;
+                            cnt.iters += (unsigned)o.iters;
+                            if (!o.conv) cnt.rare(ENZO_ST_NEWTON_NONCONV);
+                        }
                         const R t1 = o.ustar >= (R)0 ? sLprev[3] : sR[3];
                         const R t2 = o.ustar >= (R)0 ? sLprev[4] : sR[4];
                         R Fg[5];
@@ -642,7 +800,7 @@ struct Marcher {
                                         bad = !((rho_old(c) + g0) - g1 > 0.0);
                                     }
                                 }
-                                if (bad) cnt.rare(ENZO_ST_HLL_CELLS);
+                                if (bad && active) cnt.rare(ENZO_ST_HLL_CELLS);
                             }
                             // final flux at face (kk-4)+1/2
                             R Fu1[5];
@@ -699,18 +857,24 @@ __device__ __forceinline__ void warp_flush(unsigned long long *status, unsigned 
 #ifndef ENZO_SWEEP_MIN_BLOCKS_FP32
 #define ENZO_SWEEP_MIN_BLOCKS_FP32 4   // 128 registers per thread: 16 warps per SM
 #endif
-template <class R, int DIR>
-__global__ void __launch_bounds__(kSweepThreads, sizeof(R) == 4 ? ENZO_SWEEP_MIN_BLOCKS_FP32 : 2)
+// LEARNED: the CTA evaluates the learned Newton guess on the tensor cores at
+// every interface step, so all 128 threads march in step (threads without a
+// pencil march a stand-in copy of the tile's first pencil and write nothing).
+template <class R, int DIR, bool LEARNED>
+__global__ void __launch_bounds__(kSweepThreads, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_SWEEP_MIN_BLOCKS_FP32 : 2))
     ppm_sweep_kernel(const __grid_constant__ SweepArgs a)
 {
     constexpr int A1 = DIR == 0 ? 1 : 0, A2 = DIR == 2 ? 1 : 2;
     __shared__ int s_tile;
+    extern __shared__ unsigned char dsmem[];
     Counters cnt;
     cnt.st = a.status;
     const Consts<R> k = make_consts<R>(a.mp);
     const double dt = a.dt_ptr ? *a.dt_ptr : a.dt;
     const int total = a.prefix[a.npatch];
     unsigned long long interfaces = 0;
+    typename std::conditional<LEARNED, LearnedGuess, PlainGuess>::type guess;
+    if constexpr (LEARNED) guess.setup(dsmem, a.mp.mlp, (float)a.mp.gamma);
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.tile_counter, 1u);
         __syncthreads();
@@ -726,9 +890,12 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(R) == 4 ? ENZO_SWEEP_MIN
         int rlo[3], rhi[3];
         sweep_ranges(P, DIR, a.cover_mask, rlo, rhi);
         const int cnt1 = rhi[A1] - rlo[A1], cnt2 = rhi[A2] - rlo[A2];
-        const int pen = (tile - a.prefix[lo]) * kSweepThreads + (int)threadIdx.x;
-        if (pen >= cnt1 * cnt2) continue;
-        const int i1 = rlo[A1] + pen % cnt1, i2 = rlo[A2] + pen / cnt1;
+        const int pen0 = (tile - a.prefix[lo]) * kSweepThreads;
+        const int pen = pen0 + (int)threadIdx.x;
+        const bool valid = pen < cnt1 * cnt2;
+        if (!LEARNED && !valid) continue;
+        const int pe = valid ? pen : pen0;
+        const int i1 = rlo[A1] + pe % cnt1, i2 = rlo[A2] + pe / cnt1;
         const int64_t N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng;
         const int64_t stride[3] = {1, N0, N0 * N1};
         Pencil pc;
@@ -739,14 +906,19 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(R) == 4 ? ENZO_SWEEP_MIN
         pc.n = P.n[DIR];
         const double dtdx64 = dt / P.dx[DIR];
         const R dtdx = (R)dtdx64;
-        interfaces += (unsigned long long)(P.n[DIR] + 1);
+        if (valid) interfaces += (unsigned long long)(P.n[DIR] + 1);
+        const unsigned key = (unsigned)lo * 7919u + (unsigned)pe;
         if (P.flags & ENZO_PATCH_PERIODIC) {
-            Marcher<R, true, DIR> m{a, pc, k};
-            m.run(dtdx, dtdx64, a.mp, cnt);
+            Marcher<R, true, DIR> m{a, pc, k, valid, key};
+            m.run(dtdx, dtdx64, a.mp, cnt, guess);
         } else {
-            Marcher<R, false, DIR> m{a, pc, k};
-            m.run(dtdx, dtdx64, a.mp, cnt);
+            Marcher<R, false, DIR> m{a, pc, k, valid, key};
+            m.run(dtdx, dtdx64, a.mp, cnt, guess);
         }
+    }
+    if constexpr (LEARNED) {
+        if (threadIdx.x == 0 && !guess.ok) atomicAdd(a.status + ENZO_ST_TIMEOUT, 1ull);
+        guess.teardown();
     }
     warp_flush(a.status, interfaces, ENZO_ST_INTERFACES);
     warp_flush(a.status, cnt.iters, ENZO_ST_NEWTON_ITERS);
@@ -860,7 +1032,7 @@ int sweep_grid_for(int device)
     if (cached[device]) return cached[device];
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<R, 0>, kSweepThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<R, 0, false>, kSweepThreads, 0);
     if (sms < 1) sms = 1;
     if (per < 1) per = 1;
     cached[device] = sms * per;
@@ -871,9 +1043,9 @@ template <class R>
 cudaError_t launch_sweep_dir(const SweepArgs &a, int grid, cudaStream_t s)
 {
     switch (a.dir) {
-    case 0: ppm_sweep_kernel<R, 0><<<grid, kSweepThreads, 0, s>>>(a); break;
-    case 1: ppm_sweep_kernel<R, 1><<<grid, kSweepThreads, 0, s>>>(a); break;
-    default: ppm_sweep_kernel<R, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
+    case 0: ppm_sweep_kernel<R, 0, false><<<grid, kSweepThreads, 0, s>>>(a); break;
+    case 1: ppm_sweep_kernel<R, 1, false><<<grid, kSweepThreads, 0, s>>>(a); break;
+    default: ppm_sweep_kernel<R, 2, false><<<grid, kSweepThreads, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }

@@ -50,7 +50,7 @@ def grf_kpow(rng: np.random.Generator, shape, power: float = -4.0) -> np.ndarray
     k2[(0,) * len(shape)] = 1.0
     amp = k2 ** (power / 4.0)          # sqrt(P(k)) = k^(power/2)
     amp[(0,) * len(shape)] = 0.0
-    f = np.fft.irfftn(fk * amp, s=shape)
+    f = np.fft.irfftn(fk * amp, s=shape, axes=tuple(range(len(shape))))
     f -= f.mean()
     return f / f.std()
 
