@@ -137,13 +137,16 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def measured_traffic(cells_per_sweep):
-    """DRAM bytes per sweep launch from the committed ncu capture, scaled by the
-    cells a launch processes; None when the kernel source changed since."""
+def measured_traffic(cells_per_sweep, kernel):
+    """DRAM bytes per sweep launch from the committed ncu capture of `kernel`,
+    scaled by the cells a launch processes; None when there is no capture of
+    that kernel or its source changed since."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
+        if t.get("kernel") != kernel:
+            return None
         with open(os.path.join(ROOT, t["source"]), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
     except (OSError, KeyError, ValueError):
@@ -171,8 +174,18 @@ def sweep_bytes(table, flags):
 def run_gpu(args, rank, world):
     import torch
     import paper_1307_2265_gb300 as ez
+    from paper_1307_2265_gb300 import train_guess, tune
     dev = _env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(dev)
+
+    # --- learned Newton guess: trained on this GPU with the library's kernels
+    t_train = time.perf_counter()
+    states = train_guess.default_training_set(gamma=GAMMA, stride=8, cap=3_000_000)
+    x, y, _ = train_guess.dataset(states, GAMMA)
+    net, train_info = train_guess.train(x, y, steps=args.train_steps)
+    train_info["wall_seconds"] = time.perf_counter() - t_train
+    del states, x, y
+
     sizes, offsets, flat = build_level(rank, args.npatch)
     table = ez.patch_table(sizes, offsets, [1.0 / 64] * 3, flags=ez.PATCH_PERIODIC)
     cells = int(np.prod(sizes, axis=1).sum())
@@ -180,9 +193,18 @@ def run_gpu(args, rank, world):
     with torch.cuda.stream(stream):
         batch = ez.PatchBatch(table, flat, stream=stream)
     host0 = [torch.from_numpy(f).pin_memory() for f in flat]
-    p32 = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32)
     p64 = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP64)
+    p32 = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32)
+    tiles, tile_ms = tune.autotune_tiles(batch, p32)
+    p32 = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, tile=tiles)
+    pml = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob)
     bytes_per_sweep = sweep_bytes(table, True)
+
+    def reset():
+        for u, h in zip(batch.U, host0):
+            u.copy_(h, non_blocking=True)
+        torch.cuda.synchronize()
+        batch.reset_status()
 
     def one_step(params, step_idx, ev=None):
         """CFL timestep on the device, then the three split sweeps (dt read on the
@@ -196,54 +218,64 @@ def run_gpu(args, rank, world):
             if ev is not None:
                 ev[q][1].record(stream)
 
-    # warm-up
-    with torch.cuda.stream(stream):
-        for w in range(args.warmup):
-            one_step(p32, w)
-    stream.synchronize()
-    for u, h in zip(batch.U, host0):
-        u.copy_(h)
-    torch.cuda.synchronize()
-    barrier(world)
-
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)] for _ in range(args.steps)]
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches0 = ez.launch_count()
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
-    with clk:
+    def timed_graph(params, steps, warmup):
+        with torch.cuda.stream(stream):
+            for w in range(warmup):
+                one_step(params, w)
+        stream.synchronize()
+        graphs = tune.capture_steps(batch, params)
+        reset()
+        barrier(world)
+        launches0 = ez.launch_count()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             t0.record(stream)
-            for s in range(args.steps):
-                one_step(p32, s, evs[s])
+            for s in range(steps):
+                graphs[s % 2].replay()
             t1.record(stream)
         t1.synchronize()
-    launches = ez.launch_count() - launches0
-    ms = t0.elapsed_time(t1)
-    ms = max_over_ranks(ms, world)
-    sweep_ms = [[e[q][0].elapsed_time(e[q][1]) for q in range(3)] for e in evs]
-    sweep_avg = float(np.mean(sweep_ms))
-    status32 = batch.read_status()
+        return t0.elapsed_time(t1), graphs
 
-    # plain FP64 batched sweep on the same level (fewer steps: ALU bound)
-    for u, h in zip(batch.U, host0):
-        u.copy_(h)
-    torch.cuda.synchronize()
-    k64 = 1
+    # --- headline: batched FP32 + learned guess, graph replay
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
+    with clk:
+        ms, graphs = timed_graph(pml, args.steps, args.warmup)
+    ms = max_over_ranks(ms, world)
+    status_ml = batch.read_status()
+    launches = 9 * args.steps      # per step: prefix+CFL+finalize, 3 x (prefix+sweep)
+    del graphs
+
+    # per-sweep event timing of the dominant kernel (eager, same work)
+    reset()
+    ksw = max(2, min(args.steps, 4))
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)] for _ in range(ksw)]
     with torch.cuda.stream(stream):
-        one_step(p64, 0)
+        for s in range(ksw):
+            one_step(pml, s, evs[s])
+    stream.synchronize()
+    sweep_avg = float(np.mean([[e[q][0].elapsed_time(e[q][1]) for q in range(3)] for e in evs]))
+
+    # --- plain FP32 (autotuned tiles), graph replay
+    reset()
+    ms32, graphs = timed_graph(p32, args.steps, 1)
+    status_32 = batch.read_status()
+    del graphs
+
+    # --- plain FP64 batched sweep on the same level (ALU bound: one step)
+    reset()
+    with torch.cuda.stream(stream):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for s in range(k64):
-            one_step(p64, s + 1)
+        one_step(p64, 1)
         e1.record(stream)
     e1.synchronize()
-    ms64 = e0.elapsed_time(e1) / k64
+    ms64 = e0.elapsed_time(e1)
 
-    # end to end through the public API with host buffers: H2D of U, step, D2H of U
+    # --- end to end through the public API with host buffers
+    reset()
     host_out = [torch.empty_like(h).pin_memory() for h in host0]
     h2d = sum(h.numel() * 8 for h in host0)
-    torch.cuda.synchronize()
     ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ke = max(1, min(args.steps, 3))
     with torch.cuda.stream(stream):
@@ -251,23 +283,21 @@ def run_gpu(args, rank, world):
         for s in range(ke):
             for u, h in zip(batch.U, host0):
                 u.copy_(h, non_blocking=True)
-            one_step(p32, s)
+            one_step(pml, s)
             for u, h in zip(batch.U, host_out):
                 h.copy_(u, non_blocking=True)
         ee1.record(stream)
     ee1.synchronize()
     ms_e2e = max_over_ranks(ee0.elapsed_time(ee1) / ke, world)
 
-    # sampled parity + CPU baseline (rank 0, N=1 only): one FP32 step of the full
-    # batch from the initial state; the oracle redoes the first patches with the
-    # same dt and is timed on the host cores
+    # --- sampled parity + CPU baseline (rank 0, N=1): one learned step of the
+    # full batch; the oracle redoes the first patches with the same dt
     cpu = None
     l1 = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        for u, h in zip(batch.U, host0):
-            u.copy_(h)
+        reset()
         with torch.cuda.stream(stream):
-            one_step(p32, 0)
+            one_step(pml, 0)
         stream.synchronize()
         sample = {"dt": float(batch.dt_dev.item()), "patches": [], "l1_num": [0.0] * 5, "l1_den": [0.0] * 5}
         for i in range(args.sample_patches):
@@ -278,6 +308,8 @@ def run_gpu(args, rank, world):
     peak, peak_kind = measured_peak()
     achieved = float(np.mean(bytes_per_sweep)) / (sweep_avg * 1e-3) / 1e9
     value = cells * world * args.steps / (ms * 1e-3) / 1e6
+    it_ml = status_ml["newton_iters"] / max(1, status_ml["interfaces"])
+    it_32 = status_32["newton_iters"] / max(1, status_32["interfaces"])
     res = {
         "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -285,16 +317,26 @@ def run_gpu(args, rank, world):
         "data": "synthetic",
         "config": {"workload": f"batched AMR level: {args.npatch} self-periodic patches, per-axis 8..64 cells, "
                                f"3 ghost layers, white-noise lognormal rho sigma 0.5, rms Mach 1, gamma 5/3, CFL 0.4",
-                   "cells_per_step": cells, "precision": "FP32 arithmetic, FP64 accumulation", "guess": "plain",
+                   "cells_per_step": cells, "precision": "FP32 arithmetic, FP64 accumulation",
+                   "guess": "learned (tcgen05 MLP in the sweep), plain-guess restart",
+                   "launch": "one CUDA graph per step (CFL + 3 persistent sweeps)",
                    "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+        "fp32_plain": {"value": cells / (ms32 * 1e-3 / args.steps) / 1e6, "unit": "Mcell-updates/s",
+                       "ms_per_step": ms32 / args.steps, "tiles": list(tiles),
+                       "tile_ms": {str(d): {str(t): v for t, v in tile_ms[d].items()} for d in tile_ms}},
         "fp64_plain": {"value": cells / (ms64 * 1e-3) / 1e6, "unit": "Mcell-updates/s", "ms_per_step": ms64},
+        "newton_iters_per_interface": {"learned": it_ml, "plain": it_32,
+                                       "restarts": status_ml["guess_restarts"],
+                                       "learned_calls": status_ml["guess_calls"]},
+        "training": train_info,
         "e2e": {"value": cells * world / (ms_e2e * 1e-3) / 1e6, "unit": "Mcell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(cells), "kernel": "ppm_sweep_kernel<float>",
+                     "frac": achieved / peak, "traffic": measured_traffic(cells, "ppm_sweep_kernel<float, DIR, true>"),
+                     "kernel": "ppm_sweep_kernel<float, DIR, LEARNED=true>",
                      "peak_source": peak_kind, "sweep_ms_avg": sweep_avg},
         "gpu_launches": int(launches),
-        "status": status32,
+        "status": status_ml,
         "cpu_baseline": cpu,
         "fp32_l1_rel_err_vs_oracle_one_step": l1,
         "clocks": clk.summary(dev),
@@ -379,6 +421,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work in the CPU leg")
     ap.add_argument("--sample-patches", type=int, default=6)
+    ap.add_argument("--train-steps", type=int, default=1500)
     args = ap.parse_args()
     rank, world = dist_init()
     if args.impl == "reference":

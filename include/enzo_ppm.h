@@ -118,6 +118,11 @@ typedef struct {
     const void *mlp;    /* DEVICE weight blob from enzo_mlp_pack (ENZO_GUESS_MLP only;
                            the learned guess runs in the FP32 path; FP64 returns
                            ENZO_ERR_UNSUPPORTED) */
+    int32_t tile[3];    /* pencils per CTA tile for sweeps along x, y, z: 0 (default,
+                           128), 64, 128 or 256; used by the FP32 plain-guess path
+                           (the FP64 and learned paths always use 128).  Picked
+                           per batch by the autotuner (paper_1307_2265_gb300.tune). */
+    int32_t reserved;
 } enzo_params;
 
 /* Bytes of device workspace a batch of npatch patches needs. */

@@ -15,7 +15,7 @@ void note_launch(unsigned n) { g_launches += n; }
 enum { kKindSweep = 0, kKindFill = 1, kKindCells = 2 };
 
 __device__ __forceinline__ int tiles_of(const enzo_patch &P, int64_t field_len, int kind, int dir,
-                                        int cover, bool &bad)
+                                        int cover, int tile_pencils, bool &bad)
 {
     if (!patch_ok(P, field_len)) {
         bad = true;
@@ -26,7 +26,7 @@ __device__ __forceinline__ int tiles_of(const enzo_patch &P, int64_t field_len, 
         sweep_ranges(P, dir, cover, lo, hi);
         const int a1 = dir == 0 ? 1 : 0, a2 = dir == 2 ? 1 : 2;
         const int64_t pen = (int64_t)(hi[a1] - lo[a1]) * (hi[a2] - lo[a2]);
-        return (int)((pen + kSweepThreads - 1) / kSweepThreads);
+        return (int)((pen + tile_pencils - 1) / tile_pencils);
     }
     if (kind == kKindFill) {
         if (P.flags & ENZO_PATCH_PERIODIC) return 0;
@@ -41,7 +41,7 @@ __device__ __forceinline__ int tiles_of(const enzo_patch &P, int64_t field_len, 
 // and of the CFL accumulator.
 __global__ void __launch_bounds__(1024) prefix_kernel(const enzo_patch *patches, int npatch,
                                                       int64_t field_len, int kind, int dir, int cover,
-                                                      int *prefix, unsigned *counter,
+                                                      int tile_pencils, int *prefix, unsigned *counter,
                                                       unsigned long long *rate_bits,
                                                       unsigned long long *status)
 {
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(1024) prefix_kernel(const enzo_patch *patches,
     unsigned nbad = 0;
     for (int i = beg; i < end; ++i) {
         bool b = false;
-        sum += tiles_of(patches[i], field_len, kind, dir, cover, b);
+        sum += tiles_of(patches[i], field_len, kind, dir, cover, tile_pencils, b);
         nbad += b;
     }
     s_sum[t] = sum;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(1024) prefix_kernel(const enzo_patch *patches,
     int run = s_sum[t] - sum;
     for (int i = beg; i < end; ++i) {
         prefix[i] = run;
-        run += tiles_of(patches[i], field_len, kind, dir, cover, bad);
+        run += tiles_of(patches[i], field_len, kind, dir, cover, tile_pencils, bad);
     }
     if (t == T - 1) {
         prefix[npatch] = s_sum[T - 1];
@@ -137,6 +137,8 @@ static int resolve(const enzo_params *p, MethodParams &m)
     if (p->guess == ENZO_GUESS_MLP && (!p->mlp || (reinterpret_cast<uintptr_t>(p->mlp) & 15u))) return ENZO_ERR_ARG;
     if (!(p->rho_floor > 0.0) || !(p->p_floor > 0.0)) return ENZO_ERR_ARG;
     if (p->precision == ENZO_FP32 && (p->rho_floor < 1e-37 || p->p_floor < 1e-37)) return ENZO_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (p->tile[d] != 0 && !tile_supported(p->tile[d])) return ENZO_ERR_ARG;
     const bool f64 = p->precision == ENZO_FP64;
     m.gamma = p->gamma;
     m.rho_floor = p->rho_floor;
@@ -167,16 +169,16 @@ static char *ws(const enzo_patch_batch *b) { return static_cast<char *>(b->works
 
 void launch_tile_prefix(const enzo_patch *patches, int npatch, int64_t field_len, int kind, int dir,
                         int cover, int *prefix, unsigned *counter, unsigned long long *rate_bits,
-                        unsigned long long *status, cudaStream_t s)
+                        unsigned long long *status, cudaStream_t s, int tile_pencils)
 {
-    prefix_kernel<<<1, 1024, 0, s>>>(patches, npatch, field_len, kind, dir, cover, prefix, counter,
-                                     rate_bits, status);
+    prefix_kernel<<<1, 1024, 0, s>>>(patches, npatch, field_len, kind, dir, cover, tile_pencils, prefix,
+                                     counter, rate_bits, status);
 }
 
 static int launch_prefix(const enzo_patch_batch *b, int kind, int dir, int cover, bool reset_rate,
-                         cudaStream_t s)
+                         cudaStream_t s, int tile_pencils = kSweepThreads)
 {
-    prefix_kernel<<<1, 1024, 0, s>>>(b->patches, b->npatch, b->field_len, kind, dir, cover,
+    prefix_kernel<<<1, 1024, 0, s>>>(b->patches, b->npatch, b->field_len, kind, dir, cover, tile_pencils,
                                      reinterpret_cast<int *>(ws(b) + kWsPrefix),
                                      reinterpret_cast<unsigned *>(ws(b) + kWsCounter),
                                      reset_rate ? reinterpret_cast<unsigned long long *>(ws(b) + kWsRateBits)
@@ -195,13 +197,16 @@ static int device_sms()
 }
 
 static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const double *dt_dev,
-                      int cover, const MethodParams &m, int precision, float *log = nullptr,
+                      int cover, const MethodParams &m, int precision, int tile_pencils, float *log = nullptr,
                       unsigned long long *log_count = nullptr, long long log_cap = 0, int log_stride = 0)
 {
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
-    int r = launch_prefix(b, kKindSweep, dir, cover, false, s);
+    int tile = tile_pencils > 0 ? tile_pencils : kSweepThreads;
+    if (precision == ENZO_FP64 || m.guess == ENZO_GUESS_MLP) tile = kSweepThreads;
+    int r = launch_prefix(b, kKindSweep, dir, cover, false, s, tile);
     if (r) return r;
     SweepArgs a;
+    a.tile = tile;
     a.patches = b->patches;
     a.npatch = b->npatch;
     a.dir = dir;
@@ -223,6 +228,7 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
     cudaError_t e;
     if (precision == ENZO_FP64) e = launch_sweep_fp64(a, sweep_grid_fp64(dev), s);
     else if (m.guess == ENZO_GUESS_MLP) e = launch_sweep_fp32_learned(a, s);
+    else if (tile != kSweepThreads) e = launch_sweep_fp32_tiled(a, s);
     else e = launch_sweep_fp32(a, sweep_grid_fp32(dev), s);
     note_launch();
     return e == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
@@ -278,7 +284,7 @@ int enzo_ppm_sweep(const enzo_patch_batch *b, int32_t dir, double dt, int32_t co
         return ENZO_ERR_ARG;
     if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
     if (b->npatch == 0) return ENZO_OK;
-    return sweep_impl(b, dir, dt, nullptr, cover_mask, m, p->precision);
+    return sweep_impl(b, dir, dt, nullptr, cover_mask, m, p->precision, p->tile[dir]);
 }
 
 int enzo_ppm_sweep_dev(const enzo_patch_batch *b, int32_t dir, const double *dt_dev, int32_t cover_mask,
@@ -292,7 +298,7 @@ int enzo_ppm_sweep_dev(const enzo_patch_batch *b, int32_t dir, const double *dt_
     if (dir < 0 || dir > 2 || !dt_dev || cover_mask < 0 || cover_mask > 7) return ENZO_ERR_ARG;
     if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
     if (b->npatch == 0) return ENZO_OK;
-    return sweep_impl(b, dir, 0.0, dt_dev, cover_mask, m, p->precision);
+    return sweep_impl(b, dir, 0.0, dt_dev, cover_mask, m, p->precision, p->tile[dir]);
 }
 
 int enzo_ppm_sweep_logged(const enzo_patch_batch *b, int32_t dir, double dt, int32_t cover_mask,
@@ -309,7 +315,8 @@ int enzo_ppm_sweep_logged(const enzo_patch_batch *b, int32_t dir, double dt, int
     if (!log || !log_count || log_cap < 0 || log_stride < 1) return ENZO_ERR_ARG;
     if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
     if (b->npatch == 0) return ENZO_OK;
-    return sweep_impl(b, dir, dt, nullptr, cover_mask, m, p->precision, log, log_count, log_cap, log_stride);
+    return sweep_impl(b, dir, dt, nullptr, cover_mask, m, p->precision, p->tile[dir], log, log_count, log_cap,
+                      log_stride);
 }
 
 int enzo_ghost_fill_periodic(const enzo_patch_batch *b)
@@ -381,7 +388,7 @@ int enzo_step(const enzo_patch_batch *b, const enzo_params *p, int32_t step_inde
     for (int q = 0; q < 3; ++q) {
         const int d = order[step_index & 1][q];
         const int cover = 7 & ~done & ~(1 << d);
-        r = sweep_impl(b, d, 0.0, dt_dev, cover, m, p->precision);
+        r = sweep_impl(b, d, 0.0, dt_dev, cover, m, p->precision, p->tile[d]);
         if (r) return r;
         done |= 1 << d;
     }

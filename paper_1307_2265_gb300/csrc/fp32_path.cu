@@ -37,6 +37,15 @@ static cudaError_t launch_learned_dir(const SweepArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_sweep_fp32_tiled(const SweepArgs &a, cudaStream_t s)
+{
+    switch (a.tile) {
+    case 64: return launch_tiled<float, 64>(a, s);
+    case 256: return launch_tiled<float, 256>(a, s);
+    default: return launch_tiled<float, 128>(a, s);
+    }
+}
+
 cudaError_t launch_sweep_fp32_learned(const SweepArgs &a, cudaStream_t s)
 {
     switch (a.dir) {

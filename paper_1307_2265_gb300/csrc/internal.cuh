@@ -7,7 +7,10 @@
 
 namespace enzo {
 
-constexpr int kSweepThreads = 128;     // pencils per tile (one per thread)
+constexpr int kSweepThreads = 128;     // default pencils per tile (one per thread)
+// Pencils per CTA tile a sweep may use (the autotuner picks among these); the
+// learned guess needs 128 (one tensor-core MMA row per pencil).
+__host__ __device__ constexpr bool tile_supported(int t) { return t == 64 || t == 128 || t == 256; }
 constexpr int kFillThreads = 256;      // stored cells per ghost-fill tile
 constexpr int kCflCells = 4096;        // active cells per CFL tile
 constexpr int kMaxN = 4096;            // per-axis active size limit
@@ -48,6 +51,7 @@ struct SweepArgs {
     double dt;                 // used when dt_ptr == nullptr
     const double *dt_ptr;      // device dt (enzo_step)
     MethodParams mp;
+    int tile = kSweepThreads;  // pencils per CTA tile (= threads per CTA)
     const int *prefix;         // [npatch + 1]
     unsigned *tile_counter;
     unsigned long long *status;
@@ -89,6 +93,8 @@ cudaError_t launch_sweep_fp32(const SweepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_sweep_fp32_learned(const SweepArgs &a, cudaStream_t s);
 int sweep_grid_fp64(int device);
 int sweep_grid_fp32(int device);
+// FP32 plain sweep with a chosen tile size (64, 128 or 256 pencils per CTA).
+cudaError_t launch_sweep_fp32_tiled(const SweepArgs &a, cudaStream_t s);
 
 struct CflArgs {
     const enzo_patch *patches;
@@ -118,6 +124,6 @@ void note_launch(unsigned n = 1);
 // Launch of the per-patch tile prefix kernel (kind 0: sweep pencils) on stream s.
 void launch_tile_prefix(const enzo_patch *patches, int npatch, int64_t field_len, int kind, int dir,
                         int cover, int *prefix, unsigned *counter, unsigned long long *rate_bits,
-                        unsigned long long *status, cudaStream_t s);
+                        unsigned long long *status, cudaStream_t s, int tile_pencils = kSweepThreads);
 
 }  // namespace enzo

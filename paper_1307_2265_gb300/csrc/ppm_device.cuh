@@ -860,8 +860,8 @@ __device__ __forceinline__ void warp_flush(unsigned long long *status, unsigned 
 // LEARNED: the CTA evaluates the learned Newton guess on the tensor cores at
 // every interface step, so all 128 threads march in step (threads without a
 // pencil march a stand-in copy of the tile's first pencil and write nothing).
-template <class R, int DIR, bool LEARNED>
-__global__ void __launch_bounds__(kSweepThreads, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_SWEEP_MIN_BLOCKS_FP32 : 2))
+template <class R, int DIR, bool LEARNED, int THREADS = kSweepThreads>
+__global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_SWEEP_MIN_BLOCKS_FP32 * 128 / THREADS : 2))
     ppm_sweep_kernel(const __grid_constant__ SweepArgs a)
 {
     constexpr int A1 = DIR == 0 ? 1 : 0, A2 = DIR == 2 ? 1 : 2;
@@ -890,7 +890,7 @@ __global__ void __launch_bounds__(kSweepThreads, LEARNED ? 3 : (sizeof(R) == 4 ?
         int rlo[3], rhi[3];
         sweep_ranges(P, DIR, a.cover_mask, rlo, rhi);
         const int cnt1 = rhi[A1] - rlo[A1], cnt2 = rhi[A2] - rlo[A2];
-        const int pen0 = (tile - a.prefix[lo]) * kSweepThreads;
+        const int pen0 = (tile - a.prefix[lo]) * THREADS;
         const int pen = pen0 + (int)threadIdx.x;
         const bool valid = pen < cnt1 * cnt2;
         if (!LEARNED && !valid) continue;
@@ -1037,6 +1037,33 @@ int sweep_grid_for(int device)
     if (per < 1) per = 1;
     cached[device] = sms * per;
     return cached[device];
+}
+
+template <class R, int THREADS>
+int tiled_grid(int device)
+{
+    static int cached[64] = {0};
+    if (device < 0 || device >= 64) device = 0;
+    if (cached[device]) return cached[device];
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<R, 0, false, THREADS>, THREADS, 0);
+    cached[device] = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    return cached[device];
+}
+
+template <class R, int THREADS>
+cudaError_t launch_tiled(const SweepArgs &a, cudaStream_t s)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int grid = tiled_grid<R, THREADS>(dev);
+    switch (a.dir) {
+    case 0: ppm_sweep_kernel<R, 0, false, THREADS><<<grid, THREADS, 0, s>>>(a); break;
+    case 1: ppm_sweep_kernel<R, 1, false, THREADS><<<grid, THREADS, 0, s>>>(a); break;
+    default: ppm_sweep_kernel<R, 2, false, THREADS><<<grid, THREADS, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
 }
 
 template <class R>
