@@ -87,6 +87,19 @@ typedef struct {
     double dx[3];
     int32_t level;
     int32_t flags;
+    int64_t freg_all;   /* offset of this patch's all-face flux register in the batch's
+                           freg buffer, or -1.  FP64 sweeps store the final flux of every face
+                           (FP32 sweeps the increment dt/dx F the cells applied, in FP64)
+                           bounding an active cell: for axis d (x, y, z in order) a block
+                           of (n_d+1) n_a1 n_a2 x 5 doubles at
+                           ((j2 n_a1 + j1)(n_d+1) + f) 5 + v, a1 < a2 the other axes, f the
+                           face left of active cell f, v = rho, m_normal, m_a1, m_a2, E. */
+    int64_t freg_bnd;   /* offset of the boundary-face register, or -1: sweeps ADD dt x flux
+                           (FP32 sweeps: the applied increment)
+                           of the two faces bounding the patch along d, block of 2 n_a1 n_a2
+                           x 5 doubles per axis at ((j2 n_a1 + j1) 2 + side) 5 + v.  Used by
+                           flux correction (Sec. 3.4); the caller zeroes it before a
+                           parent step's subcycles. */
 } enzo_patch;
 
 /* A batch of patches that share one timestep (a level, Sec. 3 and Sec. 9). */
@@ -102,6 +115,7 @@ typedef struct {
     size_t ws_bytes;
     unsigned long long *status;   /* DEVICE counters [ENZO_STATUS_WORDS]; added to */
     void *stream;                 /* cudaStream_t */
+    double *freg;                 /* DEVICE flux registers (see enzo_patch.freg_*), or NULL */
 } enzo_patch_batch;
 
 /* Method parameters (Sec. 4.1, 4.1.2, 9). */
@@ -261,6 +275,55 @@ int enzo_mlp_features(const float *rhoL, const float *uL, const float *pL, const
 int enzo_mlp_train_step(float *master, float *adam_m, float *adam_v, int32_t step, const float *x,
                         const float *target, int64_t n, float lr, float *grad, float *loss, void *blob,
                         unsigned long long *status, void *stream);
+
+/* ---- static AMR hierarchy (Sec. 3): ghost fill from parents and siblings,
+ * flux correction and projection.  A level is one enzo_patch_batch; every
+ * patch also has a link giving its place in the level's global index space. */
+typedef struct {
+    int32_t origin[3];  /* global index (at this level) of the first active cell */
+    int32_t parent;     /* index of the enclosing patch in the parent level, -1 for none */
+} enzo_patch_link;
+
+typedef struct {        /* a box of ghost cells of patch dst copied from sibling src */
+    int32_t dst, src;
+    int32_t lo[3], hi[3];   /* global cell box at the level, hi exclusive */
+} enzo_copy_box;
+
+typedef struct {        /* a face of a fine patch on the boundary of the refined region */
+    int32_t fine;       /* fine patch index */
+    int32_t dir;        /* axis of the face normal */
+    int32_t side;       /* 0: low face, 1: high face */
+    int32_t target;     /* coarse patch holding the coarse cells outside that face */
+} enzo_fc_face;
+
+/* SetBoundaryValues of a refined level (Sec. 3.1): every ghost cell of every
+ * patch with a parent is interpolated from the parent level by SecondOrderA
+ * (Appendix A) after linear interpolation in time, parent = parent_old +
+ * w (parent_new - parent_old); then the ghost cells listed in boxes are
+ * overwritten by copies of the siblings' active cells.  parent_old and
+ * parent_new share the parent level's descriptors (parent_new->patches) and
+ * differ in U.  Refinement factor r must be 2. */
+int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *fine_links,
+                          const enzo_patch_batch *parent_new, const enzo_patch_link *parent_links,
+                          double *const parent_old_U[5], double w, const enzo_copy_box *boxes,
+                          int32_t nbox, int32_t r);
+
+/* Flux correction (Sec. 3.4): for each listed face of a fine patch, the coarse
+ * cells just outside it get U += (dt_coarse F_coarse - mean of the fine
+ * register over the r^2 fine faces) / dx_coarse on the low side (minus on the
+ * high side).  F_coarse is read from the parent's all-face register, the fine
+ * sums from the fine patch's boundary register.  increments != 0: the registers
+ * were written by FP32-path sweeps and hold the increments the cells applied
+ * (dt/dx F), and the correction is G_coarse - mean(fine sums) / r. */
+int enzo_flux_correct(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_links,
+                      const enzo_patch_batch *fine, const enzo_patch_link *fine_links,
+                      const enzo_fc_face *faces, int32_t nface, double dt_coarse, int32_t r,
+                      int32_t increments);
+
+/* Projection (Sec. 3.3): every coarse cell covered by a fine patch becomes the
+ * mean of its r^3 fine cells (r = 2). */
+int enzo_project(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_links,
+                 const enzo_patch_batch *fine, const enzo_patch_link *fine_links, int32_t r);
 
 /* Text for an ENZO_ERR_* code (static storage). */
 const char *enzo_strerror(int code);

@@ -85,6 +85,9 @@ def lib():
             L.or_sweep.argtypes = five + [_I32, ctypes.c_int32, _D, ctypes.c_int32, ctypes.c_double,
                                           _I32, _I32, ctypes.POINTER(OrParams), ctypes.POINTER(OrStats)]
             L.or_sweep.restype = ctypes.c_int
+            L.or_sweep_fluxes.argtypes = five + [_I32, ctypes.c_int32, _D, ctypes.c_int32, ctypes.c_double,
+                                                 _I32, _I32, ctypes.POINTER(OrParams), ctypes.POINTER(OrStats), _D]
+            L.or_sweep_fluxes.restype = ctypes.c_int
             L.or_step_periodic.argtypes = five + [_I32, ctypes.c_int32, _D, ctypes.c_double,
                                                   ctypes.c_int32, ctypes.POINTER(OrParams),
                                                   ctypes.POINTER(OrStats)]
@@ -154,6 +157,26 @@ def sweep(U, dx, direction, dt, lo, hi, params: Params, ng=3) -> dict:
     if r:
         raise MemoryError("oracle sweep could not allocate pencil scratch")
     return st.as_dict()
+
+
+def sweep_fluxes(U, dx, direction, dt, lo, hi, params: Params, ng=3):
+    """As sweep(), also returning the final face fluxes of the active pencils as
+    an array [n_a2, n_a1, n_dir + 1, 5] (pencil field order rho, m_n, m_t1, m_t2, E)."""
+    n = _n_of(U, ng)
+    na, npn = _i32(n)
+    la, lp = _i32(lo)
+    ha, hp = _i32(hi)
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    a1 = 1 if direction == 0 else 0
+    a2 = 1 if direction == 2 else 2
+    F = np.zeros((n[a2], n[a1], n[direction] + 1, 5))
+    p = params.c()
+    st = OrStats()
+    r = lib().or_sweep_fluxes(*_fields(U), npn, ng, _dp(dxa), direction, dt, lp, hp, ctypes.byref(p),
+                              ctypes.byref(st), _dp(F))
+    if r:
+        raise MemoryError("oracle sweep could not allocate pencil scratch")
+    return F, st.as_dict()
 
 
 def step_periodic(U, dx, dt, step, params: Params, ng=3) -> dict:

@@ -531,9 +531,29 @@ double or_cfl_rate(const double *U0, const double *U1, const double *U2, const d
 
 /* One split sweep along axis dir over the pencils whose transverse storage
  * coordinates lie in [lo[a], hi[a]) for the two other axes a. */
+/* One split sweep along axis dir over the pencils whose transverse storage
+ * coordinates lie in [lo[a], hi[a]) for the two other axes a.  If fout is not
+ * NULL, the final face fluxes of every pencil whose transverse coordinates are
+ * active go to fout[((j2 * n[a1] + j1) * (n[dir] + 1) + f) * 5 + v], with j1, j2
+ * the active transverse indices and f the face left of active cell f (f = n[dir]
+ * is the right face of the last cell); v follows the pencil order rho, m_n,
+ * m_t1, m_t2, E. */
+int or_sweep_fluxes(double *U0, double *U1, double *U2, double *U3, double *U4,
+                    const int32_t n[3], int32_t ng, const double dx[3], int32_t dir, double dt,
+                    const int32_t lo[3], const int32_t hi[3], const or_params *P, or_stats *stats,
+                    double *fout);
+
 int or_sweep(double *U0, double *U1, double *U2, double *U3, double *U4,
              const int32_t n[3], int32_t ng, const double dx[3], int32_t dir, double dt,
              const int32_t lo[3], const int32_t hi[3], const or_params *P, or_stats *stats)
+{
+    return or_sweep_fluxes(U0, U1, U2, U3, U4, n, ng, dx, dir, dt, lo, hi, P, stats, NULL);
+}
+
+int or_sweep_fluxes(double *U0, double *U1, double *U2, double *U3, double *U4,
+                    const int32_t n[3], int32_t ng, const double dx[3], int32_t dir, double dt,
+                    const int32_t lo[3], const int32_t hi[3], const or_params *P, or_stats *stats,
+                    double *fout)
 {
     double *U[5] = { U0, U1, U2, U3, U4 };
     int N[3] = { n[0] + 2 * ng, n[1] + 2 * ng, n[2] + 2 * ng };
@@ -567,6 +587,14 @@ int or_sweep(double *U0, double *U1, double *U2, double *U3, double *U4,
             pencil_step(&pc, ng, dtdx, P, &st);
             for (int s = ng; s < L - ng; ++s)
                 for (int v = 0; v < 5; ++v) U[mi[v]][base + s * stride[dir]] = pc.U[v][s];
+            if (fout) {
+                int j1 = i1 - ng, j2 = i2 - ng;
+                if (j1 >= 0 && j1 < n[a1] && j2 >= 0 && j2 < n[a2]) {
+                    double *o = fout + ((int64_t)j2 * n[a1] + j1) * (int64_t)(n[dir] + 1) * 5;
+                    for (int f = 0; f <= n[dir]; ++f)
+                        for (int v = 0; v < 5; ++v) o[f * 5 + v] = pc.F[v][ng - 1 + f];
+                }
+            }
         }
         if (ok) free(pc.buf);
 #pragma omp critical

@@ -26,8 +26,8 @@ STATUS_NAMES = ("interfaces", "newton_iters", "newton_nonconv", "hll_cells", "ne
                 "guess_restarts", "guess_calls")
 
 PATCH_DTYPE = np.dtype([("n", "<i4", (3,)), ("ng", "<i4"), ("off", "<i8"), ("dx", "<f8", (3,)),
-                        ("level", "<i4"), ("flags", "<i4")])
-assert PATCH_DTYPE.itemsize == 56
+                        ("level", "<i4"), ("flags", "<i4"), ("freg_all", "<i8"), ("freg_bnd", "<i8")])
+assert PATCH_DTYPE.itemsize == 72
 
 
 class EnzoError(RuntimeError):
@@ -39,7 +39,7 @@ class _Batch(ctypes.Structure):
                 ("patches", ctypes.c_void_p), ("field_len", ctypes.c_int64),
                 ("U", ctypes.c_void_p * 5), ("workspace", ctypes.c_void_p),
                 ("ws_bytes", ctypes.c_size_t), ("status", ctypes.c_void_p),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("freg", ctypes.c_void_p)]
 
 
 class _Params(ctypes.Structure):
@@ -133,6 +133,8 @@ def patch_table(sizes, offsets, dx, flags=0, ng=3, level=0) -> np.ndarray:
     t["dx"] = np.broadcast_to(np.asarray(dx, dtype=np.float64), (len(sizes), 3))
     t["level"] = level
     t["flags"] = flags
+    t["freg_all"] = -1
+    t["freg_bnd"] = -1
     return t
 
 
@@ -162,6 +164,7 @@ class PatchBatch:
         self.dt_dev = torch.zeros(1, dtype=torch.float64, device=self.device)
         self.stream = stream
         self._ws_bytes = ws
+        self.freg = None
 
     def c(self) -> _Batch:
         b = _Batch()
@@ -175,6 +178,7 @@ class PatchBatch:
         b.status = self.status.data_ptr()
         s = self.stream if self.stream is not None else self.torch.cuda.current_stream(self.device)
         b.stream = s.cuda_stream
+        b.freg = self.freg.data_ptr() if self.freg is not None else None
         return b
 
     def read_status(self) -> dict:

@@ -5,6 +5,8 @@ Translation units and their flags:
   fp64_path.cu  FP64 sweep/CFL/Riemann: --fmad=false, IEEE div and sqrt
   fp32_path.cu  FP32 sweep/CFL/Riemann: -use_fast_math (FMA, fast rcp/sqrt)
   noalloc.cu    sweep entry point whose scratch is a library-owned device array
+  hierarchy.cu  ghost fill from parents/siblings, flux correction, projection (FP64,
+                --fmad=false)
   mlp.cu        learned p* guess: tcgen05 inference and training kernels
 Objects go to paper_1307_2265_gb300/_build/, the library next to this file.
 """
@@ -29,6 +31,7 @@ UNITS = {
     "fp32_path.cu": ["-use_fast_math"],
     "noalloc.cu": [],
     "mlp.cu": ["-use_fast_math"],
+    "hierarchy.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
 }
 OPTIONAL_UNITS = {}
 

@@ -202,7 +202,7 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
 {
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
     int tile = tile_pencils > 0 ? tile_pencils : kSweepThreads;
-    if (precision == ENZO_FP64 || m.guess == ENZO_GUESS_MLP) tile = kSweepThreads;
+    if (precision == ENZO_FP64 || m.guess == ENZO_GUESS_MLP || b->freg) tile = kSweepThreads;
     int r = launch_prefix(b, kKindSweep, dir, cover, false, s, tile);
     if (r) return r;
     SweepArgs a;
@@ -219,6 +219,7 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
     a.prefix = reinterpret_cast<const int *>(ws(b) + kWsPrefix);
     a.tile_counter = reinterpret_cast<unsigned *>(ws(b) + kWsCounter);
     a.status = b->status;
+    a.freg = b->freg;
     a.log = log;
     a.log_count = log_count;
     a.log_cap = log_cap;

@@ -14,7 +14,7 @@ int sweep_grid_fp32(int device) { return sweep_grid_for<float>(device); }
 
 // Sweep with the learned Newton guess (tensor cores inside the sweep).  TMEM
 // holds 128 columns per CTA, so at most 4 CTAs share an SM.
-template <int DIR>
+template <int DIR, bool REG>
 static cudaError_t launch_learned_dir(const SweepArgs &a, cudaStream_t s)
 {
     static int grid[64] = {0};
@@ -23,17 +23,18 @@ static cudaError_t launch_learned_dir(const SweepArgs &a, cudaStream_t s)
     if (dev < 0 || dev >= 64) dev = 0;
     const size_t smem = sizeof(GuessSmem) + 1024;
     if (!grid[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(ppm_sweep_kernel<float, DIR, true>,
+        cudaError_t e = cudaFuncSetAttribute(ppm_sweep_kernel<float, DIR, true, kSweepThreads, REG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        int sms = 0, per = 0;
+        // 3 CTAs per SM: the launch bounds cap registers for 3, TMEM holds
+        // 4 x 128 columns and shared memory 6 x GuessSmem.  (The occupancy
+        // query reported 1 here; a CTA that cannot be resident yet only starts
+        // later and finds fewer tiles, since tiles come from a counter.)
+        int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<float, DIR, true>, kSweepThreads, smem);
-        if (per > 4) per = 4;
-        if (per < 1) per = 1;
-        grid[dev] = (sms > 0 ? sms : 1) * per;
+        grid[dev] = (sms > 0 ? sms : 1) * 3;
     }
-    ppm_sweep_kernel<float, DIR, true><<<grid[dev], kSweepThreads, smem, s>>>(a);
+    ppm_sweep_kernel<float, DIR, true, kSweepThreads, REG><<<grid[dev], kSweepThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -48,10 +49,17 @@ cudaError_t launch_sweep_fp32_tiled(const SweepArgs &a, cudaStream_t s)
 
 cudaError_t launch_sweep_fp32_learned(const SweepArgs &a, cudaStream_t s)
 {
+    if (a.freg) {
+        switch (a.dir) {
+        case 0: return launch_learned_dir<0, true>(a, s);
+        case 1: return launch_learned_dir<1, true>(a, s);
+        default: return launch_learned_dir<2, true>(a, s);
+        }
+    }
     switch (a.dir) {
-    case 0: return launch_learned_dir<0>(a, s);
-    case 1: return launch_learned_dir<1>(a, s);
-    default: return launch_learned_dir<2>(a, s);
+    case 0: return launch_learned_dir<0, false>(a, s);
+    case 1: return launch_learned_dir<1, false>(a, s);
+    default: return launch_learned_dir<2, false>(a, s);
     }
 }
 

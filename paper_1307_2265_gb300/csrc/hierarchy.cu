@@ -1,0 +1,403 @@
+// Static AMR hierarchy operations around the sweep (paper Sec. 3):
+//   ghost fill of refined levels (parent interpolation by SecondOrderA,
+//   Appendix A, after linear interpolation in time; then sibling copies),
+//   flux correction at coarse-fine faces (Sec. 3.4) and projection (Sec. 3.3).
+// FP64 throughout; built with --fmad=false so every operation rounds once in
+// the order written.
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace enzo {
+
+constexpr double kEps = 1e-300;
+
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    const double aa = fabs(a), ab = fabs(b);
+    const double m = aa < ab ? aa : ab;
+    const double out = a > 0.0 ? m : (a < 0.0 ? -m : 0.0);
+    return a * b < 0.0 ? 0.0 : out;
+}
+
+// SecondOrderA value of child (kz, ky, kx) of the centre of a 3x3x3 parent
+// neighbourhood Q[z][y][x] (r = 2).
+__device__ double second_order_a(const double Q[3][3][3], int kz, int ky, int kx)
+{
+    const double Q0 = Q[1][1][1];
+    double C[2][2][2];
+    for (int sz = 0; sz < 2; ++sz)
+        for (int sy = 0; sy < 2; ++sy)
+            for (int sx = 0; sx < 2; ++sx) {
+                double acc = 0.0;
+                for (int dz = 0; dz < 2; ++dz)
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) acc = acc + Q[sz + dz][sy + dy][sx + dx];
+                C[sz][sy][sx] = acc * 0.125;
+            }
+    // diagonals: plus corners (z,y,x) = (1,1,1), (1,1,0), (1,0,1), (0,1,1)
+    const double d0 = minmod(C[1][1][1] - Q0, Q0 - C[0][0][0]);
+    const double d1 = minmod(C[1][1][0] - Q0, Q0 - C[0][0][1]);
+    const double d2 = minmod(C[1][0][1] - Q0, Q0 - C[0][1][0]);
+    const double d3 = minmod(C[0][1][1] - Q0, Q0 - C[1][0][0]);
+    double a1 = d1, a2 = d2, a3 = d3;
+    if (d0 == 0.0) {
+        a1 = a2 = a3 = 0.0;
+    } else {
+        const double s = ((d1 + d2) + d3) / d0;
+        if (s < 0.0 || s > 1.0) {
+            const double sp = s < 0.0 ? 0.0 : 1.0;
+            const double c1 = s < 0.0 ? (d1 / d0 < 0.0 ? 1.0 : 0.0) : (d1 / d0 > 0.0 ? 1.0 : 0.0);
+            const double c2 = s < 0.0 ? (d2 / d0 < 0.0 ? 1.0 : 0.0) : (d2 / d0 > 0.0 ? 1.0 : 0.0);
+            const double c3 = s < 0.0 ? (d3 / d0 < 0.0 ? 1.0 : 0.0) : (d3 / d0 > 0.0 ? 1.0 : 0.0);
+            const double num = sp * d0 - (((1.0 - c1) * d1 + (1.0 - c2) * d2) + (1.0 - c3) * d3);
+            const double den = ((c1 * d1 + c2 * d2) + c3 * d3) + kEps;
+            const double f = num / den;
+            a1 = f * c1 * d1 + (1.0 - c1) * d1;
+            a2 = f * c2 * d2 + (1.0 - c2) * d2;
+            a3 = f * c3 * d3 + (1.0 - c3) * d3;
+        }
+    }
+    const double fx = a2 + a3, fy = a1 + a3, fz = a1 + a2;
+    const double cx = kx ? 0.25 : -0.25, cy = ky ? 0.25 : -0.25, cz = kz ? 0.25 : -0.25;
+    return ((Q0 + cx * fx) + cy * fy) + cz * fz;
+}
+
+__device__ __forceinline__ int floordiv2(int g) { return g >= 0 ? g / 2 : -((1 - g) / 2); }
+
+struct InterpArgs {
+    const enzo_patch *fine;
+    const enzo_patch_link *flink;
+    int nfine;
+    double *U[5];
+    const enzo_patch *par;
+    const enzo_patch_link *plink;
+    const double *Pn[5];
+    const double *Po[5];
+    double w;
+    const int *prefix;
+};
+
+// Every ghost cell of every fine patch with a parent.
+__global__ void __launch_bounds__(256) interp_ghosts_kernel(const __grid_constant__ InterpArgs a)
+{
+    const int total = a.prefix[a.nfine];
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        int lo = 0, hi = a.nfine;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.prefix[mid] <= tile) lo = mid; else hi = mid;
+        }
+        const enzo_patch P = a.fine[lo];
+        const enzo_patch_link L = a.flink[lo];
+        if (L.parent < 0) continue;
+        const int N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng, N2 = P.n[2] + 2 * P.ng;
+        const int64_t cell = (int64_t)(tile - a.prefix[lo]) * 256 + threadIdx.x;
+        if (cell >= (int64_t)N0 * N1 * N2) continue;
+        const int s[3] = {(int)(cell % N0), (int)((cell / N0) % N1), (int)(cell / ((int64_t)N0 * N1))};
+        bool ghost = false;
+        for (int d = 0; d < 3; ++d)
+            if (s[d] < P.ng || s[d] >= P.ng + P.n[d]) ghost = true;
+        if (!ghost) continue;
+        const enzo_patch PP = a.par[L.parent];
+        const enzo_patch_link PL = a.plink[L.parent];
+        int G[3], kid[3], ps[3];
+        for (int d = 0; d < 3; ++d) {
+            const int g = L.origin[d] + s[d] - P.ng;
+            G[d] = floordiv2(g);
+            kid[d] = g - 2 * G[d];
+            ps[d] = G[d] - PL.origin[d] + PP.ng;
+        }
+        const int M0 = PP.n[0] + 2 * PP.ng, M1 = PP.n[1] + 2 * PP.ng;
+        const int64_t dst = P.off + cell;
+        for (int f = 0; f < 5; ++f) {
+            double Q[3][3][3];
+            for (int dz = 0; dz < 3; ++dz)
+                for (int dy = 0; dy < 3; ++dy)
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int64_t idx = PP.off + (ps[0] - 1 + dx) +
+                                            (int64_t)M0 * ((ps[1] - 1 + dy) + (int64_t)M1 * (ps[2] - 1 + dz));
+                        const double o = a.Po[f][idx], n = a.Pn[f][idx];
+                        Q[dz][dy][dx] = o + a.w * (n - o);
+                    }
+            a.U[f][dst] = second_order_a(Q, kid[2], kid[1], kid[0]);
+        }
+    }
+}
+
+// Ghost boxes copied from siblings (one CTA per box).
+__global__ void __launch_bounds__(256) copy_boxes_kernel(const enzo_patch *pt, const enzo_patch_link *lk,
+                                                         double *U0, double *U1, double *U2, double *U3,
+                                                         double *U4, const enzo_copy_box *boxes, int nbox)
+{
+    for (int bi = blockIdx.x; bi < nbox; bi += gridDim.x) {
+        const enzo_copy_box B = boxes[bi];
+        const enzo_patch D = pt[B.dst], S = pt[B.src];
+        const enzo_patch_link DL = lk[B.dst], SL = lk[B.src];
+        const int e0 = B.hi[0] - B.lo[0], e1 = B.hi[1] - B.lo[1], e2 = B.hi[2] - B.lo[2];
+        const int64_t vol = (int64_t)e0 * e1 * e2;
+        const int D0 = D.n[0] + 2 * D.ng, D1 = D.n[1] + 2 * D.ng;
+        const int S0 = S.n[0] + 2 * S.ng, S1 = S.n[1] + 2 * S.ng;
+        for (int64_t c = threadIdx.x; c < vol; c += blockDim.x) {
+            const int x = B.lo[0] + (int)(c % e0);
+            const int y = B.lo[1] + (int)((c / e0) % e1);
+            const int z = B.lo[2] + (int)(c / ((int64_t)e0 * e1));
+            const int64_t di = D.off + (x - DL.origin[0] + D.ng) +
+                               (int64_t)D0 * ((y - DL.origin[1] + D.ng) + (int64_t)D1 * (z - DL.origin[2] + D.ng));
+            const int64_t si = S.off + (x - SL.origin[0] + S.ng) +
+                               (int64_t)S0 * ((y - SL.origin[1] + S.ng) + (int64_t)S1 * (z - SL.origin[2] + S.ng));
+            U0[di] = U0[si];
+            U1[di] = U1[si];
+            U2[di] = U2[si];
+            U3[di] = U3[si];
+            U4[di] = U4[si];
+        }
+    }
+}
+
+struct FcArgs {
+    const enzo_patch *cp;
+    const enzo_patch_link *cl;
+    double *U[5];
+    const double *cfreg;
+    const enzo_patch *fp;
+    const enzo_patch_link *fl;
+    const double *ffreg;
+    const enzo_fc_face *faces;
+    int nface;
+    double dt_c;
+    int increments;
+};
+
+__device__ __forceinline__ int64_t reg_all_block(const enzo_patch &P, int dir)
+{
+    int64_t o = 0;
+    for (int d = 0; d < dir; ++d) {
+        const int b1 = d == 0 ? 1 : 0, b2 = d == 2 ? 1 : 2;
+        o += (int64_t)(P.n[d] + 1) * P.n[b1] * P.n[b2] * 5;
+    }
+    return o;
+}
+__device__ __forceinline__ int64_t reg_bnd_block(const enzo_patch &P, int dir)
+{
+    int64_t o = 0;
+    for (int d = 0; d < dir; ++d) {
+        const int b1 = d == 0 ? 1 : 0, b2 = d == 2 ? 1 : 2;
+        o += (int64_t)2 * P.n[b1] * P.n[b2] * 5;
+    }
+    return o;
+}
+
+// One CTA per listed fine face; threads over the coarse faces it covers.
+__global__ void __launch_bounds__(128) flux_correct_kernel(const __grid_constant__ FcArgs a)
+{
+    for (int fi = blockIdx.x; fi < a.nface; fi += gridDim.x) {
+        const enzo_fc_face F = a.faces[fi];
+        const enzo_patch FP = a.fp[F.fine];
+        const enzo_patch_link FL = a.fl[F.fine];
+        const enzo_patch PP = a.cp[FL.parent];
+        const enzo_patch_link PL = a.cl[FL.parent];
+        const enzo_patch TP = a.cp[F.target];
+        const enzo_patch_link TL = a.cl[F.target];
+        const int d = F.dir, a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+        const int X = (FL.origin[d] + (F.side ? FP.n[d] : 0)) / 2;
+        const int cell = F.side ? X : X - 1;
+        const int fc = X - PL.origin[d];
+        const int m1 = FP.n[a1] / 2, m2 = FP.n[a2] / 2;
+        const double inv_dx = 1.0 / TP.dx[d];
+        const double *creg = a.cfreg + PP.freg_all + reg_all_block(PP, d);
+        const double *freg = a.ffreg + FP.freg_bnd + reg_bnd_block(FP, d);
+        const int fna1 = FP.n[a1];
+        const int T0 = TP.n[0] + 2 * TP.ng, T1 = TP.n[1] + 2 * TP.ng;
+        const int map[5] = {0, 1 + d, 1 + a1, 1 + a2, 4};
+        for (int q = threadIdx.x; q < m1 * m2; q += blockDim.x) {
+            const int q1 = q % m1, q2 = q / m1;
+            const int c1 = FL.origin[a1] / 2 + q1, c2 = FL.origin[a2] / 2 + q2;
+            const double *cf = creg + (((int64_t)(c2 - PL.origin[a2]) * PP.n[a1] + (c1 - PL.origin[a1])) *
+                                           (PP.n[d] + 1) + fc) * 5;
+            const double *f00 = freg + (((int64_t)(2 * q2) * fna1 + 2 * q1) * 2 + F.side) * 5;
+            const double *f01 = freg + (((int64_t)(2 * q2) * fna1 + 2 * q1 + 1) * 2 + F.side) * 5;
+            const double *f10 = freg + (((int64_t)(2 * q2 + 1) * fna1 + 2 * q1) * 2 + F.side) * 5;
+            const double *f11 = freg + (((int64_t)(2 * q2 + 1) * fna1 + 2 * q1 + 1) * 2 + F.side) * 5;
+            int g[3];
+            g[d] = cell;
+            g[a1] = c1;
+            g[a2] = c2;
+            const int64_t idx = TP.off + (g[0] - TL.origin[0] + TP.ng) +
+                                (int64_t)T0 * ((g[1] - TL.origin[1] + TP.ng) + (int64_t)T1 * (g[2] - TL.origin[2] + TP.ng));
+            for (int v = 0; v < 5; ++v) {
+                double delta;
+                if (a.increments) {
+                    // registers hold applied increments (U units): the fine ones
+                    // carry a factor dx_f / dx_c = 1/2 and the 4 faces a mean
+                    delta = cf[v] - (((f00[v] + f01[v]) + f10[v]) + f11[v]) * 0.125;
+                } else {
+                    const double fine = (((f00[v] + f01[v]) + f10[v]) + f11[v]) * 0.25;
+                    delta = (a.dt_c * cf[v] - fine) / TP.dx[d];
+                }
+                atomicAdd(&a.U[map[v]][idx], F.side ? -delta : delta);
+            }
+            (void)inv_dx;
+        }
+    }
+}
+
+struct ProjArgs {
+    const enzo_patch *cp;
+    const enzo_patch_link *cl;
+    double *U[5];
+    const enzo_patch *fp;
+    const enzo_patch_link *fl;
+    const double *F[5];
+    int nfine;
+};
+
+__global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ ProjArgs a)
+{
+    for (int pi = blockIdx.x; pi < a.nfine; pi += gridDim.x) {
+        const enzo_patch FP = a.fp[pi];
+        const enzo_patch_link FL = a.fl[pi];
+        if (FL.parent < 0) continue;
+        const enzo_patch PP = a.cp[FL.parent];
+        const enzo_patch_link PL = a.cl[FL.parent];
+        const int m0 = FP.n[0] / 2, m1 = FP.n[1] / 2, m2 = FP.n[2] / 2;
+        const int F0 = FP.n[0] + 2 * FP.ng, F1 = FP.n[1] + 2 * FP.ng;
+        const int P0 = PP.n[0] + 2 * PP.ng, P1 = PP.n[1] + 2 * PP.ng;
+        const int64_t vol = (int64_t)m0 * m1 * m2;
+        for (int64_t c = threadIdx.x; c < vol; c += blockDim.x) {
+            const int x = (int)(c % m0), y = (int)((c / m0) % m1), z = (int)(c / ((int64_t)m0 * m1));
+            const int64_t pidx = PP.off + (FL.origin[0] / 2 + x - PL.origin[0] + PP.ng) +
+                                 (int64_t)P0 * ((FL.origin[1] / 2 + y - PL.origin[1] + PP.ng) +
+                                                (int64_t)P1 * (FL.origin[2] / 2 + z - PL.origin[2] + PP.ng));
+            for (int f = 0; f < 5; ++f) {
+                double s = 0.0;
+                for (int kz = 0; kz < 2; ++kz)
+                    for (int ky = 0; ky < 2; ++ky)
+                        for (int kx = 0; kx < 2; ++kx) {
+                            const int64_t fidx = FP.off + (2 * x + kx + FP.ng) +
+                                                 (int64_t)F0 * ((2 * y + ky + FP.ng) + (int64_t)F1 * (2 * z + kz + FP.ng));
+                            s = s + a.F[f][fidx];
+                        }
+                a.U[f][pidx] = s * 0.125;
+            }
+        }
+    }
+}
+
+static int sm_count()
+{
+    int dev = 0, s = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    return s > 0 ? s : 1;
+}
+
+static bool batch_ok(const enzo_patch_batch *b)
+{
+    if (!b || b->npatch < 0) return false;
+    if (b->npatch == 0) return true;
+    if (!b->patches) return false;
+    for (int f = 0; f < 5; ++f)
+        if (!b->U[f]) return false;
+    return true;
+}
+
+}  // namespace enzo
+
+using namespace enzo;
+
+extern "C" {
+
+int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *fine_links,
+                          const enzo_patch_batch *parent_new, const enzo_patch_link *parent_links,
+                          double *const parent_old_U[5], double w, const enzo_copy_box *boxes, int32_t nbox,
+                          int32_t r)
+{
+    if (r != 2 || !batch_ok(fine) || !batch_ok(parent_new) || !fine_links || !parent_links || !parent_old_U)
+        return ENZO_ERR_ARG;
+    if (!(w >= 0.0) || !(w <= 1.0) || nbox < 0 || (nbox > 0 && !boxes)) return ENZO_ERR_ARG;
+    if (fine->npatch == 0) return ENZO_OK;
+    if (!fine->workspace || fine->ws_bytes < enzo_workspace_size(fine->npatch) || !fine->status)
+        return ENZO_ERR_WORKSPACE;
+    for (int f = 0; f < 5; ++f)
+        if (!parent_old_U[f]) return ENZO_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(fine->stream);
+    char *ws = static_cast<char *>(fine->workspace);
+    // tiles of 256 stored cells per patch (kind 1 = ghost-fill tiles)
+    launch_tile_prefix(fine->patches, fine->npatch, fine->field_len, 1, 0, 0,
+                       reinterpret_cast<int *>(ws + kWsPrefix), reinterpret_cast<unsigned *>(ws + kWsCounter),
+                       nullptr, fine->status, s);
+    note_launch();
+    InterpArgs a;
+    a.fine = fine->patches;
+    a.flink = fine_links;
+    a.nfine = fine->npatch;
+    for (int f = 0; f < 5; ++f) {
+        a.U[f] = fine->U[f];
+        a.Pn[f] = parent_new->U[f];
+        a.Po[f] = parent_old_U[f];
+    }
+    a.par = parent_new->patches;
+    a.plink = parent_links;
+    a.w = w;
+    a.prefix = reinterpret_cast<const int *>(ws + kWsPrefix);
+    interp_ghosts_kernel<<<sm_count() * 8, 256, 0, s>>>(a);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
+    if (nbox > 0) {
+        copy_boxes_kernel<<<nbox < sm_count() * 16 ? nbox : sm_count() * 16, 256, 0, s>>>(
+            fine->patches, fine_links, fine->U[0], fine->U[1], fine->U[2], fine->U[3], fine->U[4], boxes, nbox);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
+    }
+    return ENZO_OK;
+}
+
+int enzo_flux_correct(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_links,
+                      const enzo_patch_batch *fine, const enzo_patch_link *fine_links, const enzo_fc_face *faces,
+                      int32_t nface, double dt_coarse, int32_t r, int32_t increments)
+{
+    if (r != 2 || !batch_ok(coarse) || !batch_ok(fine) || !coarse_links || !fine_links) return ENZO_ERR_ARG;
+    if (nface < 0 || (nface > 0 && !faces) || !(dt_coarse >= 0.0)) return ENZO_ERR_ARG;
+    if (nface == 0) return ENZO_OK;
+    if (!coarse->freg || !fine->freg) return ENZO_ERR_ARG;
+    FcArgs a;
+    a.cp = coarse->patches;
+    a.cl = coarse_links;
+    for (int f = 0; f < 5; ++f) a.U[f] = coarse->U[f];
+    a.cfreg = coarse->freg;
+    a.fp = fine->patches;
+    a.fl = fine_links;
+    a.ffreg = fine->freg;
+    a.faces = faces;
+    a.nface = nface;
+    a.dt_c = dt_coarse;
+    a.increments = increments ? 1 : 0;
+    flux_correct_kernel<<<nface < sm_count() * 16 ? nface : sm_count() * 16, 128, 0,
+                          static_cast<cudaStream_t>(coarse->stream)>>>(a);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
+}
+
+int enzo_project(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_links, const enzo_patch_batch *fine,
+                 const enzo_patch_link *fine_links, int32_t r)
+{
+    if (r != 2 || !batch_ok(coarse) || !batch_ok(fine) || !coarse_links || !fine_links) return ENZO_ERR_ARG;
+    if (fine->npatch == 0) return ENZO_OK;
+    ProjArgs a;
+    a.cp = coarse->patches;
+    a.cl = coarse_links;
+    for (int f = 0; f < 5; ++f) {
+        a.U[f] = coarse->U[f];
+        a.F[f] = fine->U[f];
+    }
+    a.fp = fine->patches;
+    a.fl = fine_links;
+    a.nfine = fine->npatch;
+    project_kernel<<<fine->npatch < sm_count() * 16 ? fine->npatch : sm_count() * 16, 256, 0,
+                     static_cast<cudaStream_t>(coarse->stream)>>>(a);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -62,6 +62,7 @@ struct SweepArgs {
     unsigned long long *log_count = nullptr;
     long long log_cap = 0;
     int log_stride = 0;
+    double *freg = nullptr;    // flux registers (enzo_patch.freg_all / freg_bnd)
 };
 
 // Tiles of a sweep along dir for one patch: ceil(pencils / kSweepThreads).

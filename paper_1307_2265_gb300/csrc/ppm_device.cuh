@@ -646,7 +646,7 @@ struct LearnedGuess {
     }
 };
 
-template <class R, bool WRAP, int DIR>
+template <class R, bool WRAP, int DIR, bool REG = false>
 struct Marcher {
     static constexpr int A1 = DIR == 0 ? 1 : 0;
     static constexpr int A2 = DIR == 2 ? 1 : 2;
@@ -655,6 +655,9 @@ struct Marcher {
     Consts<R> k;
     bool active;          // false: a stand-in pencil that only keeps the CTA in step
     unsigned log_key;     // pencil identity for the interface-state log
+    double *reg_all;      // this pencil's all-face flux register row, or nullptr
+    double *reg_bnd;      // this pencil's boundary-face register pair, or nullptr
+    double dt64;
     Zone<R> c0, c1, c2;   // WRAP: initial state of the first three active cells
 
     __device__ __forceinline__ const double *F(int f) const { return a.U[f]; }
@@ -720,6 +723,23 @@ struct Marcher {
         float *o = a.log + 6 * slot;
         o[0] = (float)sl[0]; o[1] = (float)sl[1]; o[2] = (float)sl[2];
         o[3] = (float)sr[0]; o[4] = (float)sr[1]; o[5] = (float)sr[2];
+    }
+
+    // Flux register entries of face f (left of active cell f; f = n is the
+    // right face of the last cell) once its final flux is known.  FP64 path:
+    // the flux F (all faces) and dt F summed over steps (boundary faces).  FP32
+    // path: the increment G = dt/dx F exactly as the cells applied it, and its
+    // sum, so a flux correction cancels the applied coarse increment exactly.
+    __device__ __forceinline__ void record(int f, const R Fv[5], const double G[5])
+    {
+        if (!REG) return;
+        if (reg_all) {
+            _Pragma("unroll") for (int v = 0; v < 5; ++v) reg_all[f * 5 + v] = sizeof(R) == 8 ? (double)Fv[v] : G[v];
+        }
+        if (reg_bnd && (f == 0 || f == pc.n)) {
+            double *o = reg_bnd + (f == 0 ? 0 : 5);
+            _Pragma("unroll") for (int v = 0; v < 5; ++v) o[v] = o[v] + (sizeof(R) == 8 ? dt64 * (double)Fv[v] : G[v]);
+        }
     }
 
     template <class GS>
@@ -814,6 +834,7 @@ struct Marcher {
                             }
                             double G1[5];
                             widen(Fu1, dtdx, G1);
+                            record(kk - 6, Fu1, G1);
                             if (kk >= 7) update(kk - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt);
                             _Pragma("unroll") for (int v = 0; v < 5; ++v)
                             {
@@ -842,6 +863,7 @@ struct Marcher {
         }
         double G1[5];
         widen(Fu1, dtdx, G1);
+        record(pc.n, Fu1, G1);
         update(L - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt);
     }
 };
@@ -860,7 +882,9 @@ __device__ __forceinline__ void warp_flush(unsigned long long *status, unsigned 
 // LEARNED: the CTA evaluates the learned Newton guess on the tensor cores at
 // every interface step, so all 128 threads march in step (threads without a
 // pencil march a stand-in copy of the tile's first pencil and write nothing).
-template <class R, int DIR, bool LEARNED, int THREADS = kSweepThreads>
+// REG: the batch has flux registers (hierarchy levels); the per-pencil register
+// rows are then tracked, otherwise the recording compiles away.
+template <class R, int DIR, bool LEARNED, int THREADS = kSweepThreads, bool REG = false>
 __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_SWEEP_MIN_BLOCKS_FP32 * 128 / THREADS : 2))
     ppm_sweep_kernel(const __grid_constant__ SweepArgs a)
 {
@@ -908,11 +932,28 @@ __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_
         const R dtdx = (R)dtdx64;
         if (valid) interfaces += (unsigned long long)(P.n[DIR] + 1);
         const unsigned key = (unsigned)lo * 7919u + (unsigned)pe;
+        // flux register rows of this pencil (active transverse position only)
+        double *reg_all = nullptr, *reg_bnd = nullptr;
+        if (REG) {
+            const int j1 = i1 - P.ng, j2 = i2 - P.ng;
+            const int na1 = P.n[A1], na2 = P.n[A2];
+            if (a.freg && valid && j1 >= 0 && j1 < na1 && j2 >= 0 && j2 < na2) {
+                int64_t oall = 0, obnd = 0;
+                for (int d = 0; d < DIR; ++d) {
+                    const int b1 = d == 0 ? 1 : 0, b2 = d == 2 ? 1 : 2;
+                    oall += (int64_t)(P.n[d] + 1) * P.n[b1] * P.n[b2] * 5;
+                    obnd += (int64_t)2 * P.n[b1] * P.n[b2] * 5;
+                }
+                const int64_t row = (int64_t)j2 * na1 + j1;
+                if (P.freg_all >= 0) reg_all = a.freg + P.freg_all + oall + row * (P.n[DIR] + 1) * 5;
+                if (P.freg_bnd >= 0) reg_bnd = a.freg + P.freg_bnd + obnd + row * 2 * 5;
+            }
+        }
         if (P.flags & ENZO_PATCH_PERIODIC) {
-            Marcher<R, true, DIR> m{a, pc, k, valid, key};
+            Marcher<R, true, DIR, REG> m{a, pc, k, valid, key, reg_all, reg_bnd, dt};
             m.run(dtdx, dtdx64, a.mp, cnt, guess);
         } else {
-            Marcher<R, false, DIR> m{a, pc, k, valid, key};
+            Marcher<R, false, DIR, REG> m{a, pc, k, valid, key, reg_all, reg_bnd, dt};
             m.run(dtdx, dtdx64, a.mp, cnt, guess);
         }
     }
@@ -1069,6 +1110,14 @@ cudaError_t launch_tiled(const SweepArgs &a, cudaStream_t s)
 template <class R>
 cudaError_t launch_sweep_dir(const SweepArgs &a, int grid, cudaStream_t s)
 {
+    if (a.freg) {
+        switch (a.dir) {
+        case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+        case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+        default: ppm_sweep_kernel<R, 2, false, kSweepThreads, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+        }
+        return cudaGetLastError();
+    }
     switch (a.dir) {
     case 0: ppm_sweep_kernel<R, 0, false><<<grid, kSweepThreads, 0, s>>>(a); break;
     case 1: ppm_sweep_kernel<R, 1, false><<<grid, kSweepThreads, 0, s>>>(a); break;

@@ -167,3 +167,118 @@ def riemann_states(rng, n, log_rho_sd=1.0, mach=1.0, log_p_sd=1.0, gamma=5.0 / 3
     ul = rng.normal(0, mach, n) * cl
     ur = rng.normal(0, mach, n) * cr
     return rl, ul, pl, rr, ur, pr
+
+
+# ---------------------------------------------------------------------------
+# static refinement hierarchies (geometry only)
+# ---------------------------------------------------------------------------
+def _compose(length, sizes, rng):
+    """Random split of `length` into parts drawn from `sizes` (all even)."""
+    sizes = sorted(sizes)
+    parts = []
+    left = length
+    while left > 0:
+        opts = [s for s in sizes if s == left or (left - s) >= sizes[0]]
+        opts = [s for s in opts if _composable(left - s, sizes)]
+        if not opts:
+            raise ValueError(f"cannot split {length} into {sizes}")
+        s = int(rng.choice(opts))
+        parts.append(s)
+        left -= s
+    return parts
+
+
+def _composable(n, sizes):
+    ok = [False] * (n + 1)
+    ok[0] = True
+    for v in range(1, n + 1):
+        ok[v] = any(v >= s and ok[v - s] for s in sizes)
+    return ok[n]
+
+
+def hierarchy_layout(root_n, regions, sizes, seed=0, r=2):
+    """Static nested refinement: level 0 is one root patch of root_n^3 cells;
+    level l >= 1 covers the box [a_l, b_l)^3 of root cells, tiled by the tensor
+    product of per-axis cuts with part lengths from `sizes`.  Every level-(l+1)
+    patch lies inside one level-l patch (its parent), and patch edges sit on
+    parent cell boundaries (all sizes even).
+
+    regions: [(a_1, b_1), (a_2, b_2), ...] in root cells, nested.
+    Returns a list of levels, each {"n": int array [P, 3] (nx, ny, nz),
+    "origin": int array [P, 3] (global index of the first active cell at that
+    level), "parent": int array [P] (-1 for the root), "cuts": per-axis segment
+    lists}.
+    """
+    rng = np.random.default_rng(SEED_BASE + 500 + seed)
+    levels = [{"n": np.array([[root_n] * 3]), "origin": np.zeros((1, 3), dtype=np.int64),
+               "parent": np.array([-1]), "segs": [[(0, root_n)]] * 3}]
+    for l, (a, b) in enumerate(regions, start=1):
+        scale = r ** l
+        lo, hi = a * scale, b * scale
+        # breakpoints: the parent level's cut positions inside the region (doubled)
+        # and the boundaries of every deeper region at this level
+        deeper = [(aa * scale, bb * scale) for (aa, bb) in regions[l:]]
+        segs_axes = []
+        for ax in range(3):
+            parent_cuts = sorted({x * r for seg in levels[l - 1]["segs"][ax] for x in seg})
+            bps = {lo, hi} | {x for x in parent_cuts if lo < x < hi}
+            for (dl, dh) in deeper:
+                bps |= {dl, dh}
+            bps = sorted(x for x in bps if lo <= x <= hi)
+            segs = []
+            for s0, s1 in zip(bps[:-1], bps[1:]):
+                x = s0
+                for part in _compose(s1 - s0, sizes, rng):
+                    segs.append((x, x + part))
+                    x += part
+            segs_axes.append(segs)
+        ns, origins, parents = [], [], []
+        prev = levels[l - 1]
+        for sz in segs_axes[2]:
+            for sy in segs_axes[1]:
+                for sx in segs_axes[0]:
+                    o = np.array([sx[0], sy[0], sz[0]])
+                    n = np.array([sx[1] - sx[0], sy[1] - sy[0], sz[1] - sz[0]])
+                    # parent: the level-(l-1) patch whose active box contains this one
+                    po, pn = prev["origin"], prev["n"]
+                    inside = np.all((po * r <= o) & (o + n <= (po + pn) * r), axis=1)
+                    idx = np.nonzero(inside)[0]
+                    if len(idx) != 1:
+                        raise ValueError("patch not enclosed by exactly one parent")
+                    ns.append(n)
+                    origins.append(o)
+                    parents.append(int(idx[0]))
+        levels.append({"n": np.array(ns), "origin": np.array(origins, dtype=np.int64),
+                       "parent": np.array(parents), "segs": segs_axes})
+    return levels
+
+
+def hierarchy_fields(layout, config=5, gamma=5.0 / 3.0, ng=NG):
+    """White-noise initial state on the root (rms Mach 1, lognormal rho); finer
+    levels start from their parent's values (each fine cell takes its parent
+    cell's conserved state).  Returns per level a list of per-patch field lists."""
+    root = single_grid(tuple(int(v) for v in layout[0]["n"][0]), "white", config=config, gamma=gamma, ng=ng)
+    out = [[root]]
+    for l in range(1, len(layout)):
+        L = layout[l]
+        prev = layout[l - 1]
+        fields = []
+        for i in range(len(L["n"])):
+            nx, ny, nz = (int(v) for v in L["n"][i])
+            o = L["origin"][i]
+            p = int(L["parent"][i])
+            po = prev["origin"][p]
+            PU = out[l - 1][p]
+            gz = np.arange(nz) + o[2]
+            gy = np.arange(ny) + o[1]
+            gx = np.arange(nx) + o[0]
+            iz = gz // 2 - po[2] + ng
+            iy = gy // 2 - po[1] + ng
+            ix = gx // 2 - po[0] + ng
+            fl = []
+            for f in range(5):
+                act = PU[f][np.ix_(iz, iy, ix)]
+                fl.append(embed(act, ng))
+            fields.append(fl)
+        out.append(fields)
+    return out

@@ -66,6 +66,7 @@ def test_null_and_bad_arguments_rejected_without_gpu():
 def test_validate_patches_ranges():
     L = ez.lib()
     t = ez.patch_table([(8, 9, 10), (1, 1, 1)], [0, 14 * 15 * 16], [0.1, 0.1, 0.1])
+    assert t["freg_all"][0] == -1 and t["freg_bnd"][1] == -1
     total = 14 * 15 * 16 + 7 * 7 * 7
     bad = ctypes.c_int32(0)
     assert L.enzo_validate_patches(t.ctypes.data, 2, total, ctypes.byref(bad)) == 0 and bad.value == -1
@@ -80,5 +81,5 @@ def test_validate_patches_ranges():
 
 
 def test_patch_struct_layout_matches_header():
-    assert ez.PATCH_DTYPE.itemsize == 56
-    assert ctypes.sizeof(ez._Batch) == 4 + 4 + 8 + 8 + 40 + 8 + 8 + 8 + 8
+    assert ez.PATCH_DTYPE.itemsize == 72
+    assert ctypes.sizeof(ez._Batch) == 4 + 4 + 8 + 8 + 40 + 8 + 8 + 8 + 8 + 8

@@ -1,0 +1,101 @@
+"""Pins of the hierarchy reference (oracle/hierarchy.py): SecondOrderA against
+the properties Appendix A states for it (conservative, exact for linear
+fields, monotone), projection, and conservation of the composite grid over a
+full root step with subcycling, flux correction and projection."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import hierarchy as H
+from paper_1307_2265_gb300 import synth
+
+
+def test_second_order_a_exact_for_linear_fields_and_conservative():
+    rng = np.random.default_rng(0)
+    n = 200
+    a, b, c, d = (rng.normal(0, 1, n) for _ in range(4))
+    z, y, x = np.meshgrid([-1, 0, 1], [-1, 0, 1], [-1, 0, 1], indexing="ij")
+    Q = d[:, None, None, None] + a[:, None, None, None] * x + b[:, None, None, None] * y + c[:, None, None, None] * z
+    kids = H.second_order_a(Q)
+    off = np.array([-0.25, 0.25])
+    exact = (d[:, None, None, None] + a[:, None, None, None] * off[None, None, None, :]
+             + b[:, None, None, None] * off[None, None, :, None] + c[:, None, None, None] * off[None, :, None, None])
+    assert np.allclose(kids, exact, atol=1e-13)
+    # conservation for arbitrary data: children average to the parent
+    Q = rng.normal(0, 1, (n, 3, 3, 3))
+    kids = H.second_order_a(Q)
+    assert np.allclose(kids.mean(axis=(1, 2, 3)), Q[:, 1, 1, 1], atol=1e-14)
+
+
+def test_second_order_a_adds_no_new_extrema_on_smooth_data():
+    rng = np.random.default_rng(1)
+    n = 2000
+    base = rng.normal(0, 1, (n, 4))
+    z, y, x = np.meshgrid([-1, 0, 1], [-1, 0, 1], [-1, 0, 1], indexing="ij")
+    Q = (base[:, 0, None, None, None] + base[:, 1, None, None, None] * x + base[:, 2, None, None, None] * y
+         + base[:, 3, None, None, None] * z + 0.3 * rng.normal(0, 1, (n, 3, 3, 3)))
+    kids = H.second_order_a(Q)
+    lo = Q.reshape(n, -1).min(axis=1)
+    hi = Q.reshape(n, -1).max(axis=1)
+    assert np.all(kids.reshape(n, -1).min(axis=1) >= lo - 1e-12)
+    assert np.all(kids.reshape(n, -1).max(axis=1) <= hi + 1e-12)
+
+
+def test_minmod_definition():
+    a = np.array([1.0, -2.0, 3.0, 0.0, -1.0])
+    b = np.array([2.0, -1.0, -1.0, 5.0, -3.0])
+    assert np.array_equal(H.minmod(a, b), np.array([1.0, -1.0, 0.0, 0.0, -1.0]))
+
+
+def _small(seed=0):
+    layout = synth.hierarchy_layout(16, [(4, 12), (6, 10)], [4, 8], seed=seed)
+    fields = synth.hierarchy_fields(layout, config=5)
+    return layout, H.make_levels(layout, fields, 1.0 / 16)
+
+
+def test_projection_of_piecewise_constant_children_is_identity():
+    layout, levels = _small()
+    before = [f.copy() for f in levels[0]["patches"][0]["U"]]
+    H.project(levels, 0)
+    for a, b in zip(levels[0]["patches"][0]["U"], before):
+        # the sum of 8 equal values rounds at each of its additions
+        assert np.allclose(a, b, rtol=4e-16, atol=0)
+        assert not np.array_equal(a, np.zeros_like(a))
+
+
+@pytest.mark.slow
+def test_composite_conservation_over_a_root_step():
+    layout, levels = _small(seed=3)
+    P = oracle.Params()
+    t0 = H.composite_totals(levels)
+    log = []
+    H.root_step(levels, P, log=log)
+    t1 = H.composite_totals(levels)
+    scale = H.composite_totals([{"patches": [{"n": p["n"], "origin": p["origin"], "parent": p["parent"],
+                                              "U": [np.abs(f) for f in p["U"]]} for p in L["patches"]],
+                                 "dx": L["dx"]} for L in levels])
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0) / scale
+    # the finer levels subcycled to catch up with their parents
+    assert sum(1 for l, _ in log if l == 2) >= 2 * sum(1 for l, _ in log if l == 1) >= 2
+
+
+def test_uniform_state_preserved_through_the_hierarchy():
+    """Preserved to round-off: corner averages and projections sum eight equal
+    values, which rounds, so the interpolated ghosts differ from the state by
+    an ulp."""
+    layout = synth.hierarchy_layout(16, [(4, 12), (6, 10)], [4, 8], seed=0)
+    uni = []
+    for l, L in enumerate(layout):
+        per = []
+        for i in range(len(L["n"])):
+            nx, ny, nz = (int(v) for v in L["n"][i])
+            sh = (nz, ny, nx)
+            prims = [np.full(sh, 1.3), np.full(sh, 0.4), np.full(sh, -0.7), np.full(sh, 0.2), np.full(sh, 0.9)]
+            per.append([synth.embed(f) for f in synth.prims_to_conserved(*prims, 5.0 / 3.0)])
+        uni.append(per)
+    levels = H.make_levels(layout, uni, 1.0 / 16)
+    H.root_step(levels, oracle.Params())
+    for L, ref in zip(levels, uni):
+        for p, r in zip(L["patches"], ref):
+            for a, b in zip(p["U"], r):
+                assert np.allclose(H._active(a), H._active(b), rtol=1e-14, atol=1e-14)
