@@ -344,6 +344,71 @@ def run_gpu(args, rank, world):
     return res
 
 
+def run_hierarchy(args, rank, world):
+    """Full hierarchy: 256^3 periodic root and three nested levels refined by 2
+    (central 192^3, 128^3 and 64^3 root cells; patches from guillotine cuts with
+    per-axis sizes 16..32), white-noise initial state on the root inherited by
+    the finer levels.  One root step is the subcycled W-cycle (level l takes
+    about 2^l steps), with ghost fill from parents and siblings, flux
+    correction and projection.  Times one root step of each path."""
+    import torch
+    import paper_1307_2265_gb300 as ez
+    from paper_1307_2265_gb300 import hierarchy as gh
+    from paper_1307_2265_gb300 import synth, train_guess
+    dev = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(dev)
+    states = train_guess.default_training_set(gamma=GAMMA, stride=8, cap=3_000_000)
+    x, y, _ = train_guess.dataset(states, GAMMA)
+    net, train_info = train_guess.train(x, y, steps=args.train_steps)
+    del states, x, y
+    t0 = time.perf_counter()
+    layout = synth.hierarchy_layout(args.root, [(args.root // 8, 7 * args.root // 8),
+                                                (args.root // 4, 3 * args.root // 4),
+                                                (3 * args.root // 8, 5 * args.root // 8)],
+                                    list(range(16, 33, 2)), seed=rank)
+    fields = synth.hierarchy_fields(layout, config=5)
+    setup = time.perf_counter() - t0
+    out = {}
+    for name, params in (("fp32_learned", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, guess=ez.GUESS_MLP,
+                                                    mlp=net.blob)),
+                         ("fp32_plain", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32)),
+                         ("fp64_plain", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP64))):
+        hier = gh.Hierarchy(layout, fields, 1.0 / args.root)
+        hier.timing = {}
+        cflp = ez.Params(gamma=GAMMA, cfl=CFL, precision=params.precision)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(hier.stream)
+        log = []
+        hier.root_step(params, cflp, log=log)
+        e1.record(hier.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = {}
+        for lev in hier.levels:
+            for k, v in lev["batch"].read_status().items():
+                st[k] = st.get(k, 0) + v
+        out[name] = {"value": hier.cell_updates / (ms * 1e-3) / 1e6, "unit": "Mcell-updates/s",
+                     "ms_per_root_step": ms, "cell_updates_per_root_step": hier.cell_updates,
+                     "substeps_per_level": [sum(1 for l, _ in log if l == k) for k in range(len(layout))],
+                     "newton_iters_per_interface": st["newton_iters"] / max(1, st["interfaces"]),
+                     "nan": st["nan"], "hll_cells": st["hll_cells"],
+                     "ms_by_operation": hier.timing_ms()}
+        del hier
+        torch.cuda.empty_cache()
+    res = {"metric": METRIC, "value": out["fp32_learned"]["value"], "unit": "Mcell-updates/s", "n_gpus": world,
+           "steps": 1, "warmup": 0, "ms_per_step": out["fp32_learned"]["ms_per_root_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc",
+           "data": "synthetic",
+           "config": {"workload": f"static hierarchy: {args.root}^3 periodic root + 3 levels (r=2) over the central "
+                                  f"3/4, 1/2, 1/4 of the root per axis, patches 16..32 per axis, "
+                                  f"{sum(len(L['n']) for L in layout)} patches, one subcycled root step",
+                      "patches_per_level": [len(L["n"]) for L in layout],
+                      "cells_per_level": [int(np.prod(L["n"], axis=1).sum()) for L in layout]},
+           "paths": out, "training": train_info, "setup_seconds": setup}
+    return res
+
+
 def run_reference(args):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the same level:
     each step advances the first patches of the batch (by index) until about
@@ -422,13 +487,15 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work in the CPU leg")
     ap.add_argument("--sample-patches", type=int, default=6)
     ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--workload", default="level", choices=["level", "hierarchy"])
+    ap.add_argument("--root", type=int, default=256, help="root grid size of the hierarchy workload")
     args = ap.parse_args()
     rank, world = dist_init()
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)))
         return
-    res = run_gpu(args, rank, world)
+    res = run_hierarchy(args, rank, world) if args.workload == "hierarchy" else run_gpu(args, rank, world)
     if rank == 0:
         print(json.dumps(res))
 

@@ -296,17 +296,21 @@ typedef struct {        /* a face of a fine patch on the boundary of the refined
     int32_t target;     /* coarse patch holding the coarse cells outside that face */
 } enzo_fc_face;
 
-/* SetBoundaryValues of a refined level (Sec. 3.1): every ghost cell of every
- * patch with a parent is interpolated from the parent level by SecondOrderA
- * (Appendix A) after linear interpolation in time, parent = parent_old +
- * w (parent_new - parent_old); then the ghost cells listed in boxes are
- * overwritten by copies of the siblings' active cells.  parent_old and
- * parent_new share the parent level's descriptors (parent_new->patches) and
- * differ in U.  Refinement factor r must be 2. */
+/* SetBoundaryValues of a refined level (Sec. 3.1): ghost cells are
+ * interpolated from the parent level by SecondOrderA (Appendix A) after linear
+ * interpolation in time, parent = parent_old + w (parent_new - parent_old),
+ * then overwritten by copies of the siblings' active cells.  Only the ghost
+ * regions listed in interp_boxes (regions no sibling covers; src unused) are
+ * interpolated, since the copies replace the rest; copy_boxes list the
+ * sibling copies.  parent_old and parent_new share the parent level's
+ * descriptors (parent_new->patches) and differ in U.  precision ENZO_FP64: the
+ * interpolation arithmetic in FP64; ENZO_FP32: in FP32 (for the FP32 path,
+ * whose reconstruction reads the ghosts in FP32).  Refinement factor r = 2. */
 int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *fine_links,
                           const enzo_patch_batch *parent_new, const enzo_patch_link *parent_links,
-                          double *const parent_old_U[5], double w, const enzo_copy_box *boxes,
-                          int32_t nbox, int32_t r);
+                          double *const parent_old_U[5], double w, const enzo_copy_box *interp_boxes,
+                          int32_t ninterp, const enzo_copy_box *copy_boxes, int32_t ncopy, int32_t precision,
+                          int32_t r);
 
 /* Flux correction (Sec. 3.4): for each listed face of a fine patch, the coarse
  * cells just outside it get U += (dt_coarse F_coarse - mean of the fine

@@ -21,116 +21,166 @@ __device__ __forceinline__ double minmod(double a, double b)
 }
 
 // SecondOrderA value of child (kz, ky, kx) of the centre of a 3x3x3 parent
-// neighbourhood Q[z][y][x] (r = 2).
-__device__ double second_order_a(const double Q[3][3][3], int kz, int ky, int kx)
+// neighbourhood Q[z][y][x] (r = 2).  T = double: the reference arithmetic;
+// T = float: the same steps for the FP32 path (ghost values only feed the
+// FP32 reconstruction; conservation is kept by flux correction).
+template <class T>
+__device__ __forceinline__ T minmod_t(T a, T b)
 {
-    const double Q0 = Q[1][1][1];
-    double C[2][2][2];
+    const T aa = fabs(a), ab = fabs(b);
+    const T m = aa < ab ? aa : ab;
+    const T out = a > (T)0 ? m : (a < (T)0 ? -m : (T)0);
+    return a * b < (T)0 ? (T)0 : out;
+}
+
+template <class T>
+__device__ __forceinline__ T second_order_a(const T Q[3][3][3], int kz, int ky, int kx)
+{
+    const T Q0 = Q[1][1][1];
+    T C[2][2][2];
+#pragma unroll
     for (int sz = 0; sz < 2; ++sz)
+#pragma unroll
         for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
             for (int sx = 0; sx < 2; ++sx) {
-                double acc = 0.0;
+                T acc = (T)0;
+#pragma unroll
                 for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
                     for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
                         for (int dx = 0; dx < 2; ++dx) acc = acc + Q[sz + dz][sy + dy][sx + dx];
-                C[sz][sy][sx] = acc * 0.125;
+                C[sz][sy][sx] = acc * (T)0.125;
             }
     // diagonals: plus corners (z,y,x) = (1,1,1), (1,1,0), (1,0,1), (0,1,1)
-    const double d0 = minmod(C[1][1][1] - Q0, Q0 - C[0][0][0]);
-    const double d1 = minmod(C[1][1][0] - Q0, Q0 - C[0][0][1]);
-    const double d2 = minmod(C[1][0][1] - Q0, Q0 - C[0][1][0]);
-    const double d3 = minmod(C[0][1][1] - Q0, Q0 - C[1][0][0]);
-    double a1 = d1, a2 = d2, a3 = d3;
-    if (d0 == 0.0) {
-        a1 = a2 = a3 = 0.0;
+    const T d0 = minmod_t(C[1][1][1] - Q0, Q0 - C[0][0][0]);
+    const T d1 = minmod_t(C[1][1][0] - Q0, Q0 - C[0][0][1]);
+    const T d2 = minmod_t(C[1][0][1] - Q0, Q0 - C[0][1][0]);
+    const T d3 = minmod_t(C[0][1][1] - Q0, Q0 - C[1][0][0]);
+    T a1 = d1, a2 = d2, a3 = d3;
+    if (d0 == (T)0) {
+        a1 = a2 = a3 = (T)0;
     } else {
-        const double s = ((d1 + d2) + d3) / d0;
-        if (s < 0.0 || s > 1.0) {
-            const double sp = s < 0.0 ? 0.0 : 1.0;
-            const double c1 = s < 0.0 ? (d1 / d0 < 0.0 ? 1.0 : 0.0) : (d1 / d0 > 0.0 ? 1.0 : 0.0);
-            const double c2 = s < 0.0 ? (d2 / d0 < 0.0 ? 1.0 : 0.0) : (d2 / d0 > 0.0 ? 1.0 : 0.0);
-            const double c3 = s < 0.0 ? (d3 / d0 < 0.0 ? 1.0 : 0.0) : (d3 / d0 > 0.0 ? 1.0 : 0.0);
-            const double num = sp * d0 - (((1.0 - c1) * d1 + (1.0 - c2) * d2) + (1.0 - c3) * d3);
-            const double den = ((c1 * d1 + c2 * d2) + c3 * d3) + kEps;
-            const double f = num / den;
-            a1 = f * c1 * d1 + (1.0 - c1) * d1;
-            a2 = f * c2 * d2 + (1.0 - c2) * d2;
-            a3 = f * c3 * d3 + (1.0 - c3) * d3;
+        const T s = ((d1 + d2) + d3) / d0;
+        if (s < (T)0 || s > (T)1) {
+            const T sp = s < (T)0 ? (T)0 : (T)1;
+            const T c1 = s < (T)0 ? (d1 / d0 < (T)0 ? (T)1 : (T)0) : (d1 / d0 > (T)0 ? (T)1 : (T)0);
+            const T c2 = s < (T)0 ? (d2 / d0 < (T)0 ? (T)1 : (T)0) : (d2 / d0 > (T)0 ? (T)1 : (T)0);
+            const T c3 = s < (T)0 ? (d3 / d0 < (T)0 ? (T)1 : (T)0) : (d3 / d0 > (T)0 ? (T)1 : (T)0);
+            const T num = sp * d0 - ((((T)1 - c1) * d1 + ((T)1 - c2) * d2) + ((T)1 - c3) * d3);
+            const T den = ((c1 * d1 + c2 * d2) + c3 * d3) + (sizeof(T) == 8 ? (T)kEps : (T)1e-37f);
+            const T f = num / den;
+            a1 = f * c1 * d1 + ((T)1 - c1) * d1;
+            a2 = f * c2 * d2 + ((T)1 - c2) * d2;
+            a3 = f * c3 * d3 + ((T)1 - c3) * d3;
         }
     }
-    const double fx = a2 + a3, fy = a1 + a3, fz = a1 + a2;
-    const double cx = kx ? 0.25 : -0.25, cy = ky ? 0.25 : -0.25, cz = kz ? 0.25 : -0.25;
+    const T fx = a2 + a3, fy = a1 + a3, fz = a1 + a2;
+    const T cx = kx ? (T)0.25 : (T)-0.25, cy = ky ? (T)0.25 : (T)-0.25, cz = kz ? (T)0.25 : (T)-0.25;
     return ((Q0 + cx * fx) + cy * fy) + cz * fz;
 }
+
+// float <-> double on the integer pipe (as in the FP32 sweep): round toward
+// zero into float, exact widening back.
+__device__ __forceinline__ float h_d2f(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    const unsigned bits = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return __uint_as_float(e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : bits));
+}
+__device__ __forceinline__ double h_f2d(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u;
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned m = b & 0x7fffffu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+    unsigned lo = m << 29;
+    hi = e == 0u ? sign : (e == 255u ? (sign | 0x7ff00000u | (m >> 3)) : hi);
+    lo = e == 0u ? 0u : lo;
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return h_f2d(x); }
+template <class T> __device__ __forceinline__ T from_d(double x);
+template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_d<float>(double x) { return h_d2f(x); }
 
 __device__ __forceinline__ int floordiv2(int g) { return g >= 0 ? g / 2 : -((1 - g) / 2); }
 
 struct InterpArgs {
     const enzo_patch *fine;
     const enzo_patch_link *flink;
-    int nfine;
     double *U[5];
     const enzo_patch *par;
     const enzo_patch_link *plink;
     const double *Pn[5];
     const double *Po[5];
     double w;
-    const int *prefix;
+    const enzo_copy_box *boxes;   // ghost regions no sibling covers (src unused)
+    int nbox;
 };
 
-// Every ghost cell of every fine patch with a parent.
+// Ghost cells of the listed boxes get the parent's SecondOrderA value (one CTA
+// per box; cells that siblings cover are copied afterwards and skipped here).
+template <class T>
 __global__ void __launch_bounds__(256) interp_ghosts_kernel(const __grid_constant__ InterpArgs a)
 {
-    const int total = a.prefix[a.nfine];
-    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        int lo = 0, hi = a.nfine;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (a.prefix[mid] <= tile) lo = mid; else hi = mid;
-        }
-        const enzo_patch P = a.fine[lo];
-        const enzo_patch_link L = a.flink[lo];
+    for (int bi = blockIdx.x; bi < a.nbox; bi += gridDim.x) {
+        const enzo_copy_box B = a.boxes[bi];
+        const enzo_patch P = a.fine[B.dst];
+        const enzo_patch_link L = a.flink[B.dst];
         if (L.parent < 0) continue;
-        const int N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng, N2 = P.n[2] + 2 * P.ng;
-        const int64_t cell = (int64_t)(tile - a.prefix[lo]) * 256 + threadIdx.x;
-        if (cell >= (int64_t)N0 * N1 * N2) continue;
-        const int s[3] = {(int)(cell % N0), (int)((cell / N0) % N1), (int)(cell / ((int64_t)N0 * N1))};
-        bool ghost = false;
-        for (int d = 0; d < 3; ++d)
-            if (s[d] < P.ng || s[d] >= P.ng + P.n[d]) ghost = true;
-        if (!ghost) continue;
         const enzo_patch PP = a.par[L.parent];
         const enzo_patch_link PL = a.plink[L.parent];
-        int G[3], kid[3], ps[3];
-        for (int d = 0; d < 3; ++d) {
-            const int g = L.origin[d] + s[d] - P.ng;
-            G[d] = floordiv2(g);
-            kid[d] = g - 2 * G[d];
-            ps[d] = G[d] - PL.origin[d] + PP.ng;
-        }
+        const int e0 = B.hi[0] - B.lo[0], e1 = B.hi[1] - B.lo[1], e2 = B.hi[2] - B.lo[2];
+        const int64_t vol = (int64_t)e0 * e1 * e2;
+        const int N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng;
         const int M0 = PP.n[0] + 2 * PP.ng, M1 = PP.n[1] + 2 * PP.ng;
-        const int64_t dst = P.off + cell;
-        for (int f = 0; f < 5; ++f) {
-            double Q[3][3][3];
-            for (int dz = 0; dz < 3; ++dz)
-                for (int dy = 0; dy < 3; ++dy)
-                    for (int dx = 0; dx < 3; ++dx) {
-                        const int64_t idx = PP.off + (ps[0] - 1 + dx) +
-                                            (int64_t)M0 * ((ps[1] - 1 + dy) + (int64_t)M1 * (ps[2] - 1 + dz));
-                        const double o = a.Po[f][idx], n = a.Pn[f][idx];
-                        Q[dz][dy][dx] = o + a.w * (n - o);
-                    }
-            a.U[f][dst] = second_order_a(Q, kid[2], kid[1], kid[0]);
+        const T w = (T)a.w;
+        for (int64_t c = threadIdx.x; c < vol; c += blockDim.x) {
+            const int g[3] = {B.lo[0] + (int)(c % e0), B.lo[1] + (int)((c / e0) % e1),
+                              B.lo[2] + (int)(c / ((int64_t)e0 * e1))};
+            int kid[3], ps[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int G = floordiv2(g[d]);
+                kid[d] = g[d] - 2 * G;
+                ps[d] = G - PL.origin[d] + PP.ng;
+            }
+            const int64_t dst = P.off + (g[0] - L.origin[0] + P.ng) +
+                                (int64_t)N0 * ((g[1] - L.origin[1] + P.ng) + (int64_t)N1 * (g[2] - L.origin[2] + P.ng));
+            const int64_t base = PP.off + (ps[0] - 1) + (int64_t)M0 * ((ps[1] - 1) + (int64_t)M1 * (ps[2] - 1));
+            for (int f = 0; f < 5; ++f) {
+                T Q[3][3][3];
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const int64_t idx = base + dx + (int64_t)M0 * (dy + (int64_t)M1 * dz);
+                            const T o = from_d<T>(a.Po[f][idx]), n = from_d<T>(a.Pn[f][idx]);
+                            Q[dz][dy][dx] = o + w * (n - o);
+                        }
+                a.U[f][dst] = to_d(second_order_a<T>(Q, kid[2], kid[1], kid[0]));
+            }
         }
     }
 }
 
-// Ghost boxes copied from siblings (one CTA per box).
+// Ghost boxes copied from siblings: one warp per box (boxes are small: the
+// face, edge and corner slabs of a patch's ghost shell).
 __global__ void __launch_bounds__(256) copy_boxes_kernel(const enzo_patch *pt, const enzo_patch_link *lk,
                                                          double *U0, double *U1, double *U2, double *U3,
                                                          double *U4, const enzo_copy_box *boxes, int nbox)
 {
-    for (int bi = blockIdx.x; bi < nbox; bi += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); bi < nbox; bi += warps) {
         const enzo_copy_box B = boxes[bi];
         const enzo_patch D = pt[B.dst], S = pt[B.src];
         const enzo_patch_link DL = lk[B.dst], SL = lk[B.src];
@@ -138,7 +188,7 @@ __global__ void __launch_bounds__(256) copy_boxes_kernel(const enzo_patch *pt, c
         const int64_t vol = (int64_t)e0 * e1 * e2;
         const int D0 = D.n[0] + 2 * D.ng, D1 = D.n[1] + 2 * D.ng;
         const int S0 = S.n[0] + 2 * S.ng, S1 = S.n[1] + 2 * S.ng;
-        for (int64_t c = threadIdx.x; c < vol; c += blockDim.x) {
+        for (int64_t c = lane; c < vol; c += 32) {
             const int x = B.lo[0] + (int)(c % e0);
             const int y = B.lo[1] + (int)((c / e0) % e1);
             const int z = B.lo[2] + (int)(c / ((int64_t)e0 * e1));
@@ -310,43 +360,45 @@ extern "C" {
 
 int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *fine_links,
                           const enzo_patch_batch *parent_new, const enzo_patch_link *parent_links,
-                          double *const parent_old_U[5], double w, const enzo_copy_box *boxes, int32_t nbox,
+                          double *const parent_old_U[5], double w, const enzo_copy_box *interp_boxes,
+                          int32_t ninterp, const enzo_copy_box *copy_boxes, int32_t ncopy, int32_t precision,
                           int32_t r)
 {
     if (r != 2 || !batch_ok(fine) || !batch_ok(parent_new) || !fine_links || !parent_links || !parent_old_U)
         return ENZO_ERR_ARG;
-    if (!(w >= 0.0) || !(w <= 1.0) || nbox < 0 || (nbox > 0 && !boxes)) return ENZO_ERR_ARG;
+    if (!(w >= 0.0) || !(w <= 1.0) || ninterp < 0 || ncopy < 0 || (ninterp > 0 && !interp_boxes) ||
+        (ncopy > 0 && !copy_boxes))
+        return ENZO_ERR_ARG;
+    if (precision != ENZO_FP64 && precision != ENZO_FP32) return ENZO_ERR_ARG;
     if (fine->npatch == 0) return ENZO_OK;
-    if (!fine->workspace || fine->ws_bytes < enzo_workspace_size(fine->npatch) || !fine->status)
-        return ENZO_ERR_WORKSPACE;
     for (int f = 0; f < 5; ++f)
         if (!parent_old_U[f]) return ENZO_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(fine->stream);
-    char *ws = static_cast<char *>(fine->workspace);
-    // tiles of 256 stored cells per patch (kind 1 = ghost-fill tiles)
-    launch_tile_prefix(fine->patches, fine->npatch, fine->field_len, 1, 0, 0,
-                       reinterpret_cast<int *>(ws + kWsPrefix), reinterpret_cast<unsigned *>(ws + kWsCounter),
-                       nullptr, fine->status, s);
-    note_launch();
-    InterpArgs a;
-    a.fine = fine->patches;
-    a.flink = fine_links;
-    a.nfine = fine->npatch;
-    for (int f = 0; f < 5; ++f) {
-        a.U[f] = fine->U[f];
-        a.Pn[f] = parent_new->U[f];
-        a.Po[f] = parent_old_U[f];
+    if (ninterp > 0) {
+        InterpArgs a;
+        a.fine = fine->patches;
+        a.flink = fine_links;
+        for (int f = 0; f < 5; ++f) {
+            a.U[f] = fine->U[f];
+            a.Pn[f] = parent_new->U[f];
+            a.Po[f] = parent_old_U[f];
+        }
+        a.par = parent_new->patches;
+        a.plink = parent_links;
+        a.w = w;
+        a.boxes = interp_boxes;
+        a.nbox = ninterp;
+        const int grid = ninterp < sm_count() * 16 ? ninterp : sm_count() * 16;
+        if (precision == ENZO_FP64) interp_ghosts_kernel<double><<<grid, 256, 0, s>>>(a);
+        else interp_ghosts_kernel<float><<<grid, 256, 0, s>>>(a);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
     }
-    a.par = parent_new->patches;
-    a.plink = parent_links;
-    a.w = w;
-    a.prefix = reinterpret_cast<const int *>(ws + kWsPrefix);
-    interp_ghosts_kernel<<<sm_count() * 8, 256, 0, s>>>(a);
-    note_launch();
-    if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
-    if (nbox > 0) {
-        copy_boxes_kernel<<<nbox < sm_count() * 16 ? nbox : sm_count() * 16, 256, 0, s>>>(
-            fine->patches, fine_links, fine->U[0], fine->U[1], fine->U[2], fine->U[3], fine->U[4], boxes, nbox);
+    if (ncopy > 0) {
+        const int grid = (ncopy + 7) / 8 < sm_count() * 8 ? (ncopy + 7) / 8 : sm_count() * 8;
+        copy_boxes_kernel<<<grid, 256, 0, s>>>(
+            fine->patches, fine_links, fine->U[0], fine->U[1], fine->U[2], fine->U[3], fine->U[4], copy_boxes,
+            ncopy);
         note_launch();
         if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
     }

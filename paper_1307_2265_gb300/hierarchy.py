@@ -36,7 +36,7 @@ def _lib():
     L = lib()
     if not getattr(L, "_hier_ready", False):
         vp, i32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
-        L.enzo_ghost_fill_level.argtypes = [vp, vp, vp, vp, vp, d, vp, i32, i32]
+        L.enzo_ghost_fill_level.argtypes = [vp, vp, vp, vp, vp, d, vp, i32, vp, i32, i32, i32]
         L.enzo_flux_correct.argtypes = [vp, vp, vp, vp, vp, i32, d, i32, i32]
         L.enzo_project.argtypes = [vp, vp, vp, vp, i32]
         for n in ("enzo_ghost_fill_level", "enzo_flux_correct", "enzo_project"):
@@ -53,20 +53,95 @@ def _to_dev(arr, device):
     return torch.from_numpy(raw).to(device)
 
 
+class _Grid:
+    """Patch lookup of a level tiled by the tensor product of per-axis segments."""
+
+    def __init__(self, n, origin):
+        self.n, self.origin = np.asarray(n), np.asarray(origin)
+        self.starts = [np.unique(self.origin[:, a]) for a in range(3)]
+        self.index = {}
+        for i, o in enumerate(self.origin):
+            self.index[tuple(int(v) for v in o)] = i
+
+    def seg(self, a, x):
+        """Index of the segment of axis a containing coordinate x, or -1."""
+        k = int(np.searchsorted(self.starts[a], x, side="right")) - 1
+        return k
+
+    def find(self, g):
+        """Patch whose active box contains global cell g, or -1."""
+        key = []
+        for a in range(3):
+            k = self.seg(a, g[a])
+            if k < 0:
+                return -1
+            key.append(int(self.starts[a][k]))
+        i = self.index.get(tuple(key), -1)
+        if i < 0:
+            return -1
+        lo, hi = self.origin[i], self.origin[i] + self.n[i]
+        return i if np.all((lo <= g) & (g < hi)) else -1
+
+
 def sibling_boxes(n, origin):
-    """Copy boxes (dst, src, lo, hi) of ghost cells lying in siblings' active boxes."""
-    lo = origin
-    hi = origin + n
+    """Copy boxes (dst, src, lo, hi) of ghost cells lying in siblings' active
+    boxes.  Ghost layers (3 cells) are thinner than any patch, so only the 26
+    neighbours across faces, edges and corners can meet a patch's ghost region."""
+    n, origin = np.asarray(n), np.asarray(origin)
+    grid = _Grid(n, origin)
     boxes = []
     for a in range(len(n)):
-        glo, ghi = lo[a] - NG, hi[a] + NG
-        # candidates: patches whose active box meets the ghost region
-        ov = np.all((lo < ghi) & (hi > glo), axis=1)
-        ov[a] = False
-        for b in np.nonzero(ov)[0]:
-            blo = np.maximum(glo, lo[b])
-            bhi = np.minimum(ghi, hi[b])
-            boxes.append((a, int(b), *blo.tolist(), *bhi.tolist()))
+        lo, hi = origin[a], origin[a] + n[a]
+        glo, ghi = lo - NG, hi + NG
+        seen = set()
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if dx == dy == dz == 0:
+                        continue
+                    probe = np.array([lo[0] - 1 if dx < 0 else (hi[0] if dx > 0 else lo[0]),
+                                      lo[1] - 1 if dy < 0 else (hi[1] if dy > 0 else lo[1]),
+                                      lo[2] - 1 if dz < 0 else (hi[2] if dz > 0 else lo[2])])
+                    b = grid.find(probe)
+                    if b < 0 or b in seen:
+                        continue
+                    seen.add(b)
+                    blo = np.maximum(glo, origin[b])
+                    bhi = np.minimum(ghi, origin[b] + n[b])
+                    if np.all(blo < bhi):
+                        boxes.append((a, int(b), *blo.tolist(), *bhi.tolist()))
+    t = np.zeros(len(boxes), dtype=BOX_DTYPE)
+    for i, bx in enumerate(boxes):
+        t[i]["dst"], t[i]["src"] = bx[0], bx[1]
+        t[i]["lo"] = bx[2:5]
+        t[i]["hi"] = bx[5:8]
+    return t
+
+
+def interp_boxes(n, origin):
+    """Ghost regions (of the 26 around each patch: faces, edges, corners) that no
+    sibling covers; these are interpolated from the parent."""
+    n, origin = np.asarray(n), np.asarray(origin)
+    grid = _Grid(n, origin)
+    boxes = []
+    for a in range(len(n)):
+        lo, hi = origin[a], origin[a] + n[a]
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if dx == dy == dz == 0:
+                        continue
+                    dd = (dx, dy, dz)
+                    blo = np.array([lo[t] - NG if dd[t] < 0 else (hi[t] if dd[t] > 0 else lo[t]) for t in range(3)])
+                    bhi = np.array([lo[t] if dd[t] < 0 else (hi[t] + NG if dd[t] > 0 else hi[t]) for t in range(3)])
+                    probe = np.array([lo[t] - 1 if dd[t] < 0 else (hi[t] if dd[t] > 0 else lo[t]) for t in range(3)])
+                    if grid.find(probe) >= 0:
+                        # a sibling touches this region; it must then cover all of it
+                        corner = np.array([bhi[t] - 1 if dd[t] >= 0 else blo[t] for t in range(3)])
+                        if grid.find(corner) < 0:
+                            raise ValueError("ghost region partly covered by siblings")
+                        continue
+                    boxes.append((a, a, *blo.tolist(), *bhi.tolist()))
     t = np.zeros(len(boxes), dtype=BOX_DTYPE)
     for i, bx in enumerate(boxes):
         t[i]["dst"], t[i]["src"] = bx[0], bx[1]
@@ -78,29 +153,26 @@ def sibling_boxes(n, origin):
 def correction_faces(fine, coarse, r=2):
     """Faces of fine patches whose outside coarse cells are not covered by the
     fine level, with the coarse patch holding those cells."""
-    fn, fo = fine["n"], fine["origin"]
-    flo, fhi = fo, fo + fn
-    cn, co = coarse["n"], coarse["origin"]
+    fn, fo = np.asarray(fine["n"]), np.asarray(fine["origin"])
+    cn, co = np.asarray(coarse["n"]), np.asarray(coarse["origin"])
+    fgrid = _Grid(fn, fo)
+    cgrid = _Grid(cn, co)
     faces = []
     for i in range(len(fn)):
         for d in range(3):
             for side in (0, 1):
-                # one fine cell just outside the face, at the face's first transverse position
                 probe = fo[i].copy()
                 probe[d] = fo[i][d] - 1 if side == 0 else fo[i][d] + fn[i][d]
-                covered = np.any(np.all((flo <= probe) & (probe < fhi), axis=1))
-                if covered:
+                if fgrid.find(probe) >= 0:
                     continue
                 cell = probe // r
-                tgt = np.nonzero(np.all((co <= cell) & (cell < co + cn), axis=1))[0]
-                if len(tgt) != 1:
-                    raise ValueError("coarse cell outside a fine face is not in exactly one coarse patch")
-                # the whole face must lie against that one coarse patch
+                t = cgrid.find(cell)
+                if t < 0:
+                    raise ValueError("coarse cell outside a fine face is not in a coarse patch")
                 last = cell.copy()
                 for a in range(3):
                     if a != d:
                         last[a] = (fo[i][a] + fn[i][a]) // r - 1
-                t = int(tgt[0])
                 if not np.all((co[t] <= last) & (last < co[t] + cn[t])):
                     raise ValueError("a fine face spans more than one coarse patch")
                 faces.append((i, d, side, t))
@@ -171,6 +243,8 @@ class Hierarchy:
             if has_parent:
                 bx = sibling_boxes(n, np.asarray(L["origin"]))
                 lev["boxes"], lev["nbox"] = _to_dev(bx, self.device), len(bx)
+                ib = interp_boxes(n, np.asarray(L["origin"]))
+                lev["ibox"], lev["nibox"] = _to_dev(ib, self.device), len(ib)
                 lo = int(table["freg_bnd"].min())
                 lev["bnd_sl"] = (lo, lo + int(b_sz.sum()))
             if has_children:
@@ -181,9 +255,31 @@ class Hierarchy:
                                   {"n": self.levels[l]["n"], "origin": self.levels[l]["origin"]})
             self.levels[l]["faces"], self.levels[l]["nface"] = _to_dev(fc, self.device), len(fc)
         self.cell_updates = 0
+        self.timing = None          # {op: [(start, end) events]} when profiling
+
+    def _mark(self, op):
+        """Record a CUDA event pair around an operation when timing is on."""
+        if self.timing is None:
+            return None
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        self.timing.setdefault(op, []).append([e, None])
+        return self.timing[op][-1]
+
+    def _end(self, mark):
+        if mark is None:
+            return
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        mark[1] = e
+
+    def timing_ms(self):
+        """Milliseconds per operation type (after synchronising the stream)."""
+        self.stream.synchronize()
+        return {op: sum(a.elapsed_time(b) for a, b in v) for op, v in (self.timing or {}).items()}
 
     # -- primitive operations -------------------------------------------
-    def _fill(self, l):
+    def _fill(self, l, precision):
         lev = self.levels[l]
         if l == 0:
             return          # the periodic root wraps inside its sweeps
@@ -192,8 +288,9 @@ class Hierarchy:
         b, pb = lev["batch"].c(), par["batch"].c()
         old = (ctypes.c_void_p * 5)(*[u.data_ptr() for u in par["old"]])
         _check(_lib().enzo_ghost_fill_level(ctypes.byref(b), lev["links"].data_ptr(), ctypes.byref(pb),
-                                            par["links"].data_ptr(), old, w, lev["boxes"].data_ptr(),
-                                            lev["nbox"], 2), "enzo_ghost_fill_level")
+                                            par["links"].data_ptr(), old, w, lev["ibox"].data_ptr(),
+                                            lev["nibox"], lev["boxes"].data_ptr(), lev["nbox"], precision, 2),
+               "enzo_ghost_fill_level")
 
     def _step(self, l, dt, params):
         lev = self.levels[l]
@@ -221,31 +318,43 @@ class Hierarchy:
         lev = self.levels[l]
         with self.torch.cuda.stream(self.stream):
             while lev["t"] < t_parent * (1 - 1e-14):
-                self._fill(l)
+                m = self._mark("ghost_fill")
+                self._fill(l, params.precision)
+                self._end(m)
                 if l == 0:
                     dt = t_parent - lev["t"]
                 else:
+                    m = self._mark("cfl")
                     dt = min(timestep_cfl(lev["batch"], cfl_params), t_parent - lev["t"])
+                    self._end(m)
                 if lev["has_children"]:
+                    m = self._mark("save_old")
                     for u, o in zip(lev["batch"].U, lev["old"]):
                         o.copy_(u)
+                    self._end(m)
                     lev["t_old"] = lev["t"]
+                m = self._mark("sweeps")
                 self._step(l, dt, params)
+                self._end(m)
                 lev["t"] += dt
                 if log is not None:
                     log.append((l, dt))
                 if lev["has_children"]:
-                    self._fill(l)
+                    m = self._mark("ghost_fill")
+                    self._fill(l, params.precision)
+                    self._end(m)
                     child = self.levels[l + 1]
                     lo, hi = child["bnd_sl"]
                     child["batch"].freg[lo:hi].zero_()
                     self.evolve_level(l + 1, lev["t"], params, cfl_params, log)
+                    m = self._mark("correct_project")
                     self._correct_and_project(l, dt, params)
+                    self._end(m)
 
     def root_step(self, params, cfl_params=None, log=None):
         """One root step: dt_0 from the root CFL rule, then the W-cycle."""
         cfl_params = cfl_params if cfl_params is not None else Params(
-            gamma=params.gamma, cfl=params.cfl, precision=0)
+            gamma=params.gamma, cfl=params.cfl, precision=params.precision)
         root = self.levels[0]
         with self.torch.cuda.stream(self.stream):
             dt0 = timestep_cfl(root["batch"], cfl_params)

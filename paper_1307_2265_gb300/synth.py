@@ -206,7 +206,7 @@ def hierarchy_layout(root_n, regions, sizes, seed=0, r=2):
     regions: [(a_1, b_1), (a_2, b_2), ...] in root cells, nested.
     Returns a list of levels, each {"n": int array [P, 3] (nx, ny, nz),
     "origin": int array [P, 3] (global index of the first active cell at that
-    level), "parent": int array [P] (-1 for the root), "cuts": per-axis segment
+    level), "parent": int array [P] (-1 for the root), "segs": per-axis segment
     lists}.
     """
     rng = np.random.default_rng(SEED_BASE + 500 + seed)
@@ -234,20 +234,23 @@ def hierarchy_layout(root_n, regions, sizes, seed=0, r=2):
             segs_axes.append(segs)
         ns, origins, parents = [], [], []
         prev = levels[l - 1]
+        pindex = {tuple(int(v) for v in o): i for i, o in enumerate(prev["origin"])}
+        pstarts = [np.array(sorted({sg[0] for sg in prev["segs"][a]})) for a in range(3)]
         for sz in segs_axes[2]:
             for sy in segs_axes[1]:
                 for sx in segs_axes[0]:
                     o = np.array([sx[0], sy[0], sz[0]])
                     n = np.array([sx[1] - sx[0], sy[1] - sy[0], sz[1] - sz[0]])
                     # parent: the level-(l-1) patch whose active box contains this one
-                    po, pn = prev["origin"], prev["n"]
-                    inside = np.all((po * r <= o) & (o + n <= (po + pn) * r), axis=1)
-                    idx = np.nonzero(inside)[0]
-                    if len(idx) != 1:
+                    key = tuple(int(pstarts[a][np.searchsorted(pstarts[a], o[a] // r, side="right") - 1])
+                                for a in range(3))
+                    pi = pindex.get(key, -1)
+                    po, pn = prev["origin"][pi], prev["n"][pi]
+                    if pi < 0 or not np.all((po * r <= o) & (o + n <= (po + pn) * r)):
                         raise ValueError("patch not enclosed by exactly one parent")
                     ns.append(n)
                     origins.append(o)
-                    parents.append(int(idx[0]))
+                    parents.append(int(pi))
         levels.append({"n": np.array(ns), "origin": np.array(origins, dtype=np.int64),
                        "parent": np.array(parents), "segs": segs_axes})
     return levels
@@ -269,15 +272,11 @@ def hierarchy_fields(layout, config=5, gamma=5.0 / 3.0, ng=NG):
             p = int(L["parent"][i])
             po = prev["origin"][p]
             PU = out[l - 1][p]
-            gz = np.arange(nz) + o[2]
-            gy = np.arange(ny) + o[1]
-            gx = np.arange(nx) + o[0]
-            iz = gz // 2 - po[2] + ng
-            iy = gy // 2 - po[1] + ng
-            ix = gx // 2 - po[0] + ng
+            c0 = o // 2 - po + ng           # first covering parent cell (storage index)
             fl = []
             for f in range(5):
-                act = PU[f][np.ix_(iz, iy, ix)]
+                blk = PU[f][c0[2]:c0[2] + nz // 2, c0[1]:c0[1] + ny // 2, c0[0]:c0[0] + nx // 2]
+                act = blk.repeat(2, axis=0).repeat(2, axis=1).repeat(2, axis=2)
                 fl.append(embed(act, ng))
             fields.append(fl)
         out.append(fields)
