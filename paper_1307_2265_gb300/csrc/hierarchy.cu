@@ -124,12 +124,15 @@ struct InterpArgs {
     int nbox;
 };
 
-// Ghost cells of the listed boxes get the parent's SecondOrderA value (one CTA
-// per box; cells that siblings cover are copied afterwards and skipped here).
+// Ghost cells of the listed boxes get the parent's SecondOrderA value (one warp
+// per box: boxes are the 3-cell-thick face, edge and corner slabs of a patch's
+// ghost shell; cells that siblings cover are copied afterwards and not listed).
 template <class T>
 __global__ void __launch_bounds__(256) interp_ghosts_kernel(const __grid_constant__ InterpArgs a)
 {
-    for (int bi = blockIdx.x; bi < a.nbox; bi += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); bi < a.nbox; bi += warps) {
         const enzo_copy_box B = a.boxes[bi];
         const enzo_patch P = a.fine[B.dst];
         const enzo_patch_link L = a.flink[B.dst];
@@ -137,13 +140,13 @@ __global__ void __launch_bounds__(256) interp_ghosts_kernel(const __grid_constan
         const enzo_patch PP = a.par[L.parent];
         const enzo_patch_link PL = a.plink[L.parent];
         const int e0 = B.hi[0] - B.lo[0], e1 = B.hi[1] - B.lo[1], e2 = B.hi[2] - B.lo[2];
-        const int64_t vol = (int64_t)e0 * e1 * e2;
+        const int vol = e0 * e1 * e2, e01 = e0 * e1;
         const int N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng;
         const int M0 = PP.n[0] + 2 * PP.ng, M1 = PP.n[1] + 2 * PP.ng;
         const T w = (T)a.w;
-        for (int64_t c = threadIdx.x; c < vol; c += blockDim.x) {
-            const int g[3] = {B.lo[0] + (int)(c % e0), B.lo[1] + (int)((c / e0) % e1),
-                              B.lo[2] + (int)(c / ((int64_t)e0 * e1))};
+        for (int c = lane; c < vol; c += 32) {
+            const int gz = c / e01, rem = c - gz * e01, gy = rem / e0;
+            const int g[3] = {B.lo[0] + rem - gy * e0, B.lo[1] + gy, B.lo[2] + gz};
             int kid[3], ps[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -173,34 +176,51 @@ __global__ void __launch_bounds__(256) interp_ghosts_kernel(const __grid_constan
 }
 
 // Ghost boxes copied from siblings: one warp per box (boxes are small: the
-// face, edge and corner slabs of a patch's ghost shell).
-__global__ void __launch_bounds__(256) copy_boxes_kernel(const enzo_patch *pt, const enzo_patch_link *lk,
+// face, edge and corner slabs of a patch's ghost shell).  Each lane loads the
+// five fields of up to kCopyUnroll cells before storing any, so that enough
+// loads are in flight to cover HBM latency (sources are active cells, which
+// this kernel never writes).
+constexpr int kCopyUnroll = 2;
+
+__global__ void __launch_bounds__(256, 4) copy_boxes_kernel(const enzo_patch *pt, const enzo_patch_link *lk,
                                                          double *U0, double *U1, double *U2, double *U3,
                                                          double *U4, const enzo_copy_box *boxes, int nbox)
 {
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
+    double *const U[5] = {U0, U1, U2, U3, U4};
     for (int bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); bi < nbox; bi += warps) {
         const enzo_copy_box B = boxes[bi];
         const enzo_patch D = pt[B.dst], S = pt[B.src];
         const enzo_patch_link DL = lk[B.dst], SL = lk[B.src];
         const int e0 = B.hi[0] - B.lo[0], e1 = B.hi[1] - B.lo[1], e2 = B.hi[2] - B.lo[2];
-        const int64_t vol = (int64_t)e0 * e1 * e2;
-        const int D0 = D.n[0] + 2 * D.ng, D1 = D.n[1] + 2 * D.ng;
-        const int S0 = S.n[0] + 2 * S.ng, S1 = S.n[1] + 2 * S.ng;
-        for (int64_t c = lane; c < vol; c += 32) {
-            const int x = B.lo[0] + (int)(c % e0);
-            const int y = B.lo[1] + (int)((c / e0) % e1);
-            const int z = B.lo[2] + (int)(c / ((int64_t)e0 * e1));
-            const int64_t di = D.off + (x - DL.origin[0] + D.ng) +
-                               (int64_t)D0 * ((y - DL.origin[1] + D.ng) + (int64_t)D1 * (z - DL.origin[2] + D.ng));
-            const int64_t si = S.off + (x - SL.origin[0] + S.ng) +
-                               (int64_t)S0 * ((y - SL.origin[1] + S.ng) + (int64_t)S1 * (z - SL.origin[2] + S.ng));
-            U0[di] = U0[si];
-            U1[di] = U1[si];
-            U2[di] = U2[si];
-            U3[di] = U3[si];
-            U4[di] = U4[si];
+        const int vol = e0 * e1 * e2, e01 = e0 * e1;
+        const int D0 = D.n[0] + 2 * D.ng, D01 = D0 * (D.n[1] + 2 * D.ng);
+        const int S0 = S.n[0] + 2 * S.ng, S01 = S0 * (S.n[1] + 2 * S.ng);
+        // box origin inside each patch's ghosted block
+        const int64_t dbase = D.off + (B.lo[0] - DL.origin[0] + D.ng) + (int64_t)D0 * (B.lo[1] - DL.origin[1] + D.ng) +
+                              (int64_t)D01 * (B.lo[2] - DL.origin[2] + D.ng);
+        const int64_t sbase = S.off + (B.lo[0] - SL.origin[0] + S.ng) + (int64_t)S0 * (B.lo[1] - SL.origin[1] + S.ng) +
+                              (int64_t)S01 * (B.lo[2] - SL.origin[2] + S.ng);
+        for (int c0 = 0; c0 < vol; c0 += 32 * kCopyUnroll) {
+            int64_t di[kCopyUnroll], si[kCopyUnroll];
+            double v[kCopyUnroll][5];
+#pragma unroll
+            for (int k = 0; k < kCopyUnroll; ++k) {
+                const int c = c0 + lane + 32 * k;
+                const int z = c / e01, rem = c - z * e01;
+                const int y = rem / e0, x = rem - y * e0;
+                di[k] = c < vol ? dbase + x + (int64_t)D0 * y + (int64_t)D01 * z : -1;
+                si[k] = sbase + x + (int64_t)S0 * y + (int64_t)S01 * z;
+                if (c < vol)
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) v[k][f] = U[f][si[k]];
+            }
+#pragma unroll
+            for (int k = 0; k < kCopyUnroll; ++k)
+                if (di[k] >= 0)
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) U[f][di[k]] = v[k][f];
         }
     }
 }
@@ -319,15 +339,22 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Pr
             const int64_t pidx = PP.off + (FL.origin[0] / 2 + x - PL.origin[0] + PP.ng) +
                                  (int64_t)P0 * ((FL.origin[1] / 2 + y - PL.origin[1] + PP.ng) +
                                                 (int64_t)P1 * (FL.origin[2] / 2 + z - PL.origin[2] + PP.ng));
+            // all 40 loads before the five stores (coarse and fine fields are
+            // distinct arrays, but the compiler cannot know that)
+            double v[5][8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+                const int64_t fidx = FP.off + (2 * x + kx + FP.ng) +
+                                     (int64_t)F0 * ((2 * y + ky + FP.ng) + (int64_t)F1 * (2 * z + kz + FP.ng));
+#pragma unroll
+                for (int f = 0; f < 5; ++f) v[f][k] = a.F[f][fidx];
+            }
+#pragma unroll
             for (int f = 0; f < 5; ++f) {
                 double s = 0.0;
-                for (int kz = 0; kz < 2; ++kz)
-                    for (int ky = 0; ky < 2; ++ky)
-                        for (int kx = 0; kx < 2; ++kx) {
-                            const int64_t fidx = FP.off + (2 * x + kx + FP.ng) +
-                                                 (int64_t)F0 * ((2 * y + ky + FP.ng) + (int64_t)F1 * (2 * z + kz + FP.ng));
-                            s = s + a.F[f][fidx];
-                        }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) s = s + v[f][k];
                 a.U[f][pidx] = s * 0.125;
             }
         }
@@ -340,6 +367,18 @@ static int sm_count()
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
     return s > 0 ? s : 1;
+}
+
+// Grid of at most `want` CTAs that the SMs hold at once (grid-stride kernels:
+// CTAs beyond the resident set would only start after the first wave ends).
+template <class K>
+static int resident_grid(K kernel, int threads, int64_t want)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t cap = (int64_t)sm_count() * per_sm;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
 static bool batch_ok(const enzo_patch_batch *b)
@@ -388,15 +427,16 @@ int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *f
         a.w = w;
         a.boxes = interp_boxes;
         a.nbox = ninterp;
-        const int grid = ninterp < sm_count() * 16 ? ninterp : sm_count() * 16;
-        if (precision == ENZO_FP64) interp_ghosts_kernel<double><<<grid, 256, 0, s>>>(a);
-        else interp_ghosts_kernel<float><<<grid, 256, 0, s>>>(a);
+        const int64_t want = (ninterp + 7) / 8;
+        if (precision == ENZO_FP64)
+            interp_ghosts_kernel<double><<<resident_grid(interp_ghosts_kernel<double>, 256, want), 256, 0, s>>>(a);
+        else
+            interp_ghosts_kernel<float><<<resident_grid(interp_ghosts_kernel<float>, 256, want), 256, 0, s>>>(a);
         note_launch();
         if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
     }
     if (ncopy > 0) {
-        const int grid = (ncopy + 7) / 8 < sm_count() * 8 ? (ncopy + 7) / 8 : sm_count() * 8;
-        copy_boxes_kernel<<<grid, 256, 0, s>>>(
+        copy_boxes_kernel<<<resident_grid(copy_boxes_kernel, 256, (ncopy + 7) / 8), 256, 0, s>>>(
             fine->patches, fine_links, fine->U[0], fine->U[1], fine->U[2], fine->U[3], fine->U[4], copy_boxes,
             ncopy);
         note_launch();
@@ -446,7 +486,7 @@ int enzo_project(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_l
     a.fp = fine->patches;
     a.fl = fine_links;
     a.nfine = fine->npatch;
-    project_kernel<<<fine->npatch < sm_count() * 16 ? fine->npatch : sm_count() * 16, 256, 0,
+    project_kernel<<<resident_grid(project_kernel, 256, fine->npatch), 256, 0,
                      static_cast<cudaStream_t>(coarse->stream)>>>(a);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;

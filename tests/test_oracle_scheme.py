@@ -1,12 +1,14 @@
 """Grid-level pins of the oracle: exact invariants of the split scheme, the CFL rule
 (Sec. 9) by brute force, periodic ghost fill (Sec. 3.1), the Sod shock tube
-(Sec. 11.2) against the exact solution, and convergence on smooth waves."""
+(Sec. 11.2) against the exact solution, the Sedov blast (Sec. 11.6) against the
+similarity solution, and convergence on smooth waves."""
 import math
 
 import numpy as np
 import pytest
 
 import exact_riemann as ex
+import sedov_similarity
 import oracle
 from paper_1307_2265_gb300 import synth
 
@@ -185,6 +187,57 @@ def test_sod_shock_tube_against_exact_solution():
     u = _active(U[1])[0, 0] / r
     sel = (x > 1.5 + 0.25 * 1.15) & (x < 1.5 + 0.25 * 1.65)      # post-shock plateau, off the contact
     assert np.all(np.abs(r[sel] - 0.26557) < 2e-3) and np.all(np.abs(u[sel] - 0.92745) < 5e-3)
+
+
+def test_sedov_similarity_constant_matches_the_paper_cylindrical_value():
+    # Sec. 11 gives alpha = 1.0 (so xi0 = alpha^(-1/4) = 1) for the cylindrical
+    # blast with gamma = 1.4; pins the similarity integration used below
+    assert abs(sedov_similarity.xi0(1.4, nu=2) - 1.0) < 0.01
+    # spherical constants rise with gamma (stiffer gas, same energy, smaller radius factor)
+    assert sedov_similarity.xi0(1.4) < sedov_similarity.xi0(5.0 / 3.0)
+
+
+def test_sedov_blast_radius_follows_similarity_solution():
+    """Point blast E = 1 in a cold uniform box (rho = 1, p = 1e-5, gamma = 5/3):
+    the shock radius follows xi0 (E t^2 / rho)^(1/5) with xi0 from the
+    self-similar equations.  Radius: half-height point (between the peak of the
+    shell-averaged density and the background) outside the peak.  The box is
+    periodic, so the run stops at r = 0.35, before the shock meets its images."""
+    n, g = 48, 5.0 / 3.0
+    dx = 1.0 / n
+    c = (np.arange(n) + 0.5) * dx - 0.5
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    R = np.sqrt(X * X + Y * Y + Z * Z)
+    inside = R < 3.01 * dx
+    p = np.full((n, n, n), 1e-5)
+    p[inside] = (g - 1.0) / (inside.sum() * dx ** 3)          # energy 1 in the 3-cell sphere
+    one, zero = np.ones((n, n, n)), np.zeros((n, n, n))
+    U = [synth.embed(f) for f in synth.prims_to_conserved(one, zero, zero, zero, p, g)]
+    P = oracle.Params(gamma=g)
+    xi = sedov_similarity.xi0(g)
+    assert abs(xi - sedov_similarity.xi0(g, h=-2.5e-4)) < 1e-5      # step-size converged
+    bins = np.floor(R / dx).astype(int).ravel()
+    counts = np.bincount(bins)
+    t, step, rs, ts = 0.0, 0, [], []
+    for r_exact in (0.2, 0.25, 0.3, 0.35):
+        t_end = (r_exact / xi) ** 2.5
+        while t < t_end - 1e-14:
+            dt = min(0.4 / oracle.cfl_rate(U, [dx] * 3, P), t_end - t)
+            oracle.step_periodic(U, [dx] * 3, dt, step, P)
+            t += dt
+            step += 1
+        prof = np.bincount(bins, _active(U[0]).ravel()) / counts
+        k = int(np.argmax(prof))
+        half = 0.5 * (prof[k] + 1.0)
+        j = k
+        while prof[j + 1] > half:
+            j += 1
+        r_num = (j + 0.5) * dx + (prof[j] - half) / (prof[j] - prof[j + 1]) * dx
+        assert abs(r_num - r_exact) < 1.0 * dx, (r_exact, r_num)
+        rs.append(r_num)
+        ts.append(t_end)
+    slope = np.polyfit(np.log(ts), np.log(rs), 1)[0]
+    assert 0.36 < slope < 0.44, slope
 
 
 def _wave_error(N, kind, gamma=5.0 / 3.0, ndim=1):
