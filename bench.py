@@ -197,7 +197,8 @@ def run_gpu(args, rank, world):
     p32 = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32)
     tiles, tile_ms = tune.autotune_tiles(batch, p32)
     p32 = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, tile=tiles)
-    pml = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob)
+    pml = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob,
+                    mlp_gate=args.mlp_gate)
     bytes_per_sweep = sweep_bytes(table, True)
 
     def reset():
@@ -370,7 +371,7 @@ def run_hierarchy(args, rank, world):
     setup = time.perf_counter() - t0
     out = {}
     for name, params in (("fp32_learned", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, guess=ez.GUESS_MLP,
-                                                    mlp=net.blob)),
+                                                    mlp=net.blob, mlp_gate=args.mlp_gate)),
                          ("fp32_plain", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32)),
                          ("fp64_plain", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP64))):
         hier = gh.Hierarchy(layout, fields, 1.0 / args.root)
@@ -407,6 +408,132 @@ def run_hierarchy(args, rank, world):
                       "cells_per_level": [int(np.prod(L["n"], axis=1).sum()) for L in layout]},
            "paths": out, "training": train_info, "setup_seconds": setup}
     return res
+
+
+def _train_net(args):
+    """The learned Newton guess, trained on this GPU with the library's kernels
+    on interface states logged from the white-noise and turbulent recipes."""
+    from paper_1307_2265_gb300 import train_guess
+    t0 = time.perf_counter()
+    states = train_guess.default_training_set(gamma=GAMMA, stride=8, cap=3_000_000)
+    x, y, _ = train_guess.dataset(states, GAMMA)
+    net, info = train_guess.train(x, y, steps=args.train_steps)
+    info["wall_seconds"] = time.perf_counter() - t0
+    return net, info
+
+
+def field_errors(got, ref, gamma):
+    """L1 relative error per field (sum |a-b| / sum |b|) and the largest per-cell
+    relative difference (rho and E against their own value; momentum components
+    against |m| + rho c_s of the cell), on the device."""
+    import torch
+    rho = ref[0]
+    mag = torch.sqrt(ref[1] ** 2 + ref[2] ** 2 + ref[3] ** 2)
+    p = (gamma - 1.0) * (ref[4] - 0.5 * mag ** 2 / rho)
+    cs = torch.sqrt(gamma * torch.clamp(p, min=1e-300) / rho)
+    l1, worst = [], 0.0
+    for f in range(5):
+        diff = (got[f] - ref[f]).abs()
+        l1.append(float(diff.sum() / ref[f].abs().sum()))
+        den = ref[f].abs() if f in (0, 4) else mag + rho * cs
+        worst = max(worst, float((diff / den).max()))
+    return {"l1_rel": l1, "max_rel": worst}
+
+
+def run_single_grid(args, rank, world):
+    """Single periodic grids of the precision and learned-guess studies:
+    turbulence: 256^3, k^-4 Gaussian random velocity at rms Mach 3, lognormal
+      rho (sigma 1), uniform p, 20 steps;
+    blast: 512^3, sixteen blast spheres (radius 4..24 cells, p up to 1e3 over
+      p = 1e-3, clipped lognormal rho with contrast 1e4), at rest, 4 steps.
+    Each path runs the same steps from the same state: plain FP64 (the
+    reference answer; bit-identical to the oracle), plain FP32 and FP32 with
+    the learned guess.  Throughput uses each path's own device CFL timestep;
+    the errors come from a second FP32 run on the FP64 path's timesteps."""
+    import torch
+    import paper_1307_2265_gb300 as ez
+    from paper_1307_2265_gb300 import synth
+    dev = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(dev)
+    net, train_info = _train_net(args)
+    if args.workload == "turbulence":
+        n, recipe, config, nsteps = 256, "turbulent", 2, args.grid_steps or 20
+    else:
+        n, recipe, config, nsteps = 512, "blast", 4, args.grid_steps or 4
+    t0 = time.perf_counter()
+    U = synth.single_grid((n, n, n), recipe, config=config + 1000 * rank, gamma=GAMMA)
+    setup = time.perf_counter() - t0
+    table = ez.patch_table([(n, n, n)], [0], [1.0 / n] * 3, flags=ez.PATCH_PERIODIC)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch = ez.PatchBatch(table, [f.ravel() for f in U], stream=stream)
+    del U
+    init = [u.clone() for u in batch.U]
+    cells = n ** 3
+
+    def reset():
+        for u, i in zip(batch.U, init):
+            u.copy_(i)
+        torch.cuda.synchronize()
+        batch.reset_status()
+
+    def run(params, dts=None):
+        """nsteps steps; own CFL timestep unless dts (device scalars) are given."""
+        reset()
+        out_dts = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for s in range(nsteps):
+                if dts is None:
+                    ez.timestep_cfl(batch, params, out=batch.dt_dev)
+                    out_dts.append(batch.dt_dev.clone())
+                else:
+                    batch.dt_dev.copy_(dts[s])
+                ez.step(batch, params, s, batch.dt_dev)
+            e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out_dts, batch.read_status()
+
+    def active():
+        return [f[3:-3, 3:-3, 3:-3] for f in batch.patch_fields(0)]
+
+    p64 = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP64)
+    p32 = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32)
+    pml = ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob,
+                    mlp_gate=args.mlp_gate)
+    launches0 = ez.launch_count()
+    ms64, dts64, st64 = run(p64)
+    ref = [a.clone() for a in active()]
+    paths = {"fp64_plain": {"value": cells * nsteps / (ms64 * 1e-3) / 1e6, "ms_per_step": ms64 / nsteps,
+                            "status": st64}}
+    for name, params in (("fp32_plain", p32), ("fp32_learned", pml)):
+        run(params)                                   # warm-up
+        ms, _, st = run(params)
+        _, _, st_e = run(params, dts64)
+        err = field_errors(active(), ref, GAMMA)
+        sweeps = 3 * cells * nsteps
+        paths[name] = {"value": cells * nsteps / (ms * 1e-3) / 1e6, "ms_per_step": ms / nsteps,
+                       "newton_iters_per_interface": st["newton_iters"] / max(1, st["interfaces"]),
+                       "learned_guess_fraction": st["guess_calls"] / max(1, st["interfaces"]),
+                       "guess_restart_fraction": st["guess_restarts"] / max(1, st["guess_calls"]),
+                       "hll_fallback_fraction": st["hll_cells"] / sweeps,
+                       "error_vs_fp64": err, "status": st_e}
+    launches = ez.launch_count() - launches0
+    lrn, pln = paths["fp32_learned"], paths["fp32_plain"]
+    return {"metric": METRIC, "value": lrn["value"], "unit": "Mcell-updates/s", "n_gpus": world,
+            "steps": nsteps, "warmup": 1, "ms_per_step": lrn["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
+            "config": {"workload": (f"{n}^3 periodic grid, " + (
+                "k^-4 Gaussian random velocity at rms Mach 3, lognormal rho sigma 1, uniform p"
+                if recipe == "turbulent" else
+                "16 blast spheres r 4..24 cells, p up to 1e3 over 1e-3, lognormal rho clipped to [1e-2, 1e2]")
+                + f", gamma 5/3, CFL 0.4, {nsteps} steps"),
+                "cells": cells, "errors": "FP32 paths run on the FP64 path's timesteps; the FP64 GPU path is "
+                                          "bit-identical to the oracle (tested at this size for the turbulent grid)"},
+            "paths": paths,
+            "newton_iters_saved_per_interface": pln["newton_iters_per_interface"] - lrn["newton_iters_per_interface"],
+            "gpu_launches": int(launches), "training": train_info, "setup_seconds": setup}
 
 
 def run_reference(args):
@@ -487,7 +614,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work in the CPU leg")
     ap.add_argument("--sample-patches", type=int, default=6)
     ap.add_argument("--train-steps", type=int, default=1500)
-    ap.add_argument("--workload", default="level", choices=["level", "hierarchy"])
+    ap.add_argument("--workload", default="level", choices=["level", "hierarchy", "turbulence", "blast"])
+    ap.add_argument("--mlp-gate", type=float, default=0.0, help="jump-strength gate of the learned guess "
+                    "(0: library default 0.03, < 0: learned guess at every interface)")
+    ap.add_argument("--grid-steps", type=int, default=0, help="steps of the single-grid workloads (0: 20 / 4)")
     ap.add_argument("--root", type=int, default=256, help="root grid size of the hierarchy workload")
     args = ap.parse_args()
     rank, world = dist_init()
@@ -495,7 +625,12 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)))
         return
-    res = run_hierarchy(args, rank, world) if args.workload == "hierarchy" else run_gpu(args, rank, world)
+    if args.workload == "hierarchy":
+        res = run_hierarchy(args, rank, world)
+    elif args.workload in ("turbulence", "blast"):
+        res = run_single_grid(args, rank, world)
+    else:
+        res = run_gpu(args, rank, world)
     if rank == 0:
         print(json.dumps(res))
 

@@ -137,6 +137,12 @@ typedef struct {
                            (the FP64 and learned paths always use 128).  Picked
                            per batch by the autotuner (paper_1307_2265_gb300.tune). */
     int32_t reserved;
+    double mlp_gate;    /* ENZO_GUESS_MLP: an interface takes the learned guess only when
+                           its jump strength max(|pL-pR|/(pL+pR), |uL-uR|/c_m) exceeds this
+                           (c_m^2 = gamma (pL+pR)/(rhoL+rhoR)); weaker interfaces keep the
+                           plain guess, which is already within a Newton step of the root
+                           there.  0 selects 0.03; < 0 takes the learned guess everywhere.
+                           A CTA whose interfaces are all below the gate skips the network. */
 } enzo_params;
 
 /* Bytes of device workspace a batch of npatch patches needs. */

@@ -48,7 +48,7 @@ class _Params(ctypes.Structure):
                 ("newton_tol", ctypes.c_double), ("newton_max", ctypes.c_int32),
                 ("fallback", ctypes.c_int32), ("rho_floor", ctypes.c_double),
                 ("p_floor", ctypes.c_double), ("mlp", ctypes.c_void_p),
-                ("tile", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32)]
+                ("tile", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32), ("mlp_gate", ctypes.c_double)]
 
 
 class _Riemann(ctypes.Structure):
@@ -110,17 +110,19 @@ class Params:
     """Method parameters (enzo_params)."""
 
     def __init__(self, gamma=5.0 / 3.0, cfl=0.4, precision=FP64, guess=GUESS_PLAIN, newton_tol=0.0,
-                 newton_max=0, fallback=1, rho_floor=1e-30, p_floor=1e-30, mlp=None, tile=(0, 0, 0)):
+                 newton_max=0, fallback=1, rho_floor=1e-30, p_floor=1e-30, mlp=None, tile=(0, 0, 0),
+                 mlp_gate=0.0):
         self.gamma, self.cfl, self.precision, self.guess = gamma, cfl, precision, guess
         self.newton_tol, self.newton_max, self.fallback = newton_tol, newton_max, fallback
         self.rho_floor, self.p_floor, self.mlp = rho_floor, p_floor, mlp
         self.tile = tuple(tile)
+        self.mlp_gate = mlp_gate
 
     def c(self) -> _Params:
         mlp_ptr = 0 if self.mlp is None else (self.mlp.data_ptr() if hasattr(self.mlp, "data_ptr") else int(self.mlp))
         return _Params(self.gamma, self.cfl, self.precision, self.guess, self.newton_tol,
                        self.newton_max, self.fallback, self.rho_floor, self.p_floor, mlp_ptr,
-                       (ctypes.c_int32 * 3)(*self.tile), 0)
+                       (ctypes.c_int32 * 3)(*self.tile), 0, self.mlp_gate)
 
 
 def patch_table(sizes, offsets, dx, flags=0, ng=3, level=0) -> np.ndarray:

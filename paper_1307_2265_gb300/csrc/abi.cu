@@ -149,6 +149,8 @@ static int resolve(const enzo_params *p, MethodParams &m)
     m.fallback = p->fallback;
     m.guess = p->guess;
     m.mlp = p->mlp;
+    if (p->mlp_gate != p->mlp_gate) return ENZO_ERR_ARG;
+    m.mlp_gate = p->mlp_gate == 0.0 ? 0.03 : p->mlp_gate;
     return ENZO_OK;
 }
 

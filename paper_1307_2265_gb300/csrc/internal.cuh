@@ -39,6 +39,7 @@ struct MethodParams {
     double gamma, rho_floor, p_floor, newton_tol;
     int newton_max, fallback, guess;
     const void *mlp;
+    double mlp_gate;   // < 0: learned guess at every interface
 };
 
 struct SweepArgs {

@@ -89,6 +89,7 @@ extern "C" int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, do
     m.fallback = p->fallback;
     m.guess = p->guess;
     m.mlp = nullptr;
+    m.mlp_gate = 0.0;
 
     void *scratch = nullptr;
     int r = noalloc_scratch(&scratch);

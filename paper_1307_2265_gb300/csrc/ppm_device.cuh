@@ -513,25 +513,34 @@ __device__ __forceinline__ double cell_update(double U, double dtdx64, double Fm
 
 // Starting guess for Newton: the plain acoustic guess (inside riemann()).
 struct PlainGuess {
+    static constexpr int kDepth = 0;   // the guess of an interface is known at once
     template <class R>
     __device__ __forceinline__ R operator()(R, R, R, R, R, R) { return (R)-1; }
 };
 
 // Learned guess evaluated on the tensor cores for the 128 interfaces the CTA's
 // pencils reach at the same march step (one per thread = one MMA row).
+// Operands, as the sweep keeps them: both layers' weights pre-scaled by 1/2 (so
+// the accumulators hold h = z/2, the argument SiLU needs) and both biases folded
+// into the products through an input column held at 1 (column 6 of the 16
+// feature columns; column 64 of the 80 activation columns).
 struct alignas(1024) GuessSmem {
-    unsigned char w1[64 * 16 * 2];
-    unsigned char w2[64 * 64 * 2];
-    unsigned char a1[128 * 16 * 2];
-    unsigned char a2[128 * 64 * 2];
-    float vec[4 * 64 + 4];   // b1, b2, w3, b3
+    unsigned char w1[64 * 16 * 2];   // B of layer 1: 64 units x 16 inputs
+    unsigned char w2[64 * 80 * 2];   // B of layer 2: 64 units x (64 + 16) inputs
+    unsigned char a1[128 * 16 * 2];  // A of layer 1: features
+    unsigned char a2[128 * 80 * 2];  // A of layer 2: layer-1 activations
+    float4 ring[2][128][3];          // per thread: traced states (sL, sR) of two march steps
+    float w3[64];
+    float b3;
+    int err;
     uint64_t mbar;
     uint32_t tmem;
 };
 
-__device__ __forceinline__ uint32_t silu_bf16x2(float a, float b)
+// SiLU of two accumulator values holding h = z/2: z sigmoid(z) = h + h tanh(h).
+__device__ __forceinline__ uint32_t silu_half_bf16x2(float h0, float h1)
 {
-    __nv_bfloat162 h = __floats2bfloat162_rn(0.5f * a, 0.5f * b);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(h0, h1);
     const uint32_t hb = *reinterpret_cast<const uint32_t *>(&h);
     uint32_t tb;
     asm("tanh.approx.bf16x2 %0, %1;" : "=r"(tb) : "r"(hb));
@@ -539,110 +548,188 @@ __device__ __forceinline__ uint32_t silu_bf16x2(float a, float b)
     return *reinterpret_cast<const uint32_t *>(&o);
 }
 
+__device__ __forceinline__ unsigned short bf16_half_bits(unsigned short b)
+{
+    const float f = __bfloat162float(__ushort_as_bfloat16(b)) * 0.5f;
+    return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+// Software-pipelined evaluation: each call of pipe() takes the states of the
+// CTA's newest interfaces and returns the guesses of the interfaces of two calls
+// back.  In one call the threads (i) wait for the products issued by the
+// previous call, (ii) finish layer 2 of the interface two calls back (SiLU and
+// the output unit), (iii) finish layer 1 of the interface one call back (SiLU
+// into the layer-2 operand), (iv) write the new features; one barrier (which
+// also votes whether any new interface passes the gate); then one thread issues
+// layer 1 of the new interfaces and layer 2 of the previous ones.  The products
+// run while the threads do the next march step's reconstruction, so no call
+// waits on the tensor core in the steady state.
 struct LearnedGuess {
+    static constexpr int kDepth = 2;
     GuessSmem *S;
     uint32_t phase;
     bool ok;
+    bool committed;      // products issued by the previous call (CTA-uniform)
+    bool any1, any2;     // layer 1 / layer 2 in flight for the interfaces 1 / 2 calls back
+    bool need1, need2;   // this thread's interface 1 / 2 calls back passed the gate
+    float s1, s2;        // sqrt(pL pR) of those interfaces
     float gamma;
+    float gate, gate2g;  // jump-strength gate (< 0: always) and gate^2 gamma
 
-    __device__ void setup(unsigned char *raw, const void *blob, float g)
+    __device__ void setup(unsigned char *raw, const void *blob, float g, double gate_)
     {
         S = reinterpret_cast<GuessSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
         const unsigned char *b = static_cast<const unsigned char *>(blob);
-        for (int i = threadIdx.x; i < (int)sizeof(S->w1) / 16; i += blockDim.x)
-            reinterpret_cast<uint4 *>(S->w1)[i] = reinterpret_cast<const uint4 *>(b + kBlobW1)[i];
-        for (int i = threadIdx.x; i < (int)sizeof(S->w2) / 16; i += blockDim.x)
-            reinterpret_cast<uint4 *>(S->w2)[i] = reinterpret_cast<const uint4 *>(b + kBlobW2)[i];
-        for (int i = threadIdx.x; i < 193; i += blockDim.x) S->vec[i] = reinterpret_cast<const float *>(b + kBlobF32)[i];
-        if (threadIdx.x == 0) tc::mbar_init(&S->mbar, 1);
+        const float *bvec = reinterpret_cast<const float *>(b + kBlobF32);   // b1, b2, w3, b3
+        // layer 1: inputs 0..5 from the blob (already 16-column tiles), column 6 = b1
+        for (int i = threadIdx.x; i < 64 * 16; i += blockDim.x) {
+            const int n = i >> 4, k = i & 15;
+            const uint32_t off = tc::tile_off(n, k, 16);
+            unsigned short v;
+            if (k == 6) v = __bfloat16_as_ushort(__float2bfloat16_rn(0.5f * bvec[n]));
+            else v = bf16_half_bits(*reinterpret_cast<const unsigned short *>(b + kBlobW1 + off));
+            *reinterpret_cast<unsigned short *>(S->w1 + off) = v;
+        }
+        // layer 2: 64 input columns re-tiled from K = 64 to K = 80, column 64 = b2
+        for (int i = threadIdx.x; i < 64 * 80; i += blockDim.x) {
+            const int n = i / 80, k = i - 80 * (i / 80);
+            unsigned short v = 0;
+            if (k < 64) v = bf16_half_bits(*reinterpret_cast<const unsigned short *>(b + kBlobW2 + tc::tile_off(n, k, 64)));
+            else if (k == 64) v = __bfloat16_as_ushort(__float2bfloat16_rn(0.5f * bvec[64 + n]));
+            *reinterpret_cast<unsigned short *>(S->w2 + tc::tile_off(n, k, 80)) = v;
+        }
+        // constant columns 64..79 of the activations: 1, 0, ..., 0
+        for (int i = threadIdx.x; i < 128 * 16; i += blockDim.x) {
+            const int r = i >> 4, k = 64 + (i & 15);
+            *reinterpret_cast<unsigned short *>(S->a2 + tc::tile_off(r, k, 80)) = k == 64 ? 0x3F80u : 0u;
+        }
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) S->w3[i] = bvec[128 + i];
+        if (threadIdx.x == 0) {
+            S->b3 = bvec[192];
+            S->err = 0;
+            tc::mbar_init(&S->mbar, 1);
+        }
         if (threadIdx.x < 32) tc::tmem_alloc(&S->tmem, 128);
+        tc::fence_async_smem();
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
         phase = 0;
         ok = true;
+        committed = any1 = any2 = need1 = need2 = false;
+        s1 = s2 = 0.0f;
         gamma = g;
+        gate = (float)gate_;
+        gate2g = gate * gate * g;
     }
 
     __device__ void teardown()
     {
+        // products still in flight (only after a failed wait: pencils drain
+        // the pipeline) get one more bounded wait before TMEM is released
+        if (committed) tc::mbar_wait(&S->mbar, phase);
         tc::fence_before();
         __syncthreads();
         if (threadIdx.x < 32) tc::tmem_dealloc(S->tmem, 128);
     }
 
-    // Every thread of the CTA calls this at the same march step.
-    __device__ float operator()(float rl, float ul, float pl, float rr, float ur, float pr)
+    // Every thread of the CTA calls this at the same march step; valid: this
+    // thread has a new interface.  Returns the learned p* of its interface of
+    // two calls back, or -1 (plain guess: below the gate, none, or failure).
+    __device__ float pipe(bool valid, float rl, float ul, float pl, float rr, float ur, float pr)
     {
         if (!ok) return -1.0f;
         const int row = threadIdx.x;
         const uint32_t lane = (uint32_t)((row & ~31) << 16);
-        float x[6];
-        mlp_features(rl, ul, pl, rr, ur, pr, gamma, x);
-#pragma unroll
-        for (int kk = 0; kk < 16; kk += 2) {
-            const __nv_bfloat162 v = __floats2bfloat162_rn(kk < 6 ? x[kk] : 0.0f, kk + 1 < 6 ? x[kk + 1] : 0.0f);
-            *reinterpret_cast<__nv_bfloat162 *>(S->a1 + tc::tile_off(row, kk, 16)) = v;
-        }
-        tc::fence_async_smem();
-        tc::fence_before();
-        __syncthreads();
-        if (row == 0) {
+        bool timeout = false;
+        if (committed) {
+            timeout = !tc::mbar_wait(&S->mbar, phase);
+            phase ^= 1u;
             tc::fence_after();
-            tc::mma_bf16(S->tmem, tc::smem_desc(tc::smem_u32(S->a1), 128, 256),
-                         tc::smem_desc(tc::smem_u32(S->w1), 128, 256), tc::idesc_bf16_f32(128, 64), false);
-            tc::commit(&S->mbar);
         }
-        if (__syncthreads_or(!tc::mbar_wait(&S->mbar, phase))) { ok = false; return -1.0f; }
-        phase ^= 1u;
-        tc::fence_after();
+        float p0 = -1.0f;
+        if (any2) {
+            // output unit of the interface two calls back
+            float y0 = S->b3, y1 = 0.0f;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float v[16];
-            tc::tmem_ld16(S->tmem + lane + c * 16, v);
+            for (int c = 0; c < 4; ++c) {
+                float v[16];
+                tc::tmem_ld16(S->tmem + lane + 64 + c * 16, v);
 #pragma unroll
-            for (int i = 0; i < 16; i += 2) {
-                const int j = c * 16 + i;
-                *reinterpret_cast<uint32_t *>(S->a2 + tc::tile_off(row, j, 64)) =
-                    silu_bf16x2(v[i] + S->vec[j], v[i + 1] + S->vec[j + 1]);
+                for (int i = 0; i < 16; i += 2) {
+                    const uint32_t o = silu_half_bf16x2(v[i], v[i + 1]);
+                    y0 = fmaf(S->w3[c * 16 + i], __uint_as_float(o << 16), y0);
+                    y1 = fmaf(S->w3[c * 16 + i + 1], __uint_as_float(o & 0xFFFF0000u), y1);
+                }
+            }
+            if (need2) p0 = s2 * __expf(y0 + y1);
+        }
+        if (any1) {
+            // layer-1 activations of the interface one call back
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float v[16];
+                tc::tmem_ld16(S->tmem + lane + c * 16, v);
+                uint4 lo, hi;
+                lo.x = silu_half_bf16x2(v[0], v[1]);
+                lo.y = silu_half_bf16x2(v[2], v[3]);
+                lo.z = silu_half_bf16x2(v[4], v[5]);
+                lo.w = silu_half_bf16x2(v[6], v[7]);
+                hi.x = silu_half_bf16x2(v[8], v[9]);
+                hi.y = silu_half_bf16x2(v[10], v[11]);
+                hi.z = silu_half_bf16x2(v[12], v[13]);
+                hi.w = silu_half_bf16x2(v[14], v[15]);
+                *reinterpret_cast<uint4 *>(S->a2 + tc::tile_off(row, c * 16, 80)) = lo;
+                *reinterpret_cast<uint4 *>(S->a2 + tc::tile_off(row, c * 16 + 8, 80)) = hi;
             }
         }
+        // features of the new interface (column 6 carries the bias)
+        const float psum = pl + pr, du = ul - ur;
+        const bool need = valid && (gate < 0.0f || fabsf(pl - pr) > gate * psum || du * du * (rl + rr) > gate2g * psum);
+        float x[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (need) mlp_features(rl, ul, pl, rr, ur, pr, gamma, x);
+        {
+            uint4 lo;
+            const __nv_bfloat162 x01 = __floats2bfloat162_rn(x[0], x[1]);
+            const __nv_bfloat162 x23 = __floats2bfloat162_rn(x[2], x[3]);
+            const __nv_bfloat162 x45 = __floats2bfloat162_rn(x[4], x[5]);
+            lo.x = *reinterpret_cast<const uint32_t *>(&x01);
+            lo.y = *reinterpret_cast<const uint32_t *>(&x23);
+            lo.z = *reinterpret_cast<const uint32_t *>(&x45);
+            lo.w = 0x3F80u;   // column 6 = 1, column 7 = 0
+            *reinterpret_cast<uint4 *>(S->a1 + tc::tile_off(row, 0, 16)) = lo;
+            *reinterpret_cast<uint4 *>(S->a1 + tc::tile_off(row, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (timeout) S->err = 1;
         tc::fence_async_smem();
         tc::fence_before();
-        __syncthreads();
-        if (row == 0) {
+        const bool anynew = __syncthreads_or(need) != 0;
+        if (S->err) {
+            ok = false;
+            return -1.0f;
+        }
+        if (row == 0 && (anynew || any1)) {
             tc::fence_after();
+            if (anynew)
+                tc::mma_bf16(S->tmem, tc::smem_desc(tc::smem_u32(S->a1), 128, 256),
+                             tc::smem_desc(tc::smem_u32(S->w1), 128, 256), tc::idesc_bf16_f32(128, 64), false);
+            if (any1) {
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-                tc::mma_bf16(S->tmem + 64, tc::smem_desc(tc::smem_u32(S->a2) + ks * 256, 128, 1024),
-                             tc::smem_desc(tc::smem_u32(S->w2) + ks * 256, 128, 1024), tc::idesc_bf16_f32(128, 64),
-                             ks > 0);
+                for (int ks = 0; ks < 5; ++ks)
+                    tc::mma_bf16(S->tmem + 64, tc::smem_desc(tc::smem_u32(S->a2) + ks * 256, 128, 1280),
+                                 tc::smem_desc(tc::smem_u32(S->w2) + ks * 256, 128, 1280),
+                                 tc::idesc_bf16_f32(128, 64), ks > 0);
+            }
             tc::commit(&S->mbar);
         }
-        if (__syncthreads_or(!tc::mbar_wait(&S->mbar, phase))) { ok = false; return -1.0f; }
-        phase ^= 1u;
-        tc::fence_after();
-        float y = S->vec[192];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float v[16];
-            tc::tmem_ld16(S->tmem + lane + 64 + c * 16, v);
-#pragma unroll
-            for (int i = 0; i < 16; i += 2) {
-                const int j = c * 16 + i;
-                const uint32_t hb = silu_bf16x2(v[i] + S->vec[64 + j], v[i + 1] + S->vec[64 + j + 1]);
-                const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hb));
-                y = fmaf(S->vec[128 + j], h.x, y);
-                y = fmaf(S->vec[128 + j + 1], h.y, y);
-            }
-        }
-        return sqrtf(pl * pr) * __expf(y);
-    }
-
-    template <class R>
-    __device__ __forceinline__ R operator()(R rl, R ul, R pl, R rr, R ur, R pr)
-    {
-        return (R)(*this)((float)rl, (float)ul, (float)pl, (float)rr, (float)ur, (float)pr);
+        committed = anynew || any1;
+        any2 = any1;
+        any1 = anynew;
+        need2 = need1;
+        need1 = need;
+        s2 = s1;
+        s1 = need ? sqrtf(pl * pr) : 0.0f;
+        return p0;
     }
 };
 
@@ -742,6 +829,8 @@ struct Marcher {
         }
     }
 
+    // One pencil with the plain guess: a sliding window over the zones; march
+    // step kk loads zone kk and solves interface (kk-3)+1/2.
     template <class GS>
     __device__ void run(R dtdx, double dtdx64, const MethodParams &mp, Counters &cnt, GS &guess)
     {
@@ -866,6 +955,174 @@ struct Marcher {
         record(pc.n, Fu1, G1);
         update(L - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt);
     }
+
+    // One pencil with the pipelined learned guess.  March step kk loads zone kk
+    // and traces the states of interface (kk-3)+1/2; the Riemann solve, flux and
+    // update of interface jj = kk - D follow (D = 2: the traced states wait two
+    // steps in a shared-memory ring while the tensor core evaluates the
+    // network, and the pencil takes D extra drain steps).
+    template <class GS>
+    __device__ void run_piped(R dtdx, double dtdx64, const MethodParams &mp, Counters &cnt, GS &guess)
+    {
+        constexpr int D = GS::kDepth;
+        static_assert(D == 2, "the state ring holds two steps");
+        float4 *ring = guess.S->ring[0][threadIdx.x];
+        const int ring_stride = kSweepThreads * 3;     // float4 between the two slots
+        const int L = pc.L;
+        const bool fb = mp.fallback != 0;
+        Zone<R> zm2, zm1, z0;                 // zones k-2, k-1, k
+        R dprev[5], qfprev[5], sLprev[5];
+        R Fgprev[5], Fuprev2[5];
+        double Gprev2[5];                     // FP32 path: widened face term of Fuprev2
+        R rh[6];                              // FP32: raw densities of cells kk..kk-5
+        bool qh1 = false, qh2 = false;        // the ring slots hold states of interfaces 1 / 2 steps back
+        bool badprev = false;
+        _Pragma("unroll") for (int v = 0; v < 5; ++v)
+        {
+            dprev[v] = qfprev[v] = sLprev[v] = Fgprev[v] = Fuprev2[v] = (R)0;
+            Gprev2[v] = 0.0;
+        }
+        _Pragma("unroll") for (int i = 0; i < 6; ++i) rh[i] = (R)0;
+        z0 = zm1 = zm2 = Zone<R>{};
+        for (int kk = 0; kk < L + D; ++kk) {
+            bool have = false;                // states of interface (kk-3)+1/2 traced this step
+            R sLi[5], sRi[5];
+            if (kk < L) {
+                zm2 = zm1;
+                zm1 = z0;
+                z0 = zone<true>(kk, cnt);
+                if (WRAP) {
+                    const int j = kk - pc.ng;
+                    if (j == 0) c0 = z0;
+                    else if (j == 1) c1 = z0;
+                    else if (j == 2) c2 = z0;
+                }
+            }
+            if (sizeof(R) == 4) {
+                _Pragma("unroll") for (int i = 5; i > 0; --i) rh[i] = rh[i - 1];
+                rh[0] = kk < L ? z0.r : (R)0;
+            }
+            if (kk < L && kk >= 2) {
+                R dcur[5];
+                _Pragma("unroll") for (int v = 0; v < 5; ++v) dcur[v] = limited_slope<R>(zv(zm2, v), zv(zm1, v), zv(z0, v));
+                if (kk >= 3) {
+                    R qfcur[5];
+                    _Pragma("unroll") for (int v = 0; v < 5; ++v)
+                        qfcur[v] = (R)0.5 * (zv(zm2, v) + zv(zm1, v)) - div6(dcur[v] - dprev[v]);
+                    if (kk >= 4) {
+                        // parabola of zone kk-2 (its edges: qfprev on the left, qfcur on the right)
+                        R pL[5], pR[5], pd[5], p6[5];
+                        _Pragma("unroll") for (int v = 0; v < 5; ++v) parabola<R>(zv(zm2, v), qfprev[v], qfcur[v], pL[v], pR[v], pd[v], p6[v]);
+                        R sR[5], sLnew[5];
+                        trace<R, -1>(pL, pR, pd, p6, zm2.u, zm2.c, dtdx, k, sR);
+                        trace<R, +1>(pL, pR, pd, p6, zm2.u, zm2.c, dtdx, k, sLnew);
+                        if (kk >= 5) {
+                            // interface (kk-3)+1/2: left state from zone kk-3, right from kk-2
+                            if (a.log) log_states(kk, sLprev, sR);
+                            have = true;
+                            _Pragma("unroll") for (int v = 0; v < 5; ++v)
+                            {
+                                sLi[v] = sLprev[v];
+                                sRi[v] = sR[v];
+                            }
+                        }
+                        _Pragma("unroll") for (int v = 0; v < 5; ++v) sLprev[v] = sLnew[v];
+                    }
+                    _Pragma("unroll") for (int v = 0; v < 5; ++v) qfprev[v] = qfcur[v];
+                }
+                _Pragma("unroll") for (int v = 0; v < 5; ++v) dprev[v] = dcur[v];
+            }
+            if (!have) {
+                _Pragma("unroll") for (int v = 0; v < 5; ++v) sLi[v] = sRi[v] = (R)1;
+            }
+            // interface jj = kk - D: its states (from the ring slot of step kk - 2,
+            // which then takes this step's states) and its starting guess;
+            // every thread of the CTA reaches the guess at the same kk
+            const R p0 = kk >= 5 ? (R)guess.pipe(have, (float)sLi[0], (float)sLi[1], (float)sLi[2], (float)sRi[0],
+                                                 (float)sRi[1], (float)sRi[2])
+                                 : (R)-1;
+            const bool hj = qh2;
+            qh2 = qh1;
+            qh1 = have;
+            float4 *slot = ring + (kk & 1) * ring_stride;
+            R sL[5], sRj[5];
+            {
+                const float4 a0 = slot[0], a1 = slot[1], a2 = slot[2];
+                sL[0] = a0.x; sL[1] = a0.y; sL[2] = a0.z; sL[3] = a0.w; sL[4] = a1.x;
+                sRj[0] = a1.y; sRj[1] = a1.z; sRj[2] = a1.w; sRj[3] = a2.x; sRj[4] = a2.y;
+                slot[0] = make_float4(sLi[0], sLi[1], sLi[2], sLi[3]);
+                slot[1] = make_float4(sLi[4], sRi[0], sRi[1], sRi[2]);
+                slot[2] = make_float4(sRi[3], sRi[4], 0.0f, 0.0f);
+            }
+            if (!hj) continue;
+            const int jj = kk - D;            // Riemann problem at interface (jj-3)+1/2
+            const RiemannOut<R> o = riemann<R>(sL[0], sL[1], sL[2], sRj[0], sRj[1], sRj[2], p0, k, cnt);
+            if (active) {
+                if (p0 > (R)0) cnt.guesses++;
+                cnt.iters += (unsigned)o.iters;
+                if (!o.conv) cnt.rare(ENZO_ST_NEWTON_NONCONV);
+            }
+            const R t1 = o.ustar >= (R)0 ? sL[3] : sRj[3];
+            const R t2 = o.ustar >= (R)0 ? sL[4] : sRj[4];
+            R Fg[5];
+            phys_flux<R>(o.rho, o.u, o.p, t1, t2, k, Fg);
+            if (jj >= 6) {
+                // cell c = jj-3: does the Godunov update leave rho > 0?
+                const int c = jj - 3;
+                bool bad = false;
+                if (fb) {
+                    if (sizeof(R) == 8) {
+                        bad = !(cell_update(rho_old(c), dtdx64, (double)Fgprev[0], (double)Fg[0]) > 0.0);
+                    } else {
+                        // FP32 screen; cells near zero are decided in FP64
+                        const R rc = rh[3 + D];
+                        const R rt = rc + dtdx * (Fgprev[0] - Fg[0]);
+                        if (!(rt > (R)1e-3 * rc)) {
+                            const double g0 = f2d_exact((float)(dtdx * Fgprev[0]));
+                            const double g1 = f2d_exact((float)(dtdx * Fg[0]));
+                            bad = !((rho_old(c) + g0) - g1 > 0.0);
+                        }
+                    }
+                    if (bad && active) cnt.rare(ENZO_ST_HLL_CELLS);
+                }
+                // final flux at face (jj-4)+1/2
+                R Fu1[5];
+                if (badprev || bad) {
+                    Counters quiet;
+                    const Zone<R> za = zone<false>(jj - 4, quiet);
+                    const Zone<R> zb = zone<false>(jj - 3, quiet);
+                    hll_flux<R>(za, zb, k, Fu1);
+                } else {
+                    _Pragma("unroll") for (int v = 0; v < 5; ++v) Fu1[v] = Fgprev[v];
+                }
+                double G1[5];
+                widen(Fu1, dtdx, G1);
+                record(jj - 6, Fu1, G1);
+                if (jj >= 7) update(jj - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt);
+                _Pragma("unroll") for (int v = 0; v < 5; ++v)
+                {
+                    Fuprev2[v] = Fu1[v];
+                    Gprev2[v] = G1[v];
+                }
+                badprev = bad;
+            }
+            _Pragma("unroll") for (int v = 0; v < 5; ++v) Fgprev[v] = Fg[v];
+        }
+        // last active cell L-4: its right face (L-4)+1/2 borders a ghost zone
+        R Fu1[5];
+        if (badprev) {
+            Counters quiet;
+            const Zone<R> za = zone<false>(L - 4, quiet);
+            const Zone<R> zb = zone<false>(L - 3, quiet);
+            hll_flux<R>(za, zb, k, Fu1);
+        } else {
+            _Pragma("unroll") for (int v = 0; v < 5; ++v) Fu1[v] = Fgprev[v];
+        }
+        double G1[5];
+        widen(Fu1, dtdx, G1);
+        record(pc.n, Fu1, G1);
+        update(L - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt);
+    }
 };
 
 __device__ __forceinline__ void warp_flush(unsigned long long *status, unsigned long long v, int word)
@@ -898,7 +1155,7 @@ __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_
     const int total = a.prefix[a.npatch];
     unsigned long long interfaces = 0;
     typename std::conditional<LEARNED, LearnedGuess, PlainGuess>::type guess;
-    if constexpr (LEARNED) guess.setup(dsmem, a.mp.mlp, (float)a.mp.gamma);
+    if constexpr (LEARNED) guess.setup(dsmem, a.mp.mlp, (float)a.mp.gamma, a.mp.mlp_gate);
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.tile_counter, 1u);
         __syncthreads();
@@ -951,10 +1208,12 @@ __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_
         }
         if (P.flags & ENZO_PATCH_PERIODIC) {
             Marcher<R, true, DIR, REG> m{a, pc, k, valid, key, reg_all, reg_bnd, dt};
-            m.run(dtdx, dtdx64, a.mp, cnt, guess);
+            if constexpr (LEARNED) m.run_piped(dtdx, dtdx64, a.mp, cnt, guess);
+            else m.run(dtdx, dtdx64, a.mp, cnt, guess);
         } else {
             Marcher<R, false, DIR, REG> m{a, pc, k, valid, key, reg_all, reg_bnd, dt};
-            m.run(dtdx, dtdx64, a.mp, cnt, guess);
+            if constexpr (LEARNED) m.run_piped(dtdx, dtdx64, a.mp, cnt, guess);
+            else m.run(dtdx, dtdx64, a.mp, cnt, guess);
         }
     }
     if constexpr (LEARNED) {

@@ -76,17 +76,28 @@ def turbulent_prims(rng, shape, mach=3.0, sigma=1.0, gamma=5.0 / 3.0, p0=1.0):
 
 
 def blast_prims(rng, shape, nblast=16, p_bg=1e-3, p_max=1e3, r_min=4, r_max=24):
+    """Blast spheres on a clipped lognormal background (density contrast 1e4,
+    pressure ratio up to p_max / p_bg), at rest.  Sphere centres, radii and
+    pressures are seeded; distances are periodic (minimum image, in cell
+    indices).  Each sphere touches only the cells of its bounding box."""
     rho = np.clip(lognormal(grf_kpow(rng, shape), 1.0), 1e-2, 1e2)
     p = np.full(shape, p_bg)
-    nz, ny, nx = shape
-    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    dims = np.array(shape)
     for _ in range(nblast):
-        c = rng.uniform(0, 1, 3) * np.array([nz, ny, nx])
+        c = rng.uniform(0, 1, 3) * dims
         r = rng.uniform(r_min, r_max)
         pb = p_max * 10.0 ** rng.uniform(-2.0, 0.0)
-        d = [np.minimum(np.abs(a - ci), s - np.abs(a - ci)) for a, ci, s in ((z, c[0], nz), (y, c[1], ny), (x, c[2], nx))]
-        inside = d[0] ** 2 + d[1] ** 2 + d[2] ** 2 <= r * r
-        p[inside] = np.maximum(p[inside], pb)
+        idx, dist = [], []
+        for a in range(3):
+            s = int(dims[a])
+            i = np.unique(np.mod(np.arange(int(np.floor(c[a] - r)), int(np.ceil(c[a] + r)) + 1), s))
+            d = np.abs(i - c[a])
+            idx.append(i)
+            dist.append(np.minimum(d, s - d))
+        inside = (dist[0][:, None, None] ** 2 + dist[1][None, :, None] ** 2 + dist[2][None, None, :] ** 2) <= r * r
+        box = np.ix_(*idx)
+        sub = p[box]
+        p[box] = np.where(inside, np.maximum(sub, pb), sub)
     zero = np.zeros(shape)
     return rho, zero, zero.copy(), zero.copy(), p
 

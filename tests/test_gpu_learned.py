@@ -70,7 +70,7 @@ def test_learned_sweep_agrees_with_plain_and_saves_iterations(trained, flags):
     plain = batch_from_patches([[f.copy() for f in U] for U in patches], dx, flags=flags)
     learn = batch_from_patches([[f.copy() for f in U] for U in patches], dx, flags=flags)
     gpu_evolve(plain, ez.Params(precision=ez.FP32), 6)
-    gpu_evolve(learn, ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob), 6)
+    gpu_evolve(learn, ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob, mlp_gate=-1.0), 6)
     for g_p, g_l in zip(gpu_patches(plain), gpu_patches(learn)):
         for e in l1_rel(g_l, g_p):
             assert e <= 1e-5
@@ -79,6 +79,30 @@ def test_learned_sweep_agrees_with_plain_and_saves_iterations(trained, flags):
     assert sl["guess_calls"] == sl["interfaces"]
     assert sl["nan"] == 0 and sl["newton_nonconv"] == 0
     assert sl["newton_iters"] < sp["newton_iters"], (sl["newton_iters"], sp["newton_iters"])
+
+
+def test_gate_keeps_the_plain_guess_on_weak_interfaces(trained):
+    """Smooth flow (k^-4 velocity, rms Mach 3): most interfaces are weak jumps
+    where the plain guess is already within a Newton step.  With the default
+    gate the learned guess is taken only at strong jumps, answers still match
+    the plain path, and the Newton count does not exceed the plain path's."""
+    U = synth.single_grid((48, 40, 32), "turbulent", config=2)
+    dx = [1.0 / 48] * 3
+    runs = {}
+    for name, p in (("plain", ez.Params(precision=ez.FP32)),
+                    ("gated", ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=trained[0].blob)),
+                    ("always", ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=trained[0].blob, mlp_gate=-1.0))):
+        b = batch_from_patches([[f.copy() for f in U]], dx, flags=ez.PATCH_PERIODIC)
+        gpu_evolve(b, p, 4)
+        runs[name] = (gpu_patches(b)[0], b.read_status())
+    for name in ("gated", "always"):
+        for e in l1_rel(runs[name][0], runs["plain"][0]):
+            assert e <= 1e-5
+    sp, sg, sa = runs["plain"][1], runs["gated"][1], runs["always"][1]
+    assert sa["guess_calls"] == sa["interfaces"]
+    assert 0 < sg["guess_calls"] < sg["interfaces"]
+    assert sg["newton_iters"] <= sp["newton_iters"]
+    assert sg["newton_iters"] <= sa["newton_iters"]
 
 
 def test_learned_guess_with_untrained_net_still_gives_plain_answers():
@@ -90,7 +114,7 @@ def test_learned_guess_with_untrained_net_still_gives_plain_answers():
     plain = batch_from_patches([[f.copy() for f in U]], dx, flags=ez.PATCH_PERIODIC)
     learn = batch_from_patches([[f.copy() for f in U]], dx, flags=ez.PATCH_PERIODIC)
     gpu_evolve(plain, ez.Params(precision=ez.FP32), 4)
-    gpu_evolve(learn, ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob), 4)
+    gpu_evolve(learn, ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob, mlp_gate=-1.0), 4)
     for e in l1_rel(gpu_patches(learn)[0], gpu_patches(plain)[0]):
         assert e <= 1e-5
     assert learn.read_status()["nan"] == 0
