@@ -39,13 +39,18 @@ def _env_int(name, default):
         return default
 
 
-def dist_init():
+def dist_init(backend=None):
+    """Process group of the replicas (RANK / WORLD_SIZE / MASTER_* from the
+    environment): NCCL with one GPU per rank, gloo on hosts without CUDA."""
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+        dist.init_process_group(backend)
     return rank, world
 
 
@@ -56,11 +61,13 @@ def barrier(world):
 
 
 def max_over_ranks(v, world):
+    """Largest value over the ranks (the slowest replica's time)."""
     if world <= 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

@@ -71,7 +71,7 @@ enum {
     ENZO_ST_BAD_PATCH = 8,    /* descriptors rejected on the device (skipped) */
     ENZO_ST_FP64_EKE = 9,     /* FP32 mode: cells whose E - KE was redone in FP64 */
     ENZO_ST_GUESS_RESTARTS = 10, /* learned guess abandoned for the plain guess */
-    ENZO_ST_GUESS_CALLS = 11, /* interfaces given a learned guess */
+    ENZO_ST_GUESS_CALLS = 11, /* interfaces given a learned guess (those past the gate) */
     ENZO_ST_TIMEOUT = 12,     /* bounded waits that ran out (tensor-core kernels) */
     ENZO_STATUS_WORDS = 16
 };

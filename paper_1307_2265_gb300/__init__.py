@@ -23,7 +23,7 @@ PATCH_PERIODIC = 1
 STATUS_WORDS = 16
 STATUS_NAMES = ("interfaces", "newton_iters", "newton_nonconv", "hll_cells", "neg_after",
                 "rho_floor_hits", "p_floor_hits", "nan", "bad_patch", "fp64_eke",
-                "guess_restarts", "guess_calls")
+                "guess_restarts", "guess_calls", "timeout")
 
 PATCH_DTYPE = np.dtype([("n", "<i4", (3,)), ("ng", "<i4"), ("off", "<i8"), ("dx", "<f8", (3,)),
                         ("level", "<i4"), ("flags", "<i4"), ("freg_all", "<i8"), ("freg_bnd", "<i8")])

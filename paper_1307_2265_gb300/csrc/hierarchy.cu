@@ -124,15 +124,13 @@ struct InterpArgs {
     int nbox;
 };
 
-// Ghost cells of the listed boxes get the parent's SecondOrderA value (one warp
+// Ghost cells of the listed boxes get the parent's SecondOrderA value (one CTA
 // per box: boxes are the 3-cell-thick face, edge and corner slabs of a patch's
 // ghost shell; cells that siblings cover are copied afterwards and not listed).
 template <class T>
-__global__ void __launch_bounds__(256) interp_ghosts_kernel(const __grid_constant__ InterpArgs a)
+__global__ void __launch_bounds__(128) interp_ghosts_kernel(const __grid_constant__ InterpArgs a)
 {
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); bi < a.nbox; bi += warps) {
+    for (int bi = blockIdx.x; bi < a.nbox; bi += gridDim.x) {
         const enzo_copy_box B = a.boxes[bi];
         const enzo_patch P = a.fine[B.dst];
         const enzo_patch_link L = a.flink[B.dst];
@@ -144,7 +142,7 @@ __global__ void __launch_bounds__(256) interp_ghosts_kernel(const __grid_constan
         const int N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng;
         const int M0 = PP.n[0] + 2 * PP.ng, M1 = PP.n[1] + 2 * PP.ng;
         const T w = (T)a.w;
-        for (int c = lane; c < vol; c += 32) {
+        for (int c = threadIdx.x; c < vol; c += blockDim.x) {
             const int gz = c / e01, rem = c - gz * e01, gy = rem / e0;
             const int g[3] = {B.lo[0] + rem - gy * e0, B.lo[1] + gy, B.lo[2] + gz};
             int kid[3], ps[3];
@@ -175,21 +173,17 @@ __global__ void __launch_bounds__(256) interp_ghosts_kernel(const __grid_constan
     }
 }
 
-// Ghost boxes copied from siblings: one warp per box (boxes are small: the
-// face, edge and corner slabs of a patch's ghost shell).  Each lane loads the
-// five fields of up to kCopyUnroll cells before storing any, so that enough
-// loads are in flight to cover HBM latency (sources are active cells, which
-// this kernel never writes).
-constexpr int kCopyUnroll = 2;
-
-__global__ void __launch_bounds__(256, 4) copy_boxes_kernel(const enzo_patch *pt, const enzo_patch_link *lk,
+// Ghost boxes copied from siblings: one CTA per box (boxes are the face, edge
+// and corner slabs of a patch's ghost shell, 27 to a few thousand cells).
+// Each thread loads the five fields of two cells before storing any, so that
+// enough loads are in flight to cover HBM latency (sources are active cells,
+// which this kernel never writes).
+__global__ void __launch_bounds__(128) copy_boxes_kernel(const enzo_patch *pt, const enzo_patch_link *lk,
                                                          double *U0, double *U1, double *U2, double *U3,
                                                          double *U4, const enzo_copy_box *boxes, int nbox)
 {
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
     double *const U[5] = {U0, U1, U2, U3, U4};
-    for (int bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); bi < nbox; bi += warps) {
+    for (int bi = blockIdx.x; bi < nbox; bi += gridDim.x) {
         const enzo_copy_box B = boxes[bi];
         const enzo_patch D = pt[B.dst], S = pt[B.src];
         const enzo_patch_link DL = lk[B.dst], SL = lk[B.src];
@@ -202,12 +196,12 @@ __global__ void __launch_bounds__(256, 4) copy_boxes_kernel(const enzo_patch *pt
                               (int64_t)D01 * (B.lo[2] - DL.origin[2] + D.ng);
         const int64_t sbase = S.off + (B.lo[0] - SL.origin[0] + S.ng) + (int64_t)S0 * (B.lo[1] - SL.origin[1] + S.ng) +
                               (int64_t)S01 * (B.lo[2] - SL.origin[2] + S.ng);
-        for (int c0 = 0; c0 < vol; c0 += 32 * kCopyUnroll) {
-            int64_t di[kCopyUnroll], si[kCopyUnroll];
-            double v[kCopyUnroll][5];
+        for (int c0 = 0; c0 < vol; c0 += 2 * blockDim.x) {
+            int64_t di[2], si[2];
+            double v[2][5];
 #pragma unroll
-            for (int k = 0; k < kCopyUnroll; ++k) {
-                const int c = c0 + lane + 32 * k;
+            for (int k = 0; k < 2; ++k) {
+                const int c = c0 + threadIdx.x + k * blockDim.x;
                 const int z = c / e01, rem = c - z * e01;
                 const int y = rem / e0, x = rem - y * e0;
                 di[k] = c < vol ? dbase + x + (int64_t)D0 * y + (int64_t)D01 * z : -1;
@@ -217,7 +211,7 @@ __global__ void __launch_bounds__(256, 4) copy_boxes_kernel(const enzo_patch *pt
                     for (int f = 0; f < 5; ++f) v[k][f] = U[f][si[k]];
             }
 #pragma unroll
-            for (int k = 0; k < kCopyUnroll; ++k)
+            for (int k = 0; k < 2; ++k)
                 if (di[k] >= 0)
 #pragma unroll
                     for (int f = 0; f < 5; ++f) U[f][di[k]] = v[k][f];
@@ -322,6 +316,7 @@ struct ProjArgs {
     int nfine;
 };
 
+// One CTA per fine patch: its covered coarse cells get the mean of their 8 children.
 __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ ProjArgs a)
 {
     for (int pi = blockIdx.x; pi < a.nfine; pi += gridDim.x) {
@@ -367,18 +362,6 @@ static int sm_count()
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
     return s > 0 ? s : 1;
-}
-
-// Grid of at most `want` CTAs that the SMs hold at once (grid-stride kernels:
-// CTAs beyond the resident set would only start after the first wave ends).
-template <class K>
-static int resident_grid(K kernel, int threads, int64_t want)
-{
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    const int64_t cap = (int64_t)sm_count() * per_sm;
-    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
 static bool batch_ok(const enzo_patch_batch *b)
@@ -427,16 +410,16 @@ int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *f
         a.w = w;
         a.boxes = interp_boxes;
         a.nbox = ninterp;
-        const int64_t want = (ninterp + 7) / 8;
-        if (precision == ENZO_FP64)
-            interp_ghosts_kernel<double><<<resident_grid(interp_ghosts_kernel<double>, 256, want), 256, 0, s>>>(a);
-        else
-            interp_ghosts_kernel<float><<<resident_grid(interp_ghosts_kernel<float>, 256, want), 256, 0, s>>>(a);
+        // one CTA per box (boxes are short; a grid-stride over a resident grid
+        // measured slower)
+        const int grid = ninterp < sm_count() * 16 ? ninterp : sm_count() * 16;
+        if (precision == ENZO_FP64) interp_ghosts_kernel<double><<<grid, 128, 0, s>>>(a);
+        else interp_ghosts_kernel<float><<<grid, 128, 0, s>>>(a);
         note_launch();
         if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
     }
     if (ncopy > 0) {
-        copy_boxes_kernel<<<resident_grid(copy_boxes_kernel, 256, (ncopy + 7) / 8), 256, 0, s>>>(
+        copy_boxes_kernel<<<ncopy, 128, 0, s>>>(
             fine->patches, fine_links, fine->U[0], fine->U[1], fine->U[2], fine->U[3], fine->U[4], copy_boxes,
             ncopy);
         note_launch();
@@ -486,7 +469,7 @@ int enzo_project(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_l
     a.fp = fine->patches;
     a.fl = fine_links;
     a.nfine = fine->npatch;
-    project_kernel<<<resident_grid(project_kernel, 256, fine->npatch), 256, 0,
+    project_kernel<<<fine->npatch, 256, 0,
                      static_cast<cudaStream_t>(coarse->stream)>>>(a);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;

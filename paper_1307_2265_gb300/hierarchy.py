@@ -54,33 +54,48 @@ def _to_dev(arr, device):
 
 
 class _Grid:
-    """Patch lookup of a level tiled by the tensor product of per-axis segments."""
+    """Patch lookup of a level: patches start at per-axis start positions, and a
+    dense table over the start indices maps each start corner to its patch."""
 
     def __init__(self, n, origin):
         self.n, self.origin = np.asarray(n), np.asarray(origin)
         self.starts = [np.unique(self.origin[:, a]) for a in range(3)]
-        self.index = {}
-        for i, o in enumerate(self.origin):
-            self.index[tuple(int(v) for v in o)] = i
+        k = [np.searchsorted(self.starts[a], self.origin[:, a]) for a in range(3)]
+        self.cube = np.full([len(st) for st in self.starts], -1, dtype=np.int64)
+        self.cube[k[0], k[1], k[2]] = np.arange(len(self.origin))
 
-    def seg(self, a, x):
-        """Index of the segment of axis a containing coordinate x, or -1."""
-        k = int(np.searchsorted(self.starts[a], x, side="right")) - 1
-        return k
+    def find_many(self, g):
+        """Patch whose active box contains each global cell g[m] (array [M, 3]), or -1."""
+        g = np.asarray(g).reshape(-1, 3)
+        k = [np.searchsorted(self.starts[a], g[:, a], side="right") - 1 for a in range(3)]
+        ok = (k[0] >= 0) & (k[1] >= 0) & (k[2] >= 0)
+        i = np.full(len(g), -1, dtype=np.int64)
+        i[ok] = self.cube[k[0][ok], k[1][ok], k[2][ok]]
+        hit = i >= 0
+        lo, hi = self.origin[i[hit]], self.origin[i[hit]] + self.n[i[hit]]
+        inside = np.all((lo <= g[hit]) & (g[hit] < hi), axis=1)
+        i[np.flatnonzero(hit)[~inside]] = -1
+        return i
 
     def find(self, g):
         """Patch whose active box contains global cell g, or -1."""
-        key = []
-        for a in range(3):
-            k = self.seg(a, g[a])
-            if k < 0:
-                return -1
-            key.append(int(self.starts[a][k]))
-        i = self.index.get(tuple(key), -1)
-        if i < 0:
-            return -1
-        lo, hi = self.origin[i], self.origin[i] + self.n[i]
-        return i if np.all((lo <= g) & (g < hi)) else -1
+        return int(self.find_many(np.asarray(g)[None, :])[0])
+
+
+_DIRS = np.array([(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                  if (dx, dy, dz) != (0, 0, 0)])
+
+
+def _probe(lo, hi, d):
+    """Cell just outside the active box [lo, hi) in direction d (per patch)."""
+    return np.where(d < 0, lo - 1, np.where(d > 0, hi, lo))
+
+
+def _boxes(dst, src, blo, bhi):
+    t = np.zeros(len(dst), dtype=BOX_DTYPE)
+    t["dst"], t["src"] = dst, src
+    t["lo"], t["hi"] = blo, bhi
+    return t
 
 
 def sibling_boxes(n, origin):
@@ -89,33 +104,19 @@ def sibling_boxes(n, origin):
     neighbours across faces, edges and corners can meet a patch's ghost region."""
     n, origin = np.asarray(n), np.asarray(origin)
     grid = _Grid(n, origin)
-    boxes = []
-    for a in range(len(n)):
-        lo, hi = origin[a], origin[a] + n[a]
-        glo, ghi = lo - NG, hi + NG
-        seen = set()
-        for dz in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dx in (-1, 0, 1):
-                    if dx == dy == dz == 0:
-                        continue
-                    probe = np.array([lo[0] - 1 if dx < 0 else (hi[0] if dx > 0 else lo[0]),
-                                      lo[1] - 1 if dy < 0 else (hi[1] if dy > 0 else lo[1]),
-                                      lo[2] - 1 if dz < 0 else (hi[2] if dz > 0 else lo[2])])
-                    b = grid.find(probe)
-                    if b < 0 or b in seen:
-                        continue
-                    seen.add(b)
-                    blo = np.maximum(glo, origin[b])
-                    bhi = np.minimum(ghi, origin[b] + n[b])
-                    if np.all(blo < bhi):
-                        boxes.append((a, int(b), *blo.tolist(), *bhi.tolist()))
-    t = np.zeros(len(boxes), dtype=BOX_DTYPE)
-    for i, bx in enumerate(boxes):
-        t[i]["dst"], t[i]["src"] = bx[0], bx[1]
-        t[i]["lo"] = bx[2:5]
-        t[i]["hi"] = bx[5:8]
-    return t
+    lo, hi = origin, origin + n
+    P = len(n)
+    pairs = []
+    for d in _DIRS:
+        b = grid.find_many(_probe(lo, hi, d))
+        a = np.flatnonzero(b >= 0)
+        pairs.append(np.stack([a, b[a]], axis=1))
+    pairs = np.unique(np.concatenate(pairs), axis=0) if P else np.zeros((0, 2), dtype=np.int64)
+    a, b = pairs[:, 0], pairs[:, 1]
+    blo = np.maximum(lo[a] - NG, origin[b])
+    bhi = np.minimum(hi[a] + NG, origin[b] + n[b])
+    keep = np.all(blo < bhi, axis=1)
+    return _boxes(a[keep], b[keep], blo[keep], bhi[keep])
 
 
 def interp_boxes(n, origin):
@@ -123,31 +124,22 @@ def interp_boxes(n, origin):
     sibling covers; these are interpolated from the parent."""
     n, origin = np.asarray(n), np.asarray(origin)
     grid = _Grid(n, origin)
-    boxes = []
-    for a in range(len(n)):
-        lo, hi = origin[a], origin[a] + n[a]
-        for dz in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dx in (-1, 0, 1):
-                    if dx == dy == dz == 0:
-                        continue
-                    dd = (dx, dy, dz)
-                    blo = np.array([lo[t] - NG if dd[t] < 0 else (hi[t] if dd[t] > 0 else lo[t]) for t in range(3)])
-                    bhi = np.array([lo[t] if dd[t] < 0 else (hi[t] + NG if dd[t] > 0 else hi[t]) for t in range(3)])
-                    probe = np.array([lo[t] - 1 if dd[t] < 0 else (hi[t] if dd[t] > 0 else lo[t]) for t in range(3)])
-                    if grid.find(probe) >= 0:
-                        # a sibling touches this region; it must then cover all of it
-                        corner = np.array([bhi[t] - 1 if dd[t] >= 0 else blo[t] for t in range(3)])
-                        if grid.find(corner) < 0:
-                            raise ValueError("ghost region partly covered by siblings")
-                        continue
-                    boxes.append((a, a, *blo.tolist(), *bhi.tolist()))
-    t = np.zeros(len(boxes), dtype=BOX_DTYPE)
-    for i, bx in enumerate(boxes):
-        t[i]["dst"], t[i]["src"] = bx[0], bx[1]
-        t[i]["lo"] = bx[2:5]
-        t[i]["hi"] = bx[5:8]
-    return t
+    lo, hi = origin, origin + n
+    out = []
+    for d in _DIRS:
+        blo = np.where(d < 0, lo - NG, np.where(d > 0, hi, lo))
+        bhi = np.where(d < 0, lo, np.where(d > 0, hi + NG, hi))
+        touched = grid.find_many(_probe(lo, hi, d)) >= 0
+        # a sibling touching a region must cover all of it (tensor-product tiling)
+        corner = np.where(d >= 0, bhi - 1, blo)
+        if np.any(grid.find_many(corner[touched]) < 0):
+            raise ValueError("ghost region partly covered by siblings")
+        a = np.flatnonzero(~touched)
+        out.append((a, blo[a], bhi[a]))
+    a = np.concatenate([o[0] for o in out])
+    order = np.argsort(a, kind="stable")
+    return _boxes(a[order], a[order], np.concatenate([o[1] for o in out])[order],
+                  np.concatenate([o[2] for o in out])[order])
 
 
 def correction_faces(fine, coarse, r=2):
@@ -157,28 +149,25 @@ def correction_faces(fine, coarse, r=2):
     cn, co = np.asarray(coarse["n"]), np.asarray(coarse["origin"])
     fgrid = _Grid(fn, fo)
     cgrid = _Grid(cn, co)
-    faces = []
-    for i in range(len(fn)):
-        for d in range(3):
-            for side in (0, 1):
-                probe = fo[i].copy()
-                probe[d] = fo[i][d] - 1 if side == 0 else fo[i][d] + fn[i][d]
-                if fgrid.find(probe) >= 0:
-                    continue
-                cell = probe // r
-                t = cgrid.find(cell)
-                if t < 0:
-                    raise ValueError("coarse cell outside a fine face is not in a coarse patch")
-                last = cell.copy()
-                for a in range(3):
-                    if a != d:
-                        last[a] = (fo[i][a] + fn[i][a]) // r - 1
-                if not np.all((co[t] <= last) & (last < co[t] + cn[t])):
-                    raise ValueError("a fine face spans more than one coarse patch")
-                faces.append((i, d, side, t))
-    t = np.zeros(len(faces), dtype=FACE_DTYPE)
-    for k, f in enumerate(faces):
-        t[k] = f
+    cols = []
+    for d in range(3):
+        for side in (0, 1):
+            probe = fo.copy()
+            probe[:, d] = fo[:, d] - 1 if side == 0 else fo[:, d] + fn[:, d]
+            i = np.flatnonzero(fgrid.find_many(probe) < 0)
+            cell = probe[i] // r
+            t = cgrid.find_many(cell)
+            if np.any(t < 0):
+                raise ValueError("coarse cell outside a fine face is not in a coarse patch")
+            last = (fo[i] + fn[i]) // r - 1
+            last[:, d] = cell[:, d]
+            if not np.all((co[t] <= last) & (last < co[t] + cn[t])):
+                raise ValueError("a fine face spans more than one coarse patch")
+            cols.append(np.stack([i, np.full_like(i, d), np.full_like(i, side), t], axis=1))
+    f = np.concatenate(cols) if cols else np.zeros((0, 4), dtype=np.int64)
+    f = f[np.lexsort((f[:, 2], f[:, 1], f[:, 0]))]
+    t = np.zeros(len(f), dtype=FACE_DTYPE)
+    t["fine"], t["dir"], t["side"], t["target"] = f[:, 0], f[:, 1], f[:, 2], f[:, 3]
     return t
 
 
