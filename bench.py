@@ -163,6 +163,26 @@ def measured_traffic(cells_per_sweep, kernel):
     return float(t["bytes_per_cell_sweep"]) * cells_per_sweep
 
 
+def issue_bound(value_mcu, sm_mhz, sms=152):
+    """The learned sweep's issue bound: warp instructions per cell-sweep from the
+    committed ncu capture (null once the kernel source changed), against 4
+    schedulers x 1 warp instruction per clock per SM at the sampled SM clock."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        with open(os.path.join(ROOT, t["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != t["source_sha256_16"]:
+                return None
+        wi = float(t["warp_instr_per_cell_sweep"])
+    except (OSError, KeyError, ValueError):
+        return None
+    peak = sms * 4 * sm_mhz * 1e6                    # warp instructions per second
+    bound = peak / (3 * wi) / 1e6                    # Mcell-updates/s at 100% issue
+    return {"warp_instr_per_cell_sweep": wi, "issue_active_ncu": t.get("issue_active"),
+            "peak_warp_instr_per_s": peak, "bound_mcell_updates_s": bound, "frac": value_mcu / bound}
+
+
 def sweep_bytes(table, flags):
     """Algorithmic HBM bytes of one sweep per direction: each pencil reads its
     cells once and writes its active cells once (5 float64 fields).  Periodic
@@ -186,12 +206,7 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(dev)
 
     # --- learned Newton guess: trained on this GPU with the library's kernels
-    t_train = time.perf_counter()
-    states = train_guess.default_training_set(gamma=GAMMA, stride=8, cap=3_000_000)
-    x, y, _ = train_guess.dataset(states, GAMMA)
-    net, train_info = train_guess.train(x, y, steps=args.train_steps)
-    train_info["wall_seconds"] = time.perf_counter() - t_train
-    del states, x, y
+    net, train_info = _train_net(args)
 
     sizes, offsets, flat = build_level(rank, args.npatch)
     table = ez.patch_table(sizes, offsets, [1.0 / 64] * 3, flags=ez.PATCH_PERIODIC)
@@ -349,6 +364,8 @@ def run_gpu(args, rank, world):
         "fp32_l1_rel_err_vs_oracle_one_step": l1,
         "clocks": clk.summary(dev),
     }
+    sm = (res["clocks"] or {}).get("sm_mhz") or 2070.0
+    res["roofline"]["issue"] = issue_bound(value / world, sm)
     return res
 
 
@@ -365,10 +382,7 @@ def run_hierarchy(args, rank, world):
     from paper_1307_2265_gb300 import synth, train_guess
     dev = _env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(dev)
-    states = train_guess.default_training_set(gamma=GAMMA, stride=8, cap=3_000_000)
-    x, y, _ = train_guess.dataset(states, GAMMA)
-    net, train_info = train_guess.train(x, y, steps=args.train_steps)
-    del states, x, y
+    net, train_info = _train_net(args)
     t0 = time.perf_counter()
     layout = synth.hierarchy_layout(args.root, [(args.root // 8, 7 * args.root // 8),
                                                 (args.root // 4, 3 * args.root // 4),
@@ -422,10 +436,15 @@ def _train_net(args):
     on interface states logged from the white-noise and turbulent recipes."""
     from paper_1307_2265_gb300 import train_guess
     t0 = time.perf_counter()
-    states = train_guess.default_training_set(gamma=GAMMA, stride=8, cap=3_000_000)
+    if args.train_set == "configs":
+        states = train_guess.config_training_set(gamma=GAMMA)
+    else:
+        states = train_guess.default_training_set(gamma=GAMMA, stride=8, cap=3_000_000)
     x, y, _ = train_guess.dataset(states, GAMMA)
-    net, info = train_guess.train(x, y, steps=args.train_steps)
+    del states
+    net, info = train_guess.train(x, y, steps=args.train_steps, batch=args.train_batch)
     info["wall_seconds"] = time.perf_counter() - t0
+    info["set"] = args.train_set
     return net, info
 
 
@@ -620,7 +639,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work in the CPU leg")
     ap.add_argument("--sample-patches", type=int, default=6)
-    ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--train-steps", type=int, default=6000)
+    ap.add_argument("--train-batch", type=int, default=16384)
+    ap.add_argument("--train-set", default="configs", choices=["small", "configs"],
+                    help="small: ~3e6 states from reduced grids (fast); configs: ~1e8 states from the "
+                         "full-size 32^3 and 256^3 single-grid recipes")
     ap.add_argument("--workload", default="level", choices=["level", "hierarchy", "turbulence", "blast"])
     ap.add_argument("--mlp-gate", type=float, default=0.0, help="jump-strength gate of the learned guess "
                     "(0: library default 0.03, < 0: learned guess at every interface)")

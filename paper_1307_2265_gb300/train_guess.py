@@ -86,3 +86,26 @@ def default_training_set(gamma=5.0 / 3.0, device="cuda", stride=16, cap=4_000_00
         b = PatchBatch(table, [f.ravel() for f in U], device=device)
         out.append(log_states(b, Params(gamma=gamma, precision=FP32), steps, stride, cap))
     return torch.cat(out, dim=0)
+
+
+def config_training_set(gamma=5.0 / 3.0, device="cuda", target=100_000_000):
+    """About `target` states logged from the two single-grid recipes at their
+    full sizes: the 32^3 white-noise grid (rms Mach 1, 10 steps, every
+    interface) and the 256^3 k^-4 turbulent grid (rms Mach 3, 20 steps, every
+    stride-th interface so that the total comes near the target)."""
+    import torch
+    out = []
+    U = synth.single_grid((32, 32, 32), "white", config=1, gamma=gamma)
+    b = PatchBatch(patch_table([(32, 32, 32)], [0], [1.0 / 32] * 3, flags=1), [f.ravel() for f in U], device=device)
+    out.append(log_states(b, Params(gamma=gamma, precision=FP32), 10, 1, 4_000_000))
+    del b
+    n, steps = 256, 20
+    per_run = 3 * steps * (n + 1) * n * n
+    stride = max(1, per_run // max(1, target - out[0].shape[0]))
+    U = synth.single_grid((n, n, n), "turbulent", config=2, gamma=gamma)
+    b = PatchBatch(patch_table([(n, n, n)], [0], [1.0 / n] * 3, flags=1), [f.ravel() for f in U], device=device)
+    del U
+    out.append(log_states(b, Params(gamma=gamma, precision=FP32), steps, stride, int(1.2 * per_run / stride) + 1024))
+    del b
+    torch.cuda.empty_cache()
+    return torch.cat(out, dim=0)
