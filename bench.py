@@ -625,8 +625,22 @@ def cpu_baseline_leg(flat, sizes, offsets, gpu_fields_after_one_step=None, budge
                 gpu_fields_after_one_step["l1_den"][f] += float(np.sum(np.abs(a)))
         i += 1
     el = time.perf_counter() - t0
-    return {"value": cells / el / 1e6, "unit": "Mcell-updates/s", "cores": oracle.num_threads(),
-            "kind": "oracle", "sample": f"first {i} patches of the level, one step each ({cells} cells, {el:.1f} s)"}
+    cores = oracle.num_threads()
+    # the same oracle on one thread, on the first patches, for a fifth of the budget
+    oracle.set_num_threads(1)
+    t1 = time.perf_counter()
+    cells1, j = 0, 0
+    while time.perf_counter() - t1 < budget_s / 5 and j < len(sizes):
+        U = [synth.patch_view(f, offsets[j], sizes[j]).copy() for f in flat]
+        oracle.step_periodic(U, dx, gpu_fields_after_one_step["dt"], 0, P)
+        cells1 += int(np.prod(sizes[j]))
+        j += 1
+    el1 = time.perf_counter() - t1
+    oracle.set_num_threads(cores)
+    return {"value": cells / el / 1e6, "unit": "Mcell-updates/s", "cores": cores,
+            "kind": "oracle", "sample": f"first {i} patches of the level, one step each ({cells} cells, {el:.1f} s)",
+            "single_thread": {"value": cells1 / el1 / 1e6, "cores": 1,
+                              "sample": f"first {j} patches, one step each ({cells1} cells, {el1:.1f} s)"}}
 
 
 def main():

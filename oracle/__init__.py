@@ -103,6 +103,8 @@ def lib():
             L.or_pencil_debug.restype = ctypes.c_int
             L.or_num_threads.argtypes = []
             L.or_num_threads.restype = ctypes.c_int
+            L.or_set_num_threads.argtypes = [ctypes.c_int]
+            L.or_set_num_threads.restype = None
         return _lib
 
 
@@ -248,3 +250,8 @@ def pencil_debug(Upen, dtdx, params: Params, ng=3) -> dict:
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's pencil loops (timing only)."""
+    lib().or_set_num_threads(int(n))

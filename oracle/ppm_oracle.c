@@ -729,3 +729,14 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the pencil loops (timing only: results do not depend on it). */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
