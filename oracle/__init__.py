@@ -101,6 +101,11 @@ def lib():
             L.or_pencil_debug.argtypes = [ctypes.c_int32, ctypes.c_int32, _D, ctypes.c_double,
                                           ctypes.POINTER(OrParams)] + [_D] * 7 + [ctypes.POINTER(OrStats)]
             L.or_pencil_debug.restype = ctypes.c_int
+            L.or_fill_boundary.argtypes = five + [_I32, ctypes.c_int32, _I32]
+            L.or_fill_boundary.restype = None
+            L.or_step_boundary.argtypes = five + [_I32, ctypes.c_int32, _D, ctypes.c_double, ctypes.c_int32,
+                                                  _I32, ctypes.POINTER(OrParams), ctypes.POINTER(OrStats)]
+            L.or_step_boundary.restype = ctypes.c_int
             L.or_num_threads.argtypes = []
             L.or_num_threads.restype = ctypes.c_int
             L.or_set_num_threads.argtypes = [ctypes.c_int]
@@ -134,6 +139,29 @@ def fill_periodic(U, ng=3):
     n = _n_of(U, ng)
     na, npn = _i32(n)
     lib().or_fill_periodic(*_fields(U), npn, ng)
+
+
+BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
+
+
+def fill_boundary(U, bc, ng=3):
+    """External boundaries of a single grid, bc = (bc_x, bc_y, bc_z)."""
+    na, npn = _i32(_n_of(U, ng))
+    ba, bp = _i32(bc)
+    lib().or_fill_boundary(*_fields(U), npn, ng, bp)
+
+
+def step_boundary(U, dx, dt, step, bc, params: Params, ng=3) -> dict:
+    """One step of a single grid with external boundaries bc (ghosts refilled first)."""
+    na, npn = _i32(_n_of(U, ng))
+    ba, bp = _i32(bc)
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    p = params.c()
+    st = OrStats()
+    r = lib().or_step_boundary(*_fields(U), npn, ng, _dp(dxa), dt, step, bp, ctypes.byref(p), ctypes.byref(st))
+    if r:
+        raise MemoryError("oracle step could not allocate pencil scratch")
+    return st.as_dict()
 
 
 def cfl_rate(U, dx, params: Params, ng=3) -> float:

@@ -501,6 +501,47 @@ void or_fill_periodic(double *U0, double *U1, double *U2, double *U3, double *U4
             }
 }
 
+/* External boundaries of a single grid (Sec. 3.1: reflecting, outflow or
+ * periodic).  Axes are filled in turn, x then y then z, each over the full
+ * extent of the other two axes, so edges and corners take both conditions.
+ * Layer g = 1..ng outside the face:
+ *   periodic:   the active cell n - g (left) / g - 1 (right) of the same axis
+ *               (taken modulo n);
+ *   reflecting: the mirror image about the face, active cell g - 1 (left) /
+ *               n - g (right), with the momentum along the axis negated
+ *               (needs n >= ng along that axis);
+ *   outflow:    the boundary cell itself (zero gradient). */
+void or_fill_boundary(double *U0, double *U1, double *U2, double *U3, double *U4,
+                      const int32_t n[3], int32_t ng, const int32_t bc[3])
+{
+    double *U[5] = { U0, U1, U2, U3, U4 };
+    int N[3] = { n[0] + 2 * ng, n[1] + 2 * ng, n[2] + 2 * ng };
+    for (int d = 0; d < 3; ++d) {
+        for (int k = 0; k < N[2]; ++k)
+            for (int j = 0; j < N[1]; ++j)
+                for (int i = 0; i < N[0]; ++i) {
+                    int a[3] = { i, j, k };
+                    int x = a[d] - ng;                    /* active index along d */
+                    if (x >= 0 && x < n[d]) continue;
+                    int src;
+                    double sign = 1.0;
+                    if (bc[d] == 0) {                     /* periodic */
+                        src = ((x % n[d]) + n[d]) % n[d];
+                    } else if (bc[d] == 1) {              /* reflecting */
+                        src = x < 0 ? -x - 1 : 2 * n[d] - x - 1;
+                        sign = -1.0;
+                    } else {                              /* outflow */
+                        src = x < 0 ? 0 : n[d] - 1;
+                    }
+                    int b[3] = { i, j, k };
+                    b[d] = src + ng;
+                    int64_t dst = idx3(N, i, j, k), sidx = idx3(N, b[0], b[1], b[2]);
+                    for (int v = 0; v < 5; ++v) U[v][dst] = U[v][sidx];
+                    U[1 + d][dst] = sign * U[1 + d][sidx];
+                }
+    }
+}
+
 /* Level timestep (Sec. 9): dt = cfl / max over active cells of
  * sum_d (c_s + |v_d|) / dx_d, with c_s = sqrt(gamma p / rho), a = 1.
  * Returns the max of the sum (the caller divides), so patches can be combined. */
@@ -619,6 +660,32 @@ void or_sweep_order(int32_t step, int32_t order[3])
 {
     if (step % 2 == 0) { order[0] = 0; order[1] = 1; order[2] = 2; }
     else               { order[0] = 2; order[1] = 1; order[2] = 0; }
+}
+
+/* One full step of a single grid with external boundaries bc[3] (as in
+ * or_fill_boundary): ghost fill, then the three split sweeps with transverse
+ * coverage. */
+int or_step_boundary(double *U0, double *U1, double *U2, double *U3, double *U4,
+                     const int32_t n[3], int32_t ng, const double dx[3], double dt,
+                     int32_t step, const int32_t bc[3], const or_params *P, or_stats *stats)
+{
+    int32_t order[3];
+    or_sweep_order(step, order);
+    or_fill_boundary(U0, U1, U2, U3, U4, n, ng, bc);
+    int N[3] = { n[0] + 2 * ng, n[1] + 2 * ng, n[2] + 2 * ng };
+    int done[3] = { 0, 0, 0 };
+    for (int q = 0; q < 3; ++q) {
+        int d = order[q];
+        int32_t lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            if (done[a]) { lo[a] = ng; hi[a] = ng + n[a]; }
+            else         { lo[a] = 0;  hi[a] = N[a]; }
+        }
+        int r = or_sweep(U0, U1, U2, U3, U4, n, ng, dx, d, dt, lo, hi, P, stats);
+        if (r) return r;
+        done[d] = 1;
+    }
+    return 0;
 }
 
 /* One full step of a periodic patch: ghost fill, then three split sweeps with
