@@ -208,6 +208,23 @@ int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, double dt, in
  * are left alone (their sweeps wrap). */
 int enzo_ghost_fill_periodic(const enzo_patch_batch *b);
 
+/* External boundary conditions of a grid (Sec. 3.1 lists reflecting, outflow,
+ * inflow and periodic; inflow is not provided). */
+enum {
+    ENZO_BC_PERIODIC = 0, /* ghost layer g copies the active cell g back from the far face */
+    ENZO_BC_REFLECT = 1,  /* mirror image about the face, momentum along the axis negated;
+                             needs n >= 3 along that axis (smaller patches get the mirror
+                             folded back into the patch) */
+    ENZO_BC_OUTFLOW = 2   /* zero gradient: the boundary cell is copied outward */
+};
+
+/* Ghost fill of every non-periodic patch as a single grid with external
+ * boundaries bc[3] (HOST array: condition along x, y, z; Sec. 3.1).  Edges and
+ * corners take every condition that applies (as filling x, then y, then z over
+ * the full extents).  Patches flagged ENZO_PATCH_PERIODIC are left alone.
+ * Returns ENZO_ERR_ARG for a NULL bc or an unknown condition. */
+int enzo_ghost_fill_boundary(const enzo_patch_batch *b, const int32_t bc[3]);
+
 /* Level timestep of Sec. 9: dt = cfl / max over active cells of all patches of
  * sum_d (c_s + |v_d|)/dx_d, with c_s = sqrt(gamma p / rho).  The min-reduction
  * runs on the device.  dt_out: DEVICE pointer to one double when
@@ -224,6 +241,10 @@ int enzo_timestep_cfl(const enzo_patch_batch *b, const enzo_params *p, double *d
  * each step's own dt. */
 int enzo_step(const enzo_patch_batch *b, const enzo_params *p, int32_t step_index,
               const double *dt_dev);
+
+/* As enzo_step with the ghost fill of enzo_ghost_fill_boundary(bc) (HOST bc[3]). */
+int enzo_step_boundary(const enzo_patch_batch *b, const enzo_params *p, int32_t step_index,
+                       const double *dt_dev, const int32_t bc[3]);
 
 /* Riemann problems on their own (Sec. 4.1.2): n independent interfaces given
  * as SoA DEVICE arrays of left/right primitive states.  Outputs (DEVICE,

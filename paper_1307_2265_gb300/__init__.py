@@ -80,6 +80,9 @@ def lib():
             L.enzo_ghost_fill_periodic.argtypes = [ctypes.POINTER(_Batch)]
             L.enzo_timestep_cfl.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Params), vp, i32]
             L.enzo_step.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Params), i32, vp]
+            L.enzo_ghost_fill_boundary.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(i32)]
+            L.enzo_step_boundary.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Params), i32, vp,
+                                             ctypes.POINTER(i32)]
             L.enzo_riemann_solve.argtypes = [ctypes.POINTER(_Riemann), ctypes.POINTER(_Params)]
             L.enzo_strerror.argtypes = [ctypes.c_int]
             L.enzo_strerror.restype = ctypes.c_char_p
@@ -87,7 +90,8 @@ def lib():
             L.enzo_launch_count.restype = ctypes.c_ulonglong
             for name in ("enzo_validate_patches", "enzo_ppm_sweep", "enzo_ppm_sweep_dev", "enzo_ppm_sweep_noalloc",
                          "enzo_ghost_fill_periodic", "enzo_ppm_sweep_logged",
-                         "enzo_timestep_cfl", "enzo_step", "enzo_riemann_solve"):
+                         "enzo_timestep_cfl", "enzo_step", "enzo_riemann_solve",
+                         "enzo_ghost_fill_boundary", "enzo_step_boundary"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
         return _lib
@@ -253,6 +257,29 @@ def step(batch: PatchBatch, params: Params, step_index: int, dt_dev):
     """Ghost fill + three split sweeps in the order of step_index; dt read on the device."""
     b, p = batch.c(), params.c()
     _check(lib().enzo_step(ctypes.byref(b), ctypes.byref(p), step_index, dt_dev.data_ptr()), "enzo_step")
+
+
+BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
+
+
+def _bc(bc):
+    if len(bc) != 3:
+        raise ValueError("bc needs one condition per axis")
+    return (ctypes.c_int32 * 3)(*[int(v) for v in bc])
+
+
+def ghost_fill_boundary(batch: PatchBatch, bc):
+    """Ghost fill of each non-periodic patch as a grid with external boundaries
+    bc = (bc_x, bc_y, bc_z), each BC_PERIODIC, BC_REFLECT or BC_OUTFLOW."""
+    b = batch.c()
+    _check(lib().enzo_ghost_fill_boundary(ctypes.byref(b), _bc(bc)), "enzo_ghost_fill_boundary")
+
+
+def step_boundary(batch: PatchBatch, params: Params, step_index: int, dt_dev, bc):
+    """As step(), with the external boundaries bc of ghost_fill_boundary()."""
+    b, p = batch.c(), params.c()
+    _check(lib().enzo_step_boundary(ctypes.byref(b), ctypes.byref(p), step_index, dt_dev.data_ptr(), _bc(bc)),
+           "enzo_step_boundary")
 
 
 def riemann_solve(rl, ul, pl, rr, ur, pr, params: Params, pguess=None, stream=None):

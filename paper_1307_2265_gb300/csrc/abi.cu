@@ -119,6 +119,57 @@ __global__ void __launch_bounds__(kFillThreads) ghost_fill_kernel(const enzo_pat
     }
 }
 
+// External boundaries of each patch taken as a single grid (Sec. 3.1):
+// per axis periodic (wrap), reflecting (mirror about the face, momentum along
+// the axis negated) or outflow (boundary cell copied).  The three per-axis maps
+// compose, so one pass gives what filling x, then y, then z over the full
+// extents gives: edges and corners take every condition that applies.
+__device__ __forceinline__ int bc_map(int x, int n, int bc, bool &flip)
+{
+    if (x >= 0 && x < n) return x;
+    if (bc == ENZO_BC_PERIODIC) return ((x % n) + n) % n;
+    if (bc == ENZO_BC_OUTFLOW) return x < 0 ? 0 : n - 1;
+    // reflecting; for n < 3 the mirror is folded back into the patch
+    flip = true;
+    int m = ((x % (2 * n)) + 2 * n) % (2 * n);
+    return m < n ? m : 2 * n - 1 - m;
+}
+
+__global__ void __launch_bounds__(kFillThreads) boundary_fill_kernel(const enzo_patch *patches, int npatch,
+                                                                     double *U0, double *U1, double *U2,
+                                                                     double *U3, double *U4, const int *prefix,
+                                                                     int bcx, int bcy, int bcz)
+{
+    double *const U[5] = {U0, U1, U2, U3, U4};
+    const int bc[3] = {bcx, bcy, bcz};
+    const int total = prefix[npatch];
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        int lo = 0, hi = npatch;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= tile) lo = mid; else hi = mid;
+        }
+        const enzo_patch P = patches[lo];
+        const int N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng, N2 = P.n[2] + 2 * P.ng;
+        const int64_t cell = (int64_t)(tile - prefix[lo]) * kFillThreads + threadIdx.x;
+        if (cell >= (int64_t)N0 * N1 * N2) continue;
+        const int a[3] = {(int)(cell % N0), (int)((cell / N0) % N1), (int)(cell / ((int64_t)N0 * N1))};
+        bool ghost = false, flip[3] = {false, false, false};
+        int src[3];
+        for (int d = 0; d < 3; ++d) {
+            const int x = a[d] - P.ng;
+            if (x < 0 || x >= P.n[d]) ghost = true;
+            src[d] = bc_map(x, P.n[d], bc[d], flip[d]) + P.ng;
+        }
+        if (!ghost) continue;
+        const int64_t dst = P.off + cell;
+        const int64_t s = P.off + src[0] + (int64_t)N0 * (src[1] + (int64_t)N1 * src[2]);
+        U[0][dst] = U[0][s];
+        U[4][dst] = U[4][s];
+        for (int d = 0; d < 3; ++d) U[1 + d][dst] = flip[d] ? -U[1 + d][s] : U[1 + d][s];
+    }
+}
+
 __global__ void dt_finalize_kernel(const unsigned long long *rate_bits, double cfl, double *ws_dt,
                                    double *dt_out)
 {
@@ -249,6 +300,26 @@ static int fill_impl(const enzo_patch_batch *b)
     return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
 }
 
+static bool bc_ok(const int32_t *bc)
+{
+    if (!bc) return false;
+    for (int d = 0; d < 3; ++d)
+        if (bc[d] != ENZO_BC_PERIODIC && bc[d] != ENZO_BC_REFLECT && bc[d] != ENZO_BC_OUTFLOW) return false;
+    return true;
+}
+
+static int boundary_impl(const enzo_patch_batch *b, const int32_t *bc)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(b->stream);
+    int r = launch_prefix(b, kKindFill, 0, 0, false, s);
+    if (r) return r;
+    boundary_fill_kernel<<<device_sms() * 8, kFillThreads, 0, s>>>(
+        b->patches, b->npatch, b->U[0], b->U[1], b->U[2], b->U[3], b->U[4],
+        reinterpret_cast<const int *>(ws(b) + kWsPrefix), bc[0], bc[1], bc[2]);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
+}
+
 }  // namespace enzo
 
 using namespace enzo;
@@ -330,6 +401,15 @@ int enzo_ghost_fill_periodic(const enzo_patch_batch *b)
     return fill_impl(b);
 }
 
+int enzo_ghost_fill_boundary(const enzo_patch_batch *b, const int32_t bc[3])
+{
+    int r = check_batch(b);
+    if (r) return r;
+    if (!bc_ok(bc)) return ENZO_ERR_ARG;
+    if (b->npatch == 0) return ENZO_OK;
+    return boundary_impl(b, bc);
+}
+
 int enzo_timestep_cfl(const enzo_patch_batch *b, const enzo_params *p, double *dt_out,
                       int32_t dt_out_on_device)
 {
@@ -374,7 +454,8 @@ int enzo_timestep_cfl(const enzo_patch_batch *b, const enzo_params *p, double *d
     return ENZO_OK;
 }
 
-int enzo_step(const enzo_patch_batch *b, const enzo_params *p, int32_t step_index, const double *dt_dev)
+static int step_impl(const enzo_patch_batch *b, const enzo_params *p, int32_t step_index, const double *dt_dev,
+                     const int32_t *bc)
 {
     int r = check_batch(b);
     if (r) return r;
@@ -382,9 +463,10 @@ int enzo_step(const enzo_patch_batch *b, const enzo_params *p, int32_t step_inde
     r = resolve(p, m);
     if (r) return r;
     if (!dt_dev || step_index < 0) return ENZO_ERR_ARG;
+    if (bc && !bc_ok(bc)) return ENZO_ERR_ARG;
     if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
     if (b->npatch == 0) return ENZO_OK;
-    r = fill_impl(b);
+    r = bc ? boundary_impl(b, bc) : fill_impl(b);
     if (r) return r;
     const int order[2][3] = {{0, 1, 2}, {2, 1, 0}};
     int done = 0;
@@ -396,6 +478,18 @@ int enzo_step(const enzo_patch_batch *b, const enzo_params *p, int32_t step_inde
         done |= 1 << d;
     }
     return ENZO_OK;
+}
+
+int enzo_step(const enzo_patch_batch *b, const enzo_params *p, int32_t step_index, const double *dt_dev)
+{
+    return step_impl(b, p, step_index, dt_dev, nullptr);
+}
+
+int enzo_step_boundary(const enzo_patch_batch *b, const enzo_params *p, int32_t step_index,
+                       const double *dt_dev, const int32_t bc[3])
+{
+    if (!bc) return ENZO_ERR_ARG;
+    return step_impl(b, p, step_index, dt_dev, bc);
 }
 
 int enzo_riemann_solve(const enzo_riemann_states *st, const enzo_params *p)

@@ -83,3 +83,16 @@ def test_validate_patches_ranges():
 def test_patch_struct_layout_matches_header():
     assert ez.PATCH_DTYPE.itemsize == 72
     assert ctypes.sizeof(ez._Batch) == 4 + 4 + 8 + 8 + 40 + 8 + 8 + 8 + 8 + 8
+
+
+def test_boundary_conditions_rejected_without_gpu():
+    L = ez.lib()
+    b = ez._Batch()
+    b.npatch = 0
+    bad = (ctypes.c_int32 * 3)(0, 7, 0)
+    good = (ctypes.c_int32 * 3)(ez.BC_REFLECT, ez.BC_OUTFLOW, ez.BC_PERIODIC)
+    assert L.enzo_ghost_fill_boundary(ctypes.byref(b), bad) == -1
+    assert L.enzo_ghost_fill_boundary(ctypes.byref(b), None) == -1
+    assert L.enzo_ghost_fill_boundary(ctypes.byref(b), good) == 0       # empty batch: no-op
+    p = ez.Params().c()
+    assert L.enzo_step_boundary(ctypes.byref(b), ctypes.byref(p), 0, None, good) == -1   # no dt
