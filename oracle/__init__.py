@@ -41,7 +41,8 @@ def build(force: bool = False) -> str:
 class OrParams(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("rho_floor", ctypes.c_double),
                 ("p_floor", ctypes.c_double), ("newton_tol", ctypes.c_double),
-                ("newton_max", ctypes.c_int32), ("fallback", ctypes.c_int32)]
+                ("newton_max", ctypes.c_int32), ("fallback", ctypes.c_int32),
+                ("solver", ctypes.c_int32)]
 
 
 class OrStats(ctypes.Structure):
@@ -61,10 +62,11 @@ class Params:
     newton_tol: float = 1e-14
     newton_max: int = 20
     fallback: int = 1
+    solver: int = 0          # interface fluxes: 0 two-shock, 1 HLL, 2 HLLC
 
     def c(self) -> OrParams:
         return OrParams(self.gamma, self.rho_floor, self.p_floor, self.newton_tol,
-                        self.newton_max, self.fallback)
+                        self.newton_max, self.fallback, self.solver)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -246,14 +248,18 @@ def riemann(rl, ul, pl, rr, ur, pr, params: Params, pguess=None):
     return dict(pstar=outs[0], ustar=outs[1], rho=outs[2], u=outs[3], p=outs[4], iters=it)
 
 
+SOLVER_TWOSHOCK, SOLVER_HLL, SOLVER_HLLC = 0, 1, 2
+
+
 def flux(left, right, params: Params, solver="twoshock"):
-    """Fluxes for primitive states left/right = (rho, u, p, ut1, ut2) arrays."""
+    """Fluxes for primitive states left/right = (rho, u, p, ut1, ut2) arrays;
+    solver "twoshock", "hll" or "hllc"."""
     L = [np.ascontiguousarray(a, dtype=np.float64) for a in left]
     R = [np.ascontiguousarray(a, dtype=np.float64) for a in right]
     n = L[0].size
     F = np.empty((n, 5))
     p = params.c()
-    lib().or_flux_batch(n, 1 if solver == "hll" else 0, *[_dp(a) for a in L],
+    lib().or_flux_batch(n, {"twoshock": 0, "hll": 1, "hllc": 2}[solver], *[_dp(a) for a in L],
                         *[_dp(a) for a in R], ctypes.byref(p), _dp(F))
     return F
 

@@ -60,6 +60,7 @@ typedef struct {
     double newton_tol;
     int32_t newton_max;
     int32_t fallback;     /* 1: HLL re-flux of cells that reach rho <= 0 */
+    int32_t solver;       /* interface fluxes: 0 two-shock (Sec. 4.1.2), 1 HLL, 2 HLLC */
 } or_params;
 
 typedef struct {
@@ -258,6 +259,39 @@ static void hll_flux(double rl, double ul, double pl, double t1l, double t2l,
         F[c] = (SR * FL[c] - SL * FR[c] + SL * SR * (UR[c] - UL[c])) / (SR - SL);
 }
 
+/* HLLC flux (Sec. 4.1.2 names HLLC among the Riemann solvers; Toro's
+ * three-wave form): the Davis signal speeds of hll_flux, the contact speed
+ *   S* = (pR - pL + rL uL (SL - uL) - rR uR (SR - uR)) / (rL (SL - uL) - rR (SR - uR)),
+ * and on side K the star state
+ *   U*K = rK (SK - uK)/(SK - S*) [1, S*, t1K, t2K, EK/rK + (S* - uK)(S* + pK/(rK (SK - uK)))]
+ * with flux F*K = FK + SK (U*K - UK).  The interface takes FL (0 <= SL),
+ * F*L (SL < 0 <= S*), F*R (S* < 0 < SR) or FR (SR <= 0). */
+static void hllc_flux(double rl, double ul, double pl, double t1l, double t2l,
+                      double rr, double ur, double pr, double t1r, double t2r,
+                      double gamma, double F[5])
+{
+    double gm1inv = 1.0 / (gamma - 1.0);
+    double cl = sqrt(gamma * pl / rl), cr = sqrt(gamma * pr / rr);
+    double SL = ul - cl < ur - cr ? ul - cl : ur - cr;
+    double SR = ul + cl > ur + cr ? ul + cl : ur + cr;
+    double FL[5], FR[5];
+    phys_flux(rl, ul, pl, t1l, t2l, gamma, FL);
+    phys_flux(rr, ur, pr, t1r, t2r, gamma, FR);
+    if (SL >= 0.0) { memcpy(F, FL, sizeof FL); return; }
+    if (SR <= 0.0) { memcpy(F, FR, sizeof FR); return; }
+    double ml = rl * (SL - ul), mr = rr * (SR - ur);
+    double Ss = ((pr - pl) + ul * ml - ur * mr) / (ml - mr);
+    int left = Ss >= 0.0;
+    double r = left ? rl : rr, u = left ? ul : ur, p = left ? pl : pr;
+    double t1 = left ? t1l : t1r, t2 = left ? t2l : t2r, S = left ? SL : SR, m = left ? ml : mr;
+    const double *FK = left ? FL : FR;
+    double E = p * gm1inv + 0.5 * r * ((u * u + t1 * t1) + t2 * t2);
+    double UK[5] = { r, r * u, r * t1, r * t2, E };
+    double chi = m / (S - Ss);
+    double Us[5] = { chi, chi * Ss, chi * t1, chi * t2, chi * (E / r + (Ss - u) * (Ss + p / m)) };
+    for (int c = 0; c < 5; ++c) F[c] = FK[c] + S * (Us[c] - UK[c]);
+}
+
 /* ----------------------------------------------------------------------- */
 /* One pencil: primitives -> PPM -> tracing -> Riemann -> flux -> update.   */
 /* ----------------------------------------------------------------------- */
@@ -422,17 +456,25 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
     }
     /* (f,g) Riemann problem and flux at interface s+1/2, s = ng-1 .. L-ng-1 */
     for (int s = ng - 1; s <= L - ng - 1; ++s) {
-        or_riemann_out o;
         double rl = pc->sL[0][s], ul = pc->sL[1][s], pl = pc->sL[2][s];
         double rr = pc->sR[0][s + 1], ur = pc->sR[1][s + 1], pr = pc->sR[2][s + 1];
-        riemann_twoshock(rl, ul, pl, rr, ur, pr, -1.0, P, &o);
-        st->interfaces++;
-        st->newton_iters += o.iters;
-        if (!o.converged) st->newton_nonconv++;
-        double t1 = o.ustar >= 0.0 ? pc->sL[3][s] : pc->sR[3][s + 1];
-        double t2 = o.ustar >= 0.0 ? pc->sL[4][s] : pc->sR[4][s + 1];
         double F[5];
-        phys_flux(o.rho, o.u, o.p, t1, t2, gamma, F);
+        st->interfaces++;
+        if (P->solver == 1) {
+            hll_flux(rl, ul, pl, pc->sL[3][s], pc->sL[4][s], rr, ur, pr, pc->sR[3][s + 1], pc->sR[4][s + 1],
+                     gamma, F);
+        } else if (P->solver == 2) {
+            hllc_flux(rl, ul, pl, pc->sL[3][s], pc->sL[4][s], rr, ur, pr, pc->sR[3][s + 1], pc->sR[4][s + 1],
+                      gamma, F);
+        } else {
+            or_riemann_out o;
+            riemann_twoshock(rl, ul, pl, rr, ur, pr, -1.0, P, &o);
+            st->newton_iters += o.iters;
+            if (!o.converged) st->newton_nonconv++;
+            double t1 = o.ustar >= 0.0 ? pc->sL[3][s] : pc->sR[3][s + 1];
+            double t2 = o.ustar >= 0.0 ? pc->sL[4][s] : pc->sR[4][s + 1];
+            phys_flux(o.rho, o.u, o.p, t1, t2, gamma, F);
+        }
         for (int v = 0; v < 5; ++v) pc->F[v][s] = F[v];
     }
     /* (h) conservative update of active cells, FP64 */
@@ -734,7 +776,8 @@ void or_riemann_batch(int64_t count, const double *rl, const double *ul, const d
     }
 }
 
-/* Batched fluxes (two-shock or HLL) for given left/right primitive states. */
+/* Batched fluxes (solver 0 two-shock, 1 HLL, 2 HLLC) for given left/right
+ * primitive states. */
 void or_flux_batch(int64_t count, int32_t solver, const double *rl, const double *ul,
                    const double *pl, const double *t1l, const double *t2l,
                    const double *rr, const double *ur, const double *pr,
@@ -745,6 +788,9 @@ void or_flux_batch(int64_t count, int32_t solver, const double *rl, const double
         if (solver == 1) {
             hll_flux(rl[i], ul[i], pl[i], t1l[i], t2l[i], rr[i], ur[i], pr[i], t1r[i], t2r[i],
                      P->gamma, f);
+        } else if (solver == 2) {
+            hllc_flux(rl[i], ul[i], pl[i], t1l[i], t2l[i], rr[i], ur[i], pr[i], t1r[i], t2r[i],
+                      P->gamma, f);
         } else {
             or_riemann_out o;
             riemann_twoshock(rl[i], ul[i], pl[i], rr[i], ur[i], pr[i], -1.0, P, &o);

@@ -147,3 +147,37 @@ def test_twoshock_flux_of_equal_states_is_physical_flux():
     F = oracle.flux(s, s, P)
     G = oracle.flux(s, s, P, solver="hll")
     assert np.allclose(F, G, rtol=1e-12, atol=1e-12)
+
+
+def _phys(rho, u, p, t1, t2, g):
+    E = p / (g - 1.0) + 0.5 * rho * (u * u + t1 * t1 + t2 * t2)
+    return np.stack([rho * u, rho * u * u + p, rho * u * t1, rho * u * t2, u * (E + p)], axis=1)
+
+
+def test_hllc_is_consistent_upwind_and_exact_on_contacts():
+    """HLLC: F(U, U) = F(U); supersonic flow takes the upwind physical flux;
+    and, unlike HLL, an isolated contact (equal u and p, any rho and transverse
+    velocities) gets the exact flux of the upwind side, F = F(U_L) for u > 0,
+    F(U_R) for u < 0, and (0, p, 0, 0, 0) at rest.  A wrong sign or term in the
+    contact speed S* or the star state gives a mass flux off the upwind one."""
+    g = 1.4
+    P = oracle.Params(gamma=g)
+    rng = np.random.default_rng(5)
+    n = 64
+    s = [np.exp(rng.normal(0, 1, n)), rng.normal(0, 1, n), np.exp(rng.normal(0, 1, n)),
+         rng.normal(0, 1, n), rng.normal(0, 1, n)]
+    assert np.allclose(oracle.flux(s, s, P, solver="hllc"), _phys(*s, g), rtol=1e-13, atol=1e-13)
+    left = [np.ones(1), np.full(1, 5.0), np.ones(1), np.zeros(1), np.zeros(1)]
+    right = [np.full(1, 0.5), np.full(1, 4.0), np.full(1, 0.8), np.zeros(1), np.zeros(1)]
+    assert np.array_equal(oracle.flux(left, right, P, solver="hllc"), oracle.flux(left, left, P, solver="hllc"))
+    for u0 in (0.7, -0.4, 0.0):
+        rl, rr = np.exp(rng.normal(0, 1, n)), np.exp(rng.normal(0, 1, n))
+        p = np.exp(rng.normal(0, 1, n))
+        u = np.full(n, u0)
+        L = [rl, u, p, rng.normal(0, 1, n), rng.normal(0, 1, n)]
+        R = [rr, u, p, rng.normal(0, 1, n), rng.normal(0, 1, n)]
+        F = oracle.flux(L, R, P, solver="hllc")
+        up = _phys(*(L if u0 >= 0 else R), g)
+        assert np.allclose(F, up, rtol=1e-13, atol=1e-13), u0
+        Fh = oracle.flux(L, R, P, solver="hll")
+        assert np.max(np.abs(Fh[:, 0] - up[:, 0])) > 1e-3        # HLL smears the contact

@@ -394,3 +394,55 @@ def test_outflow_lets_a_wave_leave():
         out[name] = float(np.max(np.abs(_active(U[0])[0, 0] - 1.0)))
     assert out["outflow"] < 0.05 * amp, out
     assert out["reflect"] > 0.5 * amp, out
+
+
+def test_stationary_contact_kept_sharp_by_hllc_and_two_shock_not_hll():
+    """A density jump at rest in uniform pressure: the two-shock and HLLC
+    fluxes at every interface are (0, p, 0, 0, 0), so 40 steps leave the
+    density bit-identical; HLL diffuses it."""
+    g = 1.4
+    nx = 64
+    x = np.arange(nx)
+    rho = np.where((x >= 16) & (x < 48), 1.0, 0.125).reshape(1, 1, nx)
+    z = np.zeros_like(rho)
+    U0 = [synth.embed(f) for f in synth.prims_to_conserved(rho, z, z, z, np.ones_like(rho), g)]
+    dx = [1.0 / nx, 1e30, 1e30]
+    out = {}
+    for name, solver in (("twoshock", 0), ("hllc", 2), ("hll", 1)):
+        U = [f.copy() for f in U0]
+        P = oracle.Params(gamma=g, solver=solver)
+        for s in range(40):
+            oracle.step_periodic(U, dx, 0.4 / oracle.cfl_rate(U, dx, P), s, P)
+        out[name] = float(np.max(np.abs(_active(U[0]) - _active(U0[0]))))
+    assert out["twoshock"] == 0.0 and out["hllc"] == 0.0, out
+    assert out["hll"] > 1e-2, out
+
+
+@pytest.mark.parametrize("solver", [1, 2])
+def test_sod_with_hll_and_hllc_converges(solver):
+    """Sod (Sec. 11) with the approximate solvers as the interface flux: E1
+    against the exact solution is small at 100 cells and falls with N."""
+    E1 = {}
+    for N in (100, 200):
+        g = 1.4
+        nx = 2 * N
+        x = (np.arange(nx) + 0.5) / N
+        inside = (x >= 0.5) & (x < 1.5)
+        shape = (1, 1, nx)
+        rho = np.where(inside, 1.0, 0.125).reshape(shape)
+        p = np.where(inside, 1.0, 0.1).reshape(shape)
+        zero = np.zeros(shape)
+        U = [synth.embed(f) for f in synth.prims_to_conserved(rho, zero, zero, zero, p, g)]
+        P = oracle.Params(gamma=g, solver=solver)
+        dx = [1.0 / N, 1e30, 1e30]
+        t, step = 0.0, 0
+        while t < 0.25 - 1e-14:
+            dt = min(0.4 / oracle.cfl_rate(U, dx, P), 0.25 - t)
+            oracle.step_periodic(U, dx, dt, step, P)
+            t += dt
+            step += 1
+        r = _active(U[0])[0, 0]
+        E1[N] = sum(abs(r[i] - ex.sample(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, g, (x[i] - 1.5) / 0.25)[0]) / N
+                    for i in range(nx) if x[i] >= 1.0)
+    assert E1[100] < 8e-3, E1
+    assert E1[200] < 0.75 * E1[100], E1
