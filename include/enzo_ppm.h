@@ -118,6 +118,11 @@ typedef struct {
     double *freg;                 /* DEVICE flux registers (see enzo_patch.freg_*), or NULL */
 } enzo_patch_batch;
 
+/* Interface flux solvers (Sec. 4.1.2): the two-shock Riemann solver with a
+ * Newton iteration on p*, or the HLL / HLLC approximate solvers on the traced
+ * states (Davis signal speeds).  The positivity fallback is HLL in every case. */
+enum { ENZO_SOLVER_TWOSHOCK = 0, ENZO_SOLVER_HLL = 1, ENZO_SOLVER_HLLC = 2 };
+
 /* Method parameters (Sec. 4.1, 4.1.2, 9). */
 typedef struct {
     double gamma;       /* ratio of specific heats, > 1 */
@@ -136,7 +141,9 @@ typedef struct {
                            128), 64, 128 or 256; used by the FP32 plain-guess path
                            (the FP64 and learned paths always use 128).  Picked
                            per batch by the autotuner (paper_1307_2265_gb300.tune). */
-    int32_t reserved;
+    int32_t solver;     /* interface flux (Sec. 4.1.2): ENZO_SOLVER_TWOSHOCK (default, 0),
+                           ENZO_SOLVER_HLL or ENZO_SOLVER_HLLC; the learned guess needs the
+                           two-shock solver (ENZO_ERR_ARG otherwise) */
     double mlp_gate;    /* ENZO_GUESS_MLP: an interface takes the learned guess only when
                            its jump strength max(|pL-pR|/(pL+pR), |uL-uR|/c_m) exceeds this
                            (c_m^2 = gamma (pL+pR)/(rhoL+rhoR)); weaker interfaces keep the

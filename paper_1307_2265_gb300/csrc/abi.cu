@@ -202,6 +202,10 @@ static int resolve(const enzo_params *p, MethodParams &m)
     m.mlp = p->mlp;
     if (p->mlp_gate != p->mlp_gate) return ENZO_ERR_ARG;
     m.mlp_gate = p->mlp_gate == 0.0 ? 0.03 : p->mlp_gate;
+    if (p->solver != ENZO_SOLVER_TWOSHOCK && p->solver != ENZO_SOLVER_HLL && p->solver != ENZO_SOLVER_HLLC)
+        return ENZO_ERR_ARG;
+    if (p->guess == ENZO_GUESS_MLP && p->solver != ENZO_SOLVER_TWOSHOCK) return ENZO_ERR_ARG;
+    m.solver = p->solver;
     return ENZO_OK;
 }
 

@@ -40,6 +40,7 @@ struct MethodParams {
     int newton_max, fallback, guess;
     const void *mlp;
     double mlp_gate;   // < 0: learned guess at every interface
+    int solver;        // ENZO_SOLVER_*: interface flux
 };
 
 struct SweepArgs {

@@ -90,6 +90,9 @@ extern "C" int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, do
     m.guess = p->guess;
     m.mlp = nullptr;
     m.mlp_gate = 0.0;
+    if (p->solver != ENZO_SOLVER_TWOSHOCK && p->solver != ENZO_SOLVER_HLL && p->solver != ENZO_SOLVER_HLLC)
+        return ENZO_ERR_ARG;
+    m.solver = p->solver;
 
     void *scratch = nullptr;
     int r = noalloc_scratch(&scratch);

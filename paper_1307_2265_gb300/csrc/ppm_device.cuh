@@ -489,6 +489,50 @@ __device__ __forceinline__ void hll_flux(const Zone<R> &L, const Zone<R> &Rz, co
         F[c] = (SR * FL[c] - SL * FR[c] + SL * SR * (UR[c] - UL[c])) / (SR - SL);
 }
 
+// HLL flux of two primitive states (r, u, p, t1, t2) as the interface flux
+// (the approximate solver of Sec. 4.1.2 used on the traced states).
+template <class R>
+__device__ __forceinline__ void hll_states(const R l[5], const R r[5], const Consts<R> &k, R F[5])
+{
+    const Zone<R> zl{l[0], l[1], l[2], l[3], l[4], (R)0}, zr{r[0], r[1], r[2], r[3], r[4], (R)0};
+    hll_flux<R>(zl, zr, k, F);
+}
+
+// HLLC flux of two primitive states: the Davis bounds SL, SR of hll_flux, the
+// contact speed S* = (pR - pL + rL uL (SL - uL) - rR uR (SR - uR)) /
+// (rL (SL - uL) - rR (SR - uR)), and on the upwind side of the contact the star
+// state rK (SK - uK)/(SK - S*) [1, S*, t1K, t2K, EK/rK + (S* - uK)(S* + pK/(rK (SK - uK)))]
+// with flux FK + SK (U*K - UK) (Sec. 4.1.2 names HLLC; Toro's three-wave form).
+template <class R>
+__device__ __forceinline__ void hllc_states(const R l[5], const R r[5], const Consts<R> &k, R F[5])
+{
+    const R rl = l[0], ul = l[1], pl = l[2], rr = r[0], ur = r[1], pr = r[2];
+    const R cl = sqrt(k.gamma * pl / rl), cr = sqrt(k.gamma * pr / rr);
+    const R SL = ul - cl < ur - cr ? ul - cl : ur - cr;
+    const R SR = ul + cl > ur + cr ? ul + cl : ur + cr;
+    R FL[5], FR[5];
+    phys_flux(rl, ul, pl, l[3], l[4], k, FL);
+    phys_flux(rr, ur, pr, r[3], r[4], k, FR);
+    if (SL >= (R)0) {
+        _Pragma("unroll") for (int c = 0; c < 5; ++c) F[c] = FL[c];
+        return;
+    }
+    if (SR <= (R)0) {
+        _Pragma("unroll") for (int c = 0; c < 5; ++c) F[c] = FR[c];
+        return;
+    }
+    const R ml = rl * (SL - ul), mr = rr * (SR - ur);
+    const R Ss = ((pr - pl) + ul * ml - ur * mr) / (ml - mr);
+    const bool left = Ss >= (R)0;
+    const R rk = left ? rl : rr, uk = left ? ul : ur, pk = left ? pl : pr;
+    const R t1 = left ? l[3] : r[3], t2 = left ? l[4] : r[4], S = left ? SL : SR, m = left ? ml : mr;
+    const R E = pk * k.gm1inv + (R)0.5 * rk * ((uk * uk + t1 * t1) + t2 * t2);
+    const R UK[5] = {rk, rk * uk, rk * t1, rk * t2, E};
+    const R chi = m / (S - Ss);
+    const R Us[5] = {chi, chi * Ss, chi * t1, chi * t2, chi * (E / rk + (Ss - uk) * (Ss + pk / m))};
+    _Pragma("unroll") for (int c = 0; c < 5; ++c) F[c] = (left ? FL[c] : FR[c]) + S * (Us[c] - UK[c]);
+}
+
 // Pencil addressing: storage index of pencil position s (0 .. L-1).
 struct Pencil {
     int64_t base, sd;
@@ -881,18 +925,24 @@ struct Marcher {
                     if (kk >= 5) {
                         // Riemann problem at interface (kk-3)+1/2
                         if (a.log) log_states(kk, sLprev, sR);
-                        const R p0 = guess(sLprev[0], sLprev[1], sLprev[2], sR[0], sR[1], sR[2]);
-                        const RiemannOut<R> o = riemann<R>(sLprev[0], sLprev[1], sLprev[2], sR[0], sR[1], sR[2],
-                                                           p0, k, cnt);
-                        if (active) {
-                            if (p0 > (R)0) cnt.guesses++;
-                            cnt.iters += (unsigned)o.iters;
-                            if (!o.conv) cnt.rare(ENZO_ST_NEWTON_NONCONV);
-                        }
-                        const R t1 = o.ustar >= (R)0 ? sLprev[3] : sR[3];
-                        const R t2 = o.ustar >= (R)0 ? sLprev[4] : sR[4];
                         R Fg[5];
-                        phys_flux<R>(o.rho, o.u, o.p, t1, t2, k, Fg);
+                        if (mp.solver == ENZO_SOLVER_TWOSHOCK) {
+                            const R p0 = guess(sLprev[0], sLprev[1], sLprev[2], sR[0], sR[1], sR[2]);
+                            const RiemannOut<R> o = riemann<R>(sLprev[0], sLprev[1], sLprev[2], sR[0], sR[1],
+                                                               sR[2], p0, k, cnt);
+                            if (active) {
+                                if (p0 > (R)0) cnt.guesses++;
+                                cnt.iters += (unsigned)o.iters;
+                                if (!o.conv) cnt.rare(ENZO_ST_NEWTON_NONCONV);
+                            }
+                            const R t1 = o.ustar >= (R)0 ? sLprev[3] : sR[3];
+                            const R t2 = o.ustar >= (R)0 ? sLprev[4] : sR[4];
+                            phys_flux<R>(o.rho, o.u, o.p, t1, t2, k, Fg);
+                        } else if (mp.solver == ENZO_SOLVER_HLLC) {
+                            hllc_states<R>(sLprev, sR, k, Fg);
+                        } else {
+                            hll_states<R>(sLprev, sR, k, Fg);
+                        }
                         if (kk >= 6) {
                             // cell c = kk-3: does the Godunov update leave rho > 0?
                             const int c = kk - 3;

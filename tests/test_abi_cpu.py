@@ -96,3 +96,14 @@ def test_boundary_conditions_rejected_without_gpu():
     assert L.enzo_ghost_fill_boundary(ctypes.byref(b), good) == 0       # empty batch: no-op
     p = ez.Params().c()
     assert L.enzo_step_boundary(ctypes.byref(b), ctypes.byref(p), 0, None, good) == -1   # no dt
+
+
+def test_solver_selector_rejected_without_gpu():
+    L = ez.lib()
+    b = ez._Batch()
+    b.npatch = 0
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(ez.Params(solver=ez.SOLVER_HLLC).c())) == 0
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(ez.Params(solver=5).c())) == -1
+    fake_blob = ctypes.c_void_p(4096)          # never dereferenced: rejected before any launch
+    p = ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=fake_blob.value, solver=ez.SOLVER_HLL).c()
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -1
