@@ -268,12 +268,13 @@ __global__ void __launch_bounds__(128) flux_correct_kernel(const __grid_constant
         const int cell = F.side ? X : X - 1;
         const int fc = X - PL.origin[d];
         const int m1 = FP.n[a1] / 2, m2 = FP.n[a2] / 2;
-        const double inv_dx = 1.0 / TP.dx[d];
         const double *creg = a.cfreg + PP.freg_all + reg_all_block(PP, d);
         const double *freg = a.ffreg + FP.freg_bnd + reg_bnd_block(FP, d);
         const int fna1 = FP.n[a1];
         const int T0 = TP.n[0] + 2 * TP.ng, T1 = TP.n[1] + 2 * TP.ng;
-        const int map[5] = {0, 1 + d, 1 + a1, 1 + a2, 4};
+        // fields in pencil order (rho, m_n, m_t1, m_t2, E)
+        double *const Uf[5] = {a.U[0], d == 0 ? a.U[1] : (d == 1 ? a.U[2] : a.U[3]),
+                               a1 == 0 ? a.U[1] : a.U[2], a2 == 1 ? a.U[2] : a.U[3], a.U[4]};
         for (int q = threadIdx.x; q < m1 * m2; q += blockDim.x) {
             const int q1 = q % m1, q2 = q / m1;
             const int c1 = FL.origin[a1] / 2 + q1, c2 = FL.origin[a2] / 2 + q2;
@@ -289,6 +290,7 @@ __global__ void __launch_bounds__(128) flux_correct_kernel(const __grid_constant
             g[a2] = c2;
             const int64_t idx = TP.off + (g[0] - TL.origin[0] + TP.ng) +
                                 (int64_t)T0 * ((g[1] - TL.origin[1] + TP.ng) + (int64_t)T1 * (g[2] - TL.origin[2] + TP.ng));
+#pragma unroll
             for (int v = 0; v < 5; ++v) {
                 double delta;
                 if (a.increments) {
@@ -299,9 +301,8 @@ __global__ void __launch_bounds__(128) flux_correct_kernel(const __grid_constant
                     const double fine = (((f00[v] + f01[v]) + f10[v]) + f11[v]) * 0.25;
                     delta = (a.dt_c * cf[v] - fine) / TP.dx[d];
                 }
-                atomicAdd(&a.U[map[v]][idx], F.side ? -delta : delta);
+                atomicAdd(&Uf[v][idx], F.side ? -delta : delta);
             }
-            (void)inv_dx;
         }
     }
 }
