@@ -15,9 +15,12 @@
 //   limited slopes and interface values q_{j+1/2}; monotone parabola per zone
 //   (q_L, q_R, Delta q, q6); averages over the u-c, u, u+c domains of
 //   dependence; characteristic left/right states (reference wave plus beta
-//   corrections); two-shock Riemann solve with Newton iteration on p*; fluxes;
+//   corrections); two-shock Riemann solve with Newton iteration on p* (or the
+//   HLL / HLLC approximate solvers on the traced states); fluxes;
 //   U_j += dt/dx (F_{j-1/2} - F_{j+1/2}); HLL re-flux of cells whose density
-//   would drop to <= 0.
+//   would drop to <= 0.  The Newton start is the plain two-shock guess or, in
+//   the FP32 path, a small network evaluated on the tensor cores
+//   (LearnedGuess).
 //
 // Thread layout: one thread marches one pencil from one end to the other,
 // holding a sliding window of zones in registers: reading cell k it finishes
