@@ -76,3 +76,94 @@ def test_composite_conservation_gpu(precision):
     hier.stream.synchronize()
     t1, scale = totals()
     assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0) / scale
+
+
+def _l1_by_level(a_levels, b_levels):
+    """Per level, per field: sum |a - b| / sum |b| over the active cells."""
+    out = []
+    for A, B in zip(a_levels, b_levels):
+        num, den = np.zeros(5), np.zeros(5)
+        for pa, pb in zip(A, B):
+            for f in range(5):
+                num[f] += np.sum(np.abs(H._active(pa[f]) - H._active(pb[f])))
+                den[f] += np.sum(np.abs(H._active(pb[f])))
+        out.append(num / den)
+    return np.array(out)
+
+
+@pytest.fixture(scope="module")
+def fp64_reference():
+    """Two FP64 oracle runs of two root steps: the reference, and one whose
+    initial fields carry 2^-24 relative noise (the flow's own sensitivity to
+    rounding-sized changes, the chaotic floor of the FP32 rule)."""
+    layout, fields = _setup(3)
+    P = oracle.Params()
+    ref = H.make_levels(layout, fields, 1.0 / 16)
+    rng = np.random.default_rng(9)
+    noisy = [[[f * (1.0 + 2.0 ** -24 * rng.standard_normal(f.shape)) for f in U] for U in lev] for lev in fields]
+    pert = H.make_levels(layout, noisy, 1.0 / 16)
+    logs = []
+    for _ in range(2):
+        log = []
+        H.root_step(ref, P, log=log)
+        H.root_step(pert, P)
+        logs.append(log)
+    r = [[p["U"] for p in L["patches"]] for L in ref]
+    q = [[p["U"] for p in L["patches"]] for L in pert]
+    return layout, fields, r, logs, _l1_by_level(q, r)
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_fp32_root_steps_close_to_oracle(fp64_reference, learned):
+    """The FP32 path (plain, or with the learned guess at every interface) over
+    two subcycled root steps of a white-noise hierarchy: the same substeps as
+    the FP64 oracle, and a per-level, per-field L1 relative error within
+    max(4 x chaotic floor, 2e-6), the FP32 parity rule of the single-grid tests."""
+    layout, fields, ref, logs, floor = fp64_reference
+    hier = gh.Hierarchy(layout, fields, 1.0 / 16)
+    net = ez.MLP(seed=2)
+    params = (ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob, mlp_gate=-1.0) if learned
+              else ez.Params(precision=ez.FP32))
+    for log_o in logs:
+        log_g = []
+        hier.root_step(params, log=log_g)
+        assert [l for l, _ in log_g] == [l for l, _ in log_o]
+        assert np.allclose([d for _, d in log_g], [d for _, d in log_o], rtol=1e-5)
+    hier.stream.synchronize()
+    got = [[hier.patch_fields(l, i) for i in range(len(L))] for l, L in enumerate(ref)]
+    err = _l1_by_level(got, ref)
+    bound = np.maximum(4.0 * floor, 2e-6)
+    print(f"\nFP32{' learned' if learned else ''} hierarchy L1 by level:\n{err}\nchaotic floor:\n{floor}")
+    assert np.all(err <= bound), (err, floor)
+    st = sum(np.array(list(lev["batch"].read_status().values())) for lev in hier.levels)
+    assert st[7] == 0                                   # no NaN anywhere
+
+
+def test_full_size_hierarchy_keeps_a_uniform_moving_state():
+    """The bench's hierarchy (256^3 root, 29 491 patches on three refined
+    levels) with a uniform state moving obliquely: one subcycled FP32 root step
+    with the learned guess (ghost interpolation, sibling copies, sweeps, flux
+    correction and projection) keeps it to FP32 rounding of the increments."""
+    import torch
+    root = 256
+    layout = synth.hierarchy_layout(root, [(root // 8, 7 * root // 8), (root // 4, 3 * root // 4),
+                                           (3 * root // 8, 5 * root // 8)], list(range(16, 33, 2)), seed=0)
+    g = 5.0 / 3.0
+    state = synth.prims_to_conserved(np.ones(1), np.full(1, 0.3), np.full(1, -0.2), np.full(1, 0.1), np.ones(1), g)
+    fields = []
+    for L in layout:
+        lev = []
+        for n in L["n"]:
+            shape = (int(n[2]) + 6, int(n[1]) + 6, int(n[0]) + 6)
+            lev.append([np.full(shape, float(v[0])) for v in state])
+        fields.append(lev)
+    hier = gh.Hierarchy(layout, fields, 1.0 / root)
+    net = ez.MLP(seed=4)
+    log = []
+    hier.root_step(ez.Params(gamma=g, precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob, mlp_gate=-1.0), log=log)
+    hier.stream.synchronize()
+    assert [sum(1 for l, _ in log if l == k) for k in range(4)][0] == 1
+    for lev in hier.levels:
+        for u, v in zip(lev["batch"].U, state):
+            dev = float(torch.max(torch.abs(u - float(v[0]))))
+            assert dev <= 1e-6 * max(1.0, abs(float(v[0]))), dev
