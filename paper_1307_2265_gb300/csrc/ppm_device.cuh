@@ -814,8 +814,10 @@ struct Marcher {
         } else {
             idx = pc.at(s);
         }
-        return prim<R, COUNT>(a.U[0][idx], a.U[1 + DIR][idx], a.U[1 + A1][idx], a.U[1 + A2][idx],
-                              a.U[4][idx], k, cnt);
+        // read-only (non-coherent) path: within one sweep a cell is read by the
+        // thread of its own pencil before that thread writes it, never after
+        return prim<R, COUNT>(__ldg(a.U[0] + idx), __ldg(a.U[1 + DIR] + idx), __ldg(a.U[1 + A1] + idx),
+                              __ldg(a.U[1 + A2] + idx), __ldg(a.U[4] + idx), k, cnt);
     }
 
     // Density of cell s at the start of the sweep (raw, no floor).
