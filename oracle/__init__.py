@@ -42,7 +42,7 @@ class OrParams(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("rho_floor", ctypes.c_double),
                 ("p_floor", ctypes.c_double), ("newton_tol", ctypes.c_double),
                 ("newton_max", ctypes.c_int32), ("fallback", ctypes.c_int32),
-                ("solver", ctypes.c_int32)]
+                ("solver", ctypes.c_int32), ("options", ctypes.c_int32)]
 
 
 class OrStats(ctypes.Structure):
@@ -63,10 +63,11 @@ class Params:
     newton_max: int = 20
     fallback: int = 1
     solver: int = 0          # interface fluxes: 0 two-shock, 1 HLL, 2 HLLC
+    options: int = 0         # bit 0 contact steepening, bit 1 flattening, bit 2 diffusive flux
 
     def c(self) -> OrParams:
         return OrParams(self.gamma, self.rho_floor, self.p_floor, self.newton_tol,
-                        self.newton_max, self.fallback, self.solver)
+                        self.newton_max, self.fallback, self.solver, self.options)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -249,6 +250,7 @@ def riemann(rl, ul, pl, rr, ur, pr, params: Params, pguess=None):
 
 
 SOLVER_TWOSHOCK, SOLVER_HLL, SOLVER_HLLC = 0, 1, 2
+OPT_STEEPEN, OPT_FLATTEN, OPT_DIFFUSE = 1, 2, 4
 
 
 def flux(left, right, params: Params, solver="twoshock"):

@@ -61,6 +61,7 @@ typedef struct {
     int32_t newton_max;
     int32_t fallback;     /* 1: HLL re-flux of cells that reach rho <= 0 */
     int32_t solver;       /* interface fluxes: 0 two-shock (Sec. 4.1.2), 1 HLL, 2 HLLC */
+    int32_t options;      /* bit 0 contact steepening, bit 1 flattening, bit 2 diffusive flux */
 } or_params;
 
 typedef struct {
@@ -309,12 +310,14 @@ typedef struct {
     double *sR[5];      /* right state at interface s-1/2 (from zone s) */
     double *F[5];       /* flux at interface s+1/2 */
     double *Uold[5];
+    double *eta;        /* contact-steepening weight per zone */
+    double *flat;       /* flattening weight per zone */
     double *buf;
 } pencil;
 
 static int pencil_alloc(pencil *pc, int L)
 {
-    int narr = 5 * 13 + 1;
+    int narr = 5 * 13 + 3;
     pc->L = L;
     pc->buf = (double *)calloc((size_t)narr * (size_t)L, sizeof(double));
     if (!pc->buf) return -1;
@@ -326,8 +329,60 @@ static int pencil_alloc(pencil *pc, int L)
         pc->sR[v] = b; b += L; pc->F[v] = b; b += L;  pc->Uold[v] = b; b += L;
         b += L;  /* spare */
     }
-    pc->c = b;
+    pc->c = b; b += L;
+    pc->eta = b; b += L;
+    pc->flat = b;
     return 0;
+}
+
+/* Optional dissipation of the PPM reconstruction (Sec. 4.1 calls them
+ * optional and defers to CW84; its formulas, on a uniform grid):
+ *
+ * Contact steepening (density only) of zone s, from the discontinuity
+ * detector  eta~ = -(D_{s+1} - D_{s-1}) / (6 (rho_{s+1} - rho_{s-1})),
+ * D_s = rho_{s+1} - 2 rho_s + rho_{s-1}, set to 0 where D_{s+1} D_{s-1} >= 0,
+ * where |rho_{s+1} - rho_{s-1}| < 0.01 min(rho_{s+1}, rho_{s-1}), or where the
+ * pressure jump is large against the density jump (a shock, not a contact:
+ * |p_{s+1} - p_{s-1}| / min(p) > 0.1 gamma |rho_{s+1} - rho_{s-1}| / min(rho));
+ * weight eta = max(0, min(20 (eta~ - 0.05), 1)).
+ *
+ * Flattening of zone s near strong shocks: w = 1 where the flow compresses
+ * (u_{s-1} > u_{s+1}) and |p_{s+1} - p_{s-1}| > 0.33 min(p_{s+1}, p_{s-1});
+ * weight f = w max(0, min(1, 10 ((p_{s+1} - p_{s-1}) / (p_{s+2} - p_{s-2}) - 0.75)))
+ * (f = w where p_{s+2} = p_{s-2}).  Reading: CW84 also takes the max with the
+ * upstream neighbour's weight, which needs pressures three zones away; that
+ * max is dropped so every stencil fits the three ghost zones. */
+static void dissipation_weights(pencil *pc, const or_params *P)
+{
+    const int L = pc->L;
+    const double *r = pc->q[0], *u = pc->q[1], *p = pc->q[2];
+    for (int s = 0; s < L; ++s) { pc->eta[s] = 0.0; pc->flat[s] = 0.0; }
+    for (int s = 2; s < L - 2; ++s) {
+        if (P->options & 1) {
+            double Dm = r[s] - 2.0 * r[s - 1] + r[s - 2];
+            double Dp = r[s + 2] - 2.0 * r[s + 1] + r[s];
+            double dr = r[s + 1] - r[s - 1];
+            double rmin = r[s + 1] < r[s - 1] ? r[s + 1] : r[s - 1];
+            double pmin = p[s + 1] < p[s - 1] ? p[s + 1] : p[s - 1];
+            double et = 0.0;
+            int contact = fabs(p[s + 1] - p[s - 1]) / pmin <= 0.1 * P->gamma * (fabs(dr) / rmin);
+            if (Dm * Dp < 0.0 && fabs(dr) >= 0.01 * rmin && contact) et = -(Dp - Dm) / (6.0 * dr);
+            double e = 20.0 * (et - 0.05);
+            pc->eta[s] = e < 0.0 ? 0.0 : (e > 1.0 ? 1.0 : e);
+        }
+        if (P->options & 2) {
+            double dp1 = p[s + 1] - p[s - 1], dp2 = p[s + 2] - p[s - 2];
+            double pmin = p[s + 1] < p[s - 1] ? p[s + 1] : p[s - 1];
+            if (u[s - 1] - u[s + 1] > 0.0 && fabs(dp1) > 0.33 * pmin) {
+                double f = 1.0;
+                if (dp2 != 0.0) {
+                    f = 10.0 * (dp1 / dp2 - 0.75);
+                    f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+                }
+                pc->flat[s] = f;
+            }
+        }
+    }
 }
 
 /* Domain-of-dependence average of zone parabola over its right (toward=+1) or
@@ -407,6 +462,7 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
         pc->q[4][s] = m2 / rho;
         pc->c[s] = sqrt(gamma * p / rho);
     }
+    dissipation_weights(pc, P);
     /* (b) limited slopes, CW84 1.7-1.8 */
     for (int v = 0; v < 5; ++v) {
         const double *q = pc->q[v];
@@ -426,9 +482,20 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
         /* interface value between zones s and s+1, CW84 1.6 (uniform grid) */
         for (int s = 1; s < L - 2; ++s)
             pc->qf[v][s] = 0.5 * (q[s] + q[s + 1]) - (pc->dq[v][s + 1] - pc->dq[v][s]) / 6.0;
-        /* (c) monotone parabola for zones 2..L-3, CW84 1.10 */
+        /* (c) monotone parabola for zones 2..L-3, CW84 1.10, after the optional
+         * contact steepening (density) and flattening */
         for (int s = 2; s < L - 2; ++s) {
             double qs = q[s], ql = pc->qf[v][s - 1], qr = pc->qf[v][s];
+            if (v == 0 && pc->eta[s] > 0.0) {
+                double e = pc->eta[s];
+                ql = ql * (1.0 - e) + (q[s - 1] + 0.5 * pc->dq[v][s - 1]) * e;
+                qr = qr * (1.0 - e) + (q[s + 1] - 0.5 * pc->dq[v][s + 1]) * e;
+            }
+            if (pc->flat[s] > 0.0) {
+                double f = pc->flat[s];
+                ql = f * qs + (1.0 - f) * ql;
+                qr = f * qs + (1.0 - f) * qr;
+            }
             if ((qr - qs) * (qs - ql) <= 0.0) {
                 ql = qs; qr = qs;
             } else {
@@ -474,6 +541,25 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
             double t1 = o.ustar >= 0.0 ? pc->sL[3][s] : pc->sR[3][s + 1];
             double t2 = o.ustar >= 0.0 ? pc->sL[4][s] : pc->sR[4][s + 1];
             phys_flux(o.rho, o.u, o.p, t1, t2, gamma, F);
+        }
+        if (P->options & 4) {
+            /* diffusive flux (CW84; optional in Sec. 4.1): 0.1 max(0, u_s - u_{s+1})
+             * times the jump of the conserved state across the interface, the
+             * conserved states rebuilt from the zone primitives */
+            double du = pc->q[1][s] - pc->q[1][s + 1];
+            if (du > 0.0) {
+                double nu = 0.1 * du;
+                double Ua[5], Ub[5];
+                for (int z = 0; z < 2; ++z) {
+                    double *Uz = z ? Ub : Ua;
+                    int c = s + z;
+                    double r = pc->q[0][c], u = pc->q[1][c], pz = pc->q[2][c];
+                    double t1 = pc->q[3][c], t2 = pc->q[4][c];
+                    Uz[0] = r; Uz[1] = r * u; Uz[2] = r * t1; Uz[3] = r * t2;
+                    Uz[4] = pz / (gamma - 1.0) + 0.5 * r * ((u * u + t1 * t1) + t2 * t2);
+                }
+                for (int v = 0; v < 5; ++v) F[v] = F[v] + nu * (Ua[v] - Ub[v]);
+            }
         }
         for (int v = 0; v < 5; ++v) pc->F[v][s] = F[v];
     }
