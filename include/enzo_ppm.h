@@ -123,6 +123,14 @@ typedef struct {
  * states (Davis signal speeds).  The positivity fallback is HLL in every case. */
 enum { ENZO_SOLVER_TWOSHOCK = 0, ENZO_SOLVER_HLL = 1, ENZO_SOLVER_HLLC = 2 };
 
+/* Optional dissipation of the reconstruction (Sec. 4.1 names contact
+ * steepening, flattening and a diffusive flux as options and defers to CW84):
+ * steepening of the density at contacts, flattening of every variable in zones
+ * that compress across a strong pressure jump (the zone's own weight: the
+ * stencil stays within three ghost zones), and a flux 0.1 max(0, u_L - u_R)
+ * (U_L - U_R) at compressive interfaces. */
+enum { ENZO_OPT_STEEPEN = 1, ENZO_OPT_FLATTEN = 2, ENZO_OPT_DIFFUSE = 4 };
+
 /* Method parameters (Sec. 4.1, 4.1.2, 9). */
 typedef struct {
     double gamma;       /* ratio of specific heats, > 1 */
@@ -150,6 +158,8 @@ typedef struct {
                            plain guess, which is already within a Newton step of the root
                            there.  0 selects 0.03; < 0 takes the learned guess everywhere.
                            A CTA whose interfaces are all below the gate skips the network. */
+    int32_t options;    /* ENZO_OPT_* bits (default 0): the optional reconstruction
+                           dissipation of Sec. 4.1 / CW84; not with ENZO_GUESS_MLP */
 } enzo_params;
 
 /* Bytes of device workspace a batch of npatch patches needs. */

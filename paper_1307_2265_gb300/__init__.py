@@ -20,6 +20,7 @@ from . import _build
 FP64, FP32 = 0, 1
 GUESS_PLAIN, GUESS_MLP = 0, 1
 SOLVER_TWOSHOCK, SOLVER_HLL, SOLVER_HLLC = 0, 1, 2
+OPT_STEEPEN, OPT_FLATTEN, OPT_DIFFUSE = 1, 2, 4
 PATCH_PERIODIC = 1
 STATUS_WORDS = 16
 STATUS_NAMES = ("interfaces", "newton_iters", "newton_nonconv", "hll_cells", "neg_after",
@@ -49,7 +50,8 @@ class _Params(ctypes.Structure):
                 ("newton_tol", ctypes.c_double), ("newton_max", ctypes.c_int32),
                 ("fallback", ctypes.c_int32), ("rho_floor", ctypes.c_double),
                 ("p_floor", ctypes.c_double), ("mlp", ctypes.c_void_p),
-                ("tile", ctypes.c_int32 * 3), ("solver", ctypes.c_int32), ("mlp_gate", ctypes.c_double)]
+                ("tile", ctypes.c_int32 * 3), ("solver", ctypes.c_int32), ("mlp_gate", ctypes.c_double),
+                ("options", ctypes.c_int32)]
 
 
 class _Riemann(ctypes.Structure):
@@ -116,19 +118,20 @@ class Params:
 
     def __init__(self, gamma=5.0 / 3.0, cfl=0.4, precision=FP64, guess=GUESS_PLAIN, newton_tol=0.0,
                  newton_max=0, fallback=1, rho_floor=1e-30, p_floor=1e-30, mlp=None, tile=(0, 0, 0),
-                 mlp_gate=0.0, solver=SOLVER_TWOSHOCK):
+                 mlp_gate=0.0, solver=SOLVER_TWOSHOCK, options=0):
         self.gamma, self.cfl, self.precision, self.guess = gamma, cfl, precision, guess
         self.newton_tol, self.newton_max, self.fallback = newton_tol, newton_max, fallback
         self.rho_floor, self.p_floor, self.mlp = rho_floor, p_floor, mlp
         self.tile = tuple(tile)
         self.mlp_gate = mlp_gate
         self.solver = solver
+        self.options = options
 
     def c(self) -> _Params:
         mlp_ptr = 0 if self.mlp is None else (self.mlp.data_ptr() if hasattr(self.mlp, "data_ptr") else int(self.mlp))
         return _Params(self.gamma, self.cfl, self.precision, self.guess, self.newton_tol,
                        self.newton_max, self.fallback, self.rho_floor, self.p_floor, mlp_ptr,
-                       (ctypes.c_int32 * 3)(*self.tile), self.solver, self.mlp_gate)
+                       (ctypes.c_int32 * 3)(*self.tile), self.solver, self.mlp_gate, self.options)
 
 
 def patch_table(sizes, offsets, dx, flags=0, ng=3, level=0) -> np.ndarray:

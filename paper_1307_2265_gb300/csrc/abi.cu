@@ -206,6 +206,9 @@ static int resolve(const enzo_params *p, MethodParams &m)
         return ENZO_ERR_ARG;
     if (p->guess == ENZO_GUESS_MLP && p->solver != ENZO_SOLVER_TWOSHOCK) return ENZO_ERR_ARG;
     m.solver = p->solver;
+    if (p->options & ~(ENZO_OPT_STEEPEN | ENZO_OPT_FLATTEN | ENZO_OPT_DIFFUSE)) return ENZO_ERR_ARG;
+    if (p->guess == ENZO_GUESS_MLP && p->options) return ENZO_ERR_ARG;
+    m.options = p->options;
     return ENZO_OK;
 }
 
@@ -259,7 +262,7 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
 {
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
     int tile = tile_pencils > 0 ? tile_pencils : kSweepThreads;
-    if (precision == ENZO_FP64 || m.guess == ENZO_GUESS_MLP || b->freg) tile = kSweepThreads;
+    if (precision == ENZO_FP64 || m.guess == ENZO_GUESS_MLP || b->freg || m.options) tile = kSweepThreads;
     int r = launch_prefix(b, kKindSweep, dir, cover, false, s, tile);
     if (r) return r;
     SweepArgs a;

@@ -41,6 +41,7 @@ struct MethodParams {
     const void *mlp;
     double mlp_gate;   // < 0: learned guess at every interface
     int solver;        // ENZO_SOLVER_*: interface flux
+    int options;       // ENZO_OPT_* bits of the reconstruction
 };
 
 struct SweepArgs {

@@ -93,6 +93,8 @@ extern "C" int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, do
     if (p->solver != ENZO_SOLVER_TWOSHOCK && p->solver != ENZO_SOLVER_HLL && p->solver != ENZO_SOLVER_HLLC)
         return ENZO_ERR_ARG;
     m.solver = p->solver;
+    if (p->options & ~(ENZO_OPT_STEEPEN | ENZO_OPT_FLATTEN | ENZO_OPT_DIFFUSE)) return ENZO_ERR_ARG;
+    m.options = p->options;
 
     void *scratch = nullptr;
     int r = noalloc_scratch(&scratch);

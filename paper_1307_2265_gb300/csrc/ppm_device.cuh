@@ -780,7 +780,7 @@ struct LearnedGuess {
     }
 };
 
-template <class R, bool WRAP, int DIR, bool REG = false>
+template <class R, bool WRAP, int DIR, bool REG = false, bool EXT = false>
 struct Marcher {
     static constexpr int A1 = DIR == 0 ? 1 : 0;
     static constexpr int A2 = DIR == 2 ? 1 : 2;
@@ -878,6 +878,80 @@ struct Marcher {
         }
     }
 
+    // Optional reconstruction dissipation of zone j (CW84; optional in
+    // Sec. 4.1) on its unlimited edge values el/er, in the order the monotone
+    // parabola then takes them: contact steepening of the density, then
+    // flattening of all five variables.  Zones j-2..j+2 are zj2m (density and
+    // pressure only), zj1m, zj, zj1p, zj2p; dm1 / dp1 are the limited density
+    // slopes of zones j-1 / j+1.  Detectors and weights as in the oracle:
+    // steepening where the density has an inflection across a jump of at least
+    // 1% that is a contact, not a shock; flattening where the flow compresses
+    // across a pressure jump above 33%, weighted by the ratio of the 2-zone and
+    // 4-zone pressure differences.
+    __device__ __forceinline__ void dissipate(const MethodParams &mp, const Zone<R> &zj1m, const Zone<R> &zj,
+                                              const Zone<R> &zj1p, const Zone<R> &zj2p, R rj2m, R pj2m, R dm1,
+                                              R dp1, R el[5], R er[5]) const
+    {
+        if (mp.options & ENZO_OPT_STEEPEN) {
+            const R Dm = (zj.r - (R)2 * zj1m.r) + rj2m;
+            const R Dp = (zj2p.r - (R)2 * zj1p.r) + zj.r;
+            const R dr = zj1p.r - zj1m.r;
+            const R rmin = zj1p.r < zj1m.r ? zj1p.r : zj1m.r;
+            const R pmin = zj1p.p < zj1m.p ? zj1p.p : zj1m.p;
+            R et = (R)0;
+            const bool contact = fabs(zj1p.p - zj1m.p) / pmin <= (R)0.1 * k.gamma * (fabs(dr) / rmin);
+            if (Dm * Dp < (R)0 && fabs(dr) >= (R)0.01 * rmin && contact) et = -(Dp - Dm) / ((R)6 * dr);
+            R e = (R)20 * (et - (R)0.05);
+            e = e < (R)0 ? (R)0 : (e > (R)1 ? (R)1 : e);
+            if (e > (R)0) {
+                el[0] = el[0] * ((R)1 - e) + (zj1m.r + (R)0.5 * dm1) * e;
+                er[0] = er[0] * ((R)1 - e) + (zj1p.r - (R)0.5 * dp1) * e;
+            }
+        }
+        if (mp.options & ENZO_OPT_FLATTEN) {
+            const R dp1p = zj1p.p - zj1m.p, dp2p = zj2p.p - pj2m;
+            const R pmin = zj1p.p < zj1m.p ? zj1p.p : zj1m.p;
+            if (zj1m.u - zj1p.u > (R)0 && fabs(dp1p) > (R)0.33 * pmin) {
+                R f = (R)1;
+                if (dp2p != (R)0) {
+                    f = (R)10 * (dp1p / dp2p - (R)0.75);
+                    f = f < (R)0 ? (R)0 : (f > (R)1 ? (R)1 : f);
+                }
+                if (f > (R)0) {
+                    _Pragma("unroll") for (int v = 0; v < 5; ++v)
+                    {
+                        const R q = zv(zj, v);
+                        el[v] = f * q + ((R)1 - f) * el[v];
+                        er[v] = f * q + ((R)1 - f) * er[v];
+                    }
+                }
+            }
+        }
+    }
+
+    // Diffusive flux at the interface between zones a (left) and b (right):
+    // 0.1 max(0, u_a - u_b) times the jump of the conserved state rebuilt from
+    // the zone primitives (CW84; optional in Sec. 4.1).
+    __device__ __forceinline__ void diffuse(const Zone<R> &za, const Zone<R> &zb, R F[5]) const
+    {
+        const R du = za.u - zb.u;
+        if (!(du > (R)0)) return;
+        const R nu = (R)0.1 * du;
+        R Ua[5], Ub[5];
+        const Zone<R> *zs[2] = {&za, &zb};
+        _Pragma("unroll") for (int z = 0; z < 2; ++z)
+        {
+            R *Uz = z ? Ub : Ua;
+            const Zone<R> &q = *zs[z];
+            Uz[0] = q.r;
+            Uz[1] = q.r * q.u;
+            Uz[2] = q.r * q.t1;
+            Uz[3] = q.r * q.t2;
+            Uz[4] = q.p / k.gm1 + (R)0.5 * q.r * ((q.u * q.u + q.t1 * q.t1) + q.t2 * q.t2);
+        }
+        _Pragma("unroll") for (int v = 0; v < 5; ++v) F[v] = F[v] + nu * (Ua[v] - Ub[v]);
+    }
+
     // One pencil with the plain guess: a sliding window over the zones; march
     // step kk loads zone kk and solves interface (kk-3)+1/2.
     template <class GS>
@@ -897,7 +971,16 @@ struct Marcher {
             Gprev2[v] = 0.0;
         }
         z0 = zm1 = zm2 = Zone<R>{};
+        // EXT (steepening, flattening, diffusive flux): zone k-3, density and
+        // pressure of zone k-4, and the density slope of zone k-3
+        Zone<R> zm3{};
+        R r4 = (R)0, p4 = (R)0, ds3 = (R)0;
         for (int kk = 0; kk < L; ++kk) {
+            if constexpr (EXT) {
+                r4 = zm3.r;
+                p4 = zm3.p;
+                zm3 = zm2;
+            }
             zm2 = zm1;
             zm1 = z0;
             z0 = zone<true>(kk, cnt);
@@ -923,7 +1006,18 @@ struct Marcher {
                 if (kk >= 4) {
                     // parabola of zone kk-2 (its edges: qfprev on the left, qfcur on the right)
                     R pL[5], pR[5], pd[5], p6[5];
-                    _Pragma("unroll") for (int v = 0; v < 5; ++v) parabola<R>(zv(zm2, v), qfprev[v], qfcur[v], pL[v], pR[v], pd[v], p6[v]);
+                    if constexpr (EXT) {
+                        R el[5], er[5];
+                        _Pragma("unroll") for (int v = 0; v < 5; ++v)
+                        {
+                            el[v] = qfprev[v];
+                            er[v] = qfcur[v];
+                        }
+                        dissipate(mp, zm3, zm2, zm1, z0, r4, p4, ds3, dcur[0], el, er);
+                        _Pragma("unroll") for (int v = 0; v < 5; ++v) parabola<R>(zv(zm2, v), el[v], er[v], pL[v], pR[v], pd[v], p6[v]);
+                    } else {
+                        _Pragma("unroll") for (int v = 0; v < 5; ++v) parabola<R>(zv(zm2, v), qfprev[v], qfcur[v], pL[v], pR[v], pd[v], p6[v]);
+                    }
                     R sR[5], sLnew[5];
                     trace<R, -1>(pL, pR, pd, p6, zm2.u, zm2.c, dtdx, k, sR);
                     trace<R, +1>(pL, pR, pd, p6, zm2.u, zm2.c, dtdx, k, sLnew);
@@ -947,6 +1041,9 @@ struct Marcher {
                             hllc_states<R>(sLprev, sR, k, Fg);
                         } else {
                             hll_states<R>(sLprev, sR, k, Fg);
+                        }
+                        if constexpr (EXT) {
+                            if (mp.options & ENZO_OPT_DIFFUSE) diffuse(zm3, zm2, Fg);
                         }
                         if (kk >= 6) {
                             // cell c = kk-3: does the Godunov update leave rho > 0?
@@ -993,6 +1090,7 @@ struct Marcher {
                 }
                 _Pragma("unroll") for (int v = 0; v < 5; ++v) qfprev[v] = qfcur[v];
             }
+            if constexpr (EXT) ds3 = dprev[0];
             _Pragma("unroll") for (int v = 0; v < 5; ++v) dprev[v] = dcur[v];
         }
         // last active cell L-4: its right face (L-4)+1/2 borders a ghost zone
@@ -1196,7 +1294,7 @@ __device__ __forceinline__ void warp_flush(unsigned long long *status, unsigned 
 // pencil march a stand-in copy of the tile's first pencil and write nothing).
 // REG: the batch has flux registers (hierarchy levels); the per-pencil register
 // rows are then tracked, otherwise the recording compiles away.
-template <class R, int DIR, bool LEARNED, int THREADS = kSweepThreads, bool REG = false>
+template <class R, int DIR, bool LEARNED, int THREADS = kSweepThreads, bool REG = false, bool EXT = false>
 __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_SWEEP_MIN_BLOCKS_FP32 * 128 / THREADS : 2))
     ppm_sweep_kernel(const __grid_constant__ SweepArgs a)
 {
@@ -1262,11 +1360,11 @@ __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_
             }
         }
         if (P.flags & ENZO_PATCH_PERIODIC) {
-            Marcher<R, true, DIR, REG> m{a, pc, k, valid, key, reg_all, reg_bnd, dt};
+            Marcher<R, true, DIR, REG, EXT> m{a, pc, k, valid, key, reg_all, reg_bnd, dt};
             if constexpr (LEARNED) m.run_piped(dtdx, dtdx64, a.mp, cnt, guess);
             else m.run(dtdx, dtdx64, a.mp, cnt, guess);
         } else {
-            Marcher<R, false, DIR, REG> m{a, pc, k, valid, key, reg_all, reg_bnd, dt};
+            Marcher<R, false, DIR, REG, EXT> m{a, pc, k, valid, key, reg_all, reg_bnd, dt};
             if constexpr (LEARNED) m.run_piped(dtdx, dtdx64, a.mp, cnt, guess);
             else m.run(dtdx, dtdx64, a.mp, cnt, guess);
         }
@@ -1424,6 +1522,24 @@ cudaError_t launch_tiled(const SweepArgs &a, cudaStream_t s)
 template <class R>
 cudaError_t launch_sweep_dir(const SweepArgs &a, int grid, cudaStream_t s)
 {
+    if (a.mp.options) {
+        // the reconstruction options have their own instantiations, so the
+        // default kernels stay as they are
+        if (a.freg) {
+            switch (a.dir) {
+            case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, true, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+            case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, true, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+            default: ppm_sweep_kernel<R, 2, false, kSweepThreads, true, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+            }
+        } else {
+            switch (a.dir) {
+            case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, false, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+            case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, false, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+            default: ppm_sweep_kernel<R, 2, false, kSweepThreads, false, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+            }
+        }
+        return cudaGetLastError();
+    }
     if (a.freg) {
         switch (a.dir) {
         case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, true><<<grid, kSweepThreads, 0, s>>>(a); break;

@@ -107,3 +107,14 @@ def test_solver_selector_rejected_without_gpu():
     fake_blob = ctypes.c_void_p(4096)          # never dereferenced: rejected before any launch
     p = ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=fake_blob.value, solver=ez.SOLVER_HLL).c()
     assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -1
+
+
+def test_reconstruction_options_rejected_without_gpu():
+    L = ez.lib()
+    b = ez._Batch()
+    b.npatch = 0
+    ok = ez.Params(options=ez.OPT_STEEPEN | ez.OPT_FLATTEN | ez.OPT_DIFFUSE).c()
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(ok)) == 0
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(ez.Params(options=8).c())) == -1
+    p = ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=4096, options=ez.OPT_STEEPEN).c()
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -1
