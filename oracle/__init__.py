@@ -48,7 +48,7 @@ class OrParams(ctypes.Structure):
 class OrStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("interfaces", "newton_iters", "newton_nonconv", "hll_cells", "neg_after",
-                 "rho_floor_hits", "p_floor_hits")]
+                 "rho_floor_hits", "p_floor_hits", "ge_pressure")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -109,6 +109,10 @@ def lib():
             L.or_step_boundary.argtypes = five + [_I32, ctypes.c_int32, _D, ctypes.c_double, ctypes.c_int32,
                                                   _I32, ctypes.POINTER(OrParams), ctypes.POINTER(OrStats)]
             L.or_step_boundary.restype = ctypes.c_int
+            L.or_step_periodic_dual.argtypes = five + [_D, _I32, ctypes.c_int32, _D, ctypes.c_double,
+                                                       ctypes.c_int32, ctypes.POINTER(OrParams),
+                                                       ctypes.POINTER(OrStats)]
+            L.or_step_periodic_dual.restype = ctypes.c_int
             L.or_num_threads.argtypes = []
             L.or_num_threads.restype = ctypes.c_int
             L.or_set_num_threads.argtypes = [ctypes.c_int]
@@ -224,6 +228,20 @@ def step_periodic(U, dx, dt, step, params: Params, ng=3) -> dict:
     return st.as_dict()
 
 
+def step_periodic_dual(U, ge, dx, dt, step, params: Params, ng=3) -> dict:
+    """One periodic step with the dual-energy option on; ge (a ghost-zoned
+    array like the fields) is the gas energy rho eps, updated in place."""
+    na, npn = _i32(_n_of(U, ng))
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    p = params.c()
+    st = OrStats()
+    r = lib().or_step_periodic_dual(*_fields(U), _dp(ge), npn, ng, _dp(dxa), dt, step, ctypes.byref(p),
+                                    ctypes.byref(st))
+    if r:
+        raise ValueError("oracle dual-energy step failed (option bit 8 needs the gas-energy field)")
+    return st.as_dict()
+
+
 def evolve_periodic(U, dx, nsteps, params: Params, cfl=0.4, step0=0, ng=3, dts=None):
     """Advance a periodic patch nsteps steps; dt from the CFL rule before each step
     (or from `dts` when given).  Returns (list of dt, summed stats)."""
@@ -250,7 +268,7 @@ def riemann(rl, ul, pl, rr, ur, pr, params: Params, pguess=None):
 
 
 SOLVER_TWOSHOCK, SOLVER_HLL, SOLVER_HLLC = 0, 1, 2
-OPT_STEEPEN, OPT_FLATTEN, OPT_DIFFUSE = 1, 2, 4
+OPT_STEEPEN, OPT_FLATTEN, OPT_DIFFUSE, OPT_DUAL = 1, 2, 4, 8
 
 
 def flux(left, right, params: Params, solver="twoshock"):

@@ -61,7 +61,8 @@ typedef struct {
     int32_t newton_max;
     int32_t fallback;     /* 1: HLL re-flux of cells that reach rho <= 0 */
     int32_t solver;       /* interface fluxes: 0 two-shock (Sec. 4.1.2), 1 HLL, 2 HLLC */
-    int32_t options;      /* bit 0 contact steepening, bit 1 flattening, bit 2 diffusive flux */
+    int32_t options;      /* bit 0 contact steepening, bit 1 flattening, bit 2 diffusive flux,
+                             bit 3 dual energy (a gas-energy field rides along, see pencil_step) */
 } or_params;
 
 typedef struct {
@@ -72,6 +73,7 @@ typedef struct {
     int64_t neg_after;       /* cells with rho <= 0 after the fallback */
     int64_t rho_floor_hits;  /* cell primitives raised to rho_floor */
     int64_t p_floor_hits;    /* cell primitives raised to p_floor */
+    int64_t ge_pressure;     /* dual energy: zones whose pressure came from the gas energy */
 } or_stats;
 
 /* ----------------------------------------------------------------------- */
@@ -300,29 +302,31 @@ static void hllc_flux(double rl, double ul, double pl, double t1l, double t2l,
 /* Pencil arrays, length L = n + 2 ng.  var index: 0 rho, 1 u_n, 2 p, 3 u_t1, 4 u_t2 */
 typedef struct {
     int L;
-    double *U[5];       /* conserved along the pencil: rho, m_n, m_t1, m_t2, E */
-    double *q[5];       /* primitives */
+    double *U[6];       /* conserved along the pencil: rho, m_n, m_t1, m_t2, E (and, with
+                           dual energy, the gas energy ge = rho eps) */
+    double *q[6];       /* primitives (index 5: specific internal energy eps) */
     double *c;          /* zone sound speed */
-    double *dq[5];      /* limited slopes */
-    double *qf[5];      /* unlimited interface values q_{s+1/2} */
-    double *qL[5], *qR[5], *d[5], *q6[5];   /* monotone parabola per zone */
-    double *sL[5];      /* left state at interface s+1/2 (from zone s) */
-    double *sR[5];      /* right state at interface s-1/2 (from zone s) */
-    double *F[5];       /* flux at interface s+1/2 */
-    double *Uold[5];
+    double *dq[6];      /* limited slopes */
+    double *qf[6];      /* unlimited interface values q_{s+1/2} */
+    double *qL[6], *qR[6], *d[6], *q6[6];   /* monotone parabola per zone */
+    double *sL[6];      /* left state at interface s+1/2 (from zone s) */
+    double *sR[6];      /* right state at interface s-1/2 (from zone s) */
+    double *F[6];       /* flux at interface s+1/2 */
+    double *Uold[6];
     double *eta;        /* contact-steepening weight per zone */
     double *flat;       /* flattening weight per zone */
+    double *uface;      /* dual energy: velocity at interface s+1/2 */
     double *buf;
 } pencil;
 
 static int pencil_alloc(pencil *pc, int L)
 {
-    int narr = 5 * 13 + 3;
+    int narr = 6 * 13 + 4;
     pc->L = L;
     pc->buf = (double *)calloc((size_t)narr * (size_t)L, sizeof(double));
     if (!pc->buf) return -1;
     double *b = pc->buf;
-    for (int v = 0; v < 5; ++v) {
+    for (int v = 0; v < 6; ++v) {
         pc->U[v] = b; b += L;  pc->q[v] = b; b += L;  pc->dq[v] = b; b += L;
         pc->qf[v] = b; b += L; pc->qL[v] = b; b += L; pc->qR[v] = b; b += L;
         pc->d[v] = b; b += L;  pc->q6[v] = b; b += L; pc->sL[v] = b; b += L;
@@ -331,7 +335,8 @@ static int pencil_alloc(pencil *pc, int L)
     }
     pc->c = b; b += L;
     pc->eta = b; b += L;
-    pc->flat = b;
+    pc->flat = b; b += L;
+    pc->uface = b;
     return 0;
 }
 
@@ -400,17 +405,17 @@ static double avg_left(double qL, double d, double q6, double sig)
  * side = +1: left state of the interface at the zone's right edge (waves with
  * lambda > 0 reach it); side = -1: right state of the interface at its left edge. */
 static void trace_state(const pencil *pc, int s, int side, double dtdx, const or_params *P,
-                        double out[5])
+                        int nv, double out[6])
 {
     const double gamma = P->gamma;
     double u = pc->q[1][s], c = pc->c[s];
     double lam[3] = { u - c, u, u + c };        /* -, 0, + waves */
     int reach[3];
-    double I[3][5];
+    double I[3][6];
     for (int w = 0; w < 3; ++w) {
         reach[w] = side > 0 ? lam[w] > 0.0 : lam[w] < 0.0;
         double sig = side > 0 ? lam[w] * dtdx : -lam[w] * dtdx;
-        for (int v = 0; v < 5; ++v) {
+        for (int v = 0; v < nv; ++v) {
             if (side > 0) I[w][v] = avg_right(pc->qR[v][s], pc->d[v][s], pc->q6[v][s], sig);
             else          I[w][v] = avg_left(pc->qL[v][s], pc->d[v][s], pc->q6[v][s], sig);
         }
@@ -435,7 +440,7 @@ static void trace_state(const pencil *pc, int s, int side, double dtdx, const or
     if (!(rho > P->rho_floor)) rho = P->rho_floor;
     if (!(p > P->p_floor)) p = P->p_floor;
     out[0] = rho; out[1] = un; out[2] = p;
-    for (int v = 3; v < 5; ++v) {
+    for (int v = 3; v < nv; ++v) {      /* transverse velocities and eps: passive */
         if (reach[1]) out[v] = I[1][v];
         else out[v] = side > 0 ? pc->qR[v][s] : pc->qL[v][s];
     }
@@ -443,28 +448,43 @@ static void trace_state(const pencil *pc, int s, int side, double dtdx, const or
 
 /* Advance one pencil (already gathered into pc->U) by the split update along it.
  * Active cells are [ng, L-ng).  Returns nothing; pc->U is overwritten. */
+/* Dual energy (Sec. 4.1, the dual-energy formalism: eta1 = 1e-3, eta2 = 0.1),
+ * the reading taken here:
+ *   pressure: from E - KE, or from the gas energy ge where E - KE < eta1 E;
+ *   ge = rho eps is carried with eps = ge / rho reconstructed, traced and
+ *   upwinded (by the sign of u*) like a transverse velocity, its flux the mass
+ *   flux times eps, and the source -p (u_{j+1/2} - u_{j-1/2}) dt/dx with the
+ *   zone pressure and the Godunov interface velocities; faces re-fluxed by the
+ *   HLL fallback carry the HLL mass flux times the upwind zone eps and the mean
+ *   of the two zone velocities;
+ *   after the update ge is reset to E - KE where that exceeds eta2 E. */
 static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_stats *st)
 {
     const int L = pc->L;
     const double gamma = P->gamma;
+    const int dual = (P->options & 8) != 0;
+    const int nv = dual ? 6 : 5;
     /* (a) primitives, Sec. 2.1 / 4.1 */
     for (int s = 0; s < L; ++s) {
         double rho = pc->U[0][s];
         if (!(rho >= P->rho_floor)) { rho = P->rho_floor; st->rho_floor_hits++; }
         double mn = pc->U[1][s], m1 = pc->U[2][s], m2 = pc->U[3][s], E = pc->U[4][s];
         double ke = 0.5 * ((mn * mn + m1 * m1) + m2 * m2) / rho;
-        double p = (gamma - 1.0) * (E - ke);
+        double p;
+        if (dual && E - ke < 1e-3 * E) { p = (gamma - 1.0) * pc->U[5][s]; st->ge_pressure++; }
+        else p = (gamma - 1.0) * (E - ke);
         if (!(p >= P->p_floor)) { p = P->p_floor; st->p_floor_hits++; }
         pc->q[0][s] = rho;
         pc->q[1][s] = mn / rho;
         pc->q[2][s] = p;
         pc->q[3][s] = m1 / rho;
         pc->q[4][s] = m2 / rho;
+        if (dual) pc->q[5][s] = pc->U[5][s] / rho;
         pc->c[s] = sqrt(gamma * p / rho);
     }
     dissipation_weights(pc, P);
     /* (b) limited slopes, CW84 1.7-1.8 */
-    for (int v = 0; v < 5; ++v) {
+    for (int v = 0; v < nv; ++v) {
         const double *q = pc->q[v];
         for (int s = 1; s < L - 1; ++s) {
             double dl = q[s] - q[s - 1];
@@ -512,20 +532,20 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
     }
     /* (d,e) characteristic states at the interfaces that bound active cells */
     for (int s = ng - 1; s <= L - ng - 1; ++s) {
-        double st5[5];
-        trace_state(pc, s, +1, dtdx, P, st5);
-        for (int v = 0; v < 5; ++v) pc->sL[v][s] = st5[v];
+        double st6[6];
+        trace_state(pc, s, +1, dtdx, P, nv, st6);
+        for (int v = 0; v < nv; ++v) pc->sL[v][s] = st6[v];
     }
     for (int s = ng; s <= L - ng; ++s) {
-        double st5[5];
-        trace_state(pc, s, -1, dtdx, P, st5);
-        for (int v = 0; v < 5; ++v) pc->sR[v][s] = st5[v];
+        double st6[6];
+        trace_state(pc, s, -1, dtdx, P, nv, st6);
+        for (int v = 0; v < nv; ++v) pc->sR[v][s] = st6[v];
     }
     /* (f,g) Riemann problem and flux at interface s+1/2, s = ng-1 .. L-ng-1 */
     for (int s = ng - 1; s <= L - ng - 1; ++s) {
         double rl = pc->sL[0][s], ul = pc->sL[1][s], pl = pc->sL[2][s];
         double rr = pc->sR[0][s + 1], ur = pc->sR[1][s + 1], pr = pc->sR[2][s + 1];
-        double F[5];
+        double F[6];
         st->interfaces++;
         if (P->solver == 1) {
             hll_flux(rl, ul, pl, pc->sL[3][s], pc->sL[4][s], rr, ur, pr, pc->sR[3][s + 1], pc->sR[4][s + 1],
@@ -541,6 +561,10 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
             double t1 = o.ustar >= 0.0 ? pc->sL[3][s] : pc->sR[3][s + 1];
             double t2 = o.ustar >= 0.0 ? pc->sL[4][s] : pc->sR[4][s + 1];
             phys_flux(o.rho, o.u, o.p, t1, t2, gamma, F);
+            if (dual) {
+                F[5] = F[0] * (o.ustar >= 0.0 ? pc->sL[5][s] : pc->sR[5][s + 1]);
+                pc->uface[s] = o.u;
+            }
         }
         if (P->options & 4) {
             /* diffusive flux (CW84; optional in Sec. 4.1): 0.1 max(0, u_s - u_{s+1})
@@ -549,7 +573,7 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
             double du = pc->q[1][s] - pc->q[1][s + 1];
             if (du > 0.0) {
                 double nu = 0.1 * du;
-                double Ua[5], Ub[5];
+                double Ua[6], Ub[6];
                 for (int z = 0; z < 2; ++z) {
                     double *Uz = z ? Ub : Ua;
                     int c = s + z;
@@ -557,41 +581,65 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
                     double t1 = pc->q[3][c], t2 = pc->q[4][c];
                     Uz[0] = r; Uz[1] = r * u; Uz[2] = r * t1; Uz[3] = r * t2;
                     Uz[4] = pz / (gamma - 1.0) + 0.5 * r * ((u * u + t1 * t1) + t2 * t2);
+                    if (dual) Uz[5] = r * pc->q[5][c];
                 }
-                for (int v = 0; v < 5; ++v) F[v] = F[v] + nu * (Ua[v] - Ub[v]);
+                for (int v = 0; v < nv; ++v) F[v] = F[v] + nu * (Ua[v] - Ub[v]);
             }
         }
-        for (int v = 0; v < 5; ++v) pc->F[v][s] = F[v];
+        for (int v = 0; v < nv; ++v) pc->F[v][s] = F[v];
     }
-    /* (h) conservative update of active cells, FP64 */
-    for (int v = 0; v < 5; ++v)
+    /* (h) conservative update of active cells, FP64 (and the gas energy) */
+    for (int v = 0; v < nv; ++v)
         for (int s = 0; s < L; ++s) pc->Uold[v][s] = pc->U[v][s];
-    for (int s = ng; s < L - ng; ++s)
-        for (int v = 0; v < 5; ++v)
-            pc->U[v][s] = pc->Uold[v][s] + dtdx * (pc->F[v][s - 1] - pc->F[v][s]);
-    if (!P->fallback) return;
-    /* HLL fallback (Sec. 4.1.2): re-flux both faces of each cell with rho <= 0 */
-    int nbad = 0;
-    for (int s = ng; s < L - ng; ++s) if (!(pc->U[0][s] > 0.0)) nbad++;
-    if (!nbad) return;
-    char *mark = (char *)calloc((size_t)L, 1);       /* mark[s]: interface s+1/2 */
-    for (int s = ng; s < L - ng; ++s)
-        if (!(pc->U[0][s] > 0.0)) { mark[s - 1] = 1; mark[s] = 1; st->hll_cells++; }
-    for (int s = ng - 1; s <= L - ng - 1; ++s) {
-        if (!mark[s]) continue;
-        double F[5];
-        hll_flux(pc->q[0][s], pc->q[1][s], pc->q[2][s], pc->q[3][s], pc->q[4][s],
-                 pc->q[0][s + 1], pc->q[1][s + 1], pc->q[2][s + 1], pc->q[3][s + 1], pc->q[4][s + 1],
-                 gamma, F);
-        for (int v = 0; v < 5; ++v) pc->F[v][s] = F[v];
-    }
     for (int s = ng; s < L - ng; ++s) {
-        if (!mark[s - 1] && !mark[s]) continue;
         for (int v = 0; v < 5; ++v)
             pc->U[v][s] = pc->Uold[v][s] + dtdx * (pc->F[v][s - 1] - pc->F[v][s]);
-        if (!(pc->U[0][s] > 0.0)) st->neg_after++;
+        if (dual)
+            pc->U[5][s] = (pc->Uold[5][s] + dtdx * (pc->F[5][s - 1] - pc->F[5][s])) -
+                          dtdx * pc->q[2][s] * (pc->uface[s] - pc->uface[s - 1]);
     }
-    free(mark);
+    if (P->fallback) {
+        /* HLL fallback (Sec. 4.1.2): re-flux both faces of each cell with rho <= 0 */
+        int nbad = 0;
+        for (int s = ng; s < L - ng; ++s) if (!(pc->U[0][s] > 0.0)) nbad++;
+        if (nbad) {
+            char *mark = (char *)calloc((size_t)L, 1);       /* mark[s]: interface s+1/2 */
+            for (int s = ng; s < L - ng; ++s)
+                if (!(pc->U[0][s] > 0.0)) { mark[s - 1] = 1; mark[s] = 1; st->hll_cells++; }
+            for (int s = ng - 1; s <= L - ng - 1; ++s) {
+                if (!mark[s]) continue;
+                double F[5];
+                hll_flux(pc->q[0][s], pc->q[1][s], pc->q[2][s], pc->q[3][s], pc->q[4][s],
+                         pc->q[0][s + 1], pc->q[1][s + 1], pc->q[2][s + 1], pc->q[3][s + 1], pc->q[4][s + 1],
+                         gamma, F);
+                for (int v = 0; v < 5; ++v) pc->F[v][s] = F[v];
+                if (dual) {
+                    pc->F[5][s] = F[0] * (F[0] >= 0.0 ? pc->q[5][s] : pc->q[5][s + 1]);
+                    pc->uface[s] = 0.5 * (pc->q[1][s] + pc->q[1][s + 1]);
+                }
+            }
+            for (int s = ng; s < L - ng; ++s) {
+                if (!mark[s - 1] && !mark[s]) continue;
+                for (int v = 0; v < 5; ++v)
+                    pc->U[v][s] = pc->Uold[v][s] + dtdx * (pc->F[v][s - 1] - pc->F[v][s]);
+                if (dual)
+                    pc->U[5][s] = (pc->Uold[5][s] + dtdx * (pc->F[5][s - 1] - pc->F[5][s])) -
+                                  dtdx * pc->q[2][s] * (pc->uface[s] - pc->uface[s - 1]);
+                if (!(pc->U[0][s] > 0.0)) st->neg_after++;
+            }
+            free(mark);
+        }
+    }
+    if (dual) {
+        /* gas energy resynchronised where E - KE is reliable */
+        for (int s = ng; s < L - ng; ++s) {
+            double rho = pc->U[0][s], E = pc->U[4][s];
+            if (!(rho > 0.0)) continue;
+            double ke = 0.5 * ((pc->U[1][s] * pc->U[1][s] + pc->U[2][s] * pc->U[2][s]) +
+                               pc->U[3][s] * pc->U[3][s]) / rho;
+            if (E - ke > 0.1 * E) pc->U[5][s] = E - ke;
+        }
+    }
 }
 
 /* ----------------------------------------------------------------------- */
@@ -719,12 +767,35 @@ int or_sweep(double *U0, double *U1, double *U2, double *U3, double *U4,
     return or_sweep_fluxes(U0, U1, U2, U3, U4, n, ng, dx, dir, dt, lo, hi, P, stats, NULL);
 }
 
+static int sweep_ge(double *U0, double *U1, double *U2, double *U3, double *U4, double *ge,
+                    const int32_t n[3], int32_t ng, const double dx[3], int32_t dir, double dt,
+                    const int32_t lo[3], const int32_t hi[3], const or_params *P, or_stats *stats,
+                    double *fout);
+
 int or_sweep_fluxes(double *U0, double *U1, double *U2, double *U3, double *U4,
                     const int32_t n[3], int32_t ng, const double dx[3], int32_t dir, double dt,
                     const int32_t lo[3], const int32_t hi[3], const or_params *P, or_stats *stats,
                     double *fout)
 {
+    return sweep_ge(U0, U1, U2, U3, U4, NULL, n, ng, dx, dir, dt, lo, hi, P, stats, fout);
+}
+
+/* As or_sweep, with the gas-energy field ge of the dual-energy option (may be
+ * NULL when the option is off). */
+int or_sweep_dual(double *U0, double *U1, double *U2, double *U3, double *U4, double *ge,
+                  const int32_t n[3], int32_t ng, const double dx[3], int32_t dir, double dt,
+                  const int32_t lo[3], const int32_t hi[3], const or_params *P, or_stats *stats)
+{
+    return sweep_ge(U0, U1, U2, U3, U4, ge, n, ng, dx, dir, dt, lo, hi, P, stats, NULL);
+}
+
+static int sweep_ge(double *U0, double *U1, double *U2, double *U3, double *U4, double *ge,
+                    const int32_t n[3], int32_t ng, const double dx[3], int32_t dir, double dt,
+                    const int32_t lo[3], const int32_t hi[3], const or_params *P, or_stats *stats,
+                    double *fout)
+{
     double *U[5] = { U0, U1, U2, U3, U4 };
+    if ((P->options & 8) && !ge) return -2;
     int N[3] = { n[0] + 2 * ng, n[1] + 2 * ng, n[2] + 2 * ng };
     int a1 = dir == 0 ? 1 : 0;           /* transverse axes in increasing order */
     int a2 = dir == 2 ? 1 : 2;
@@ -753,9 +824,13 @@ int or_sweep_fluxes(double *U0, double *U1, double *U2, double *U3, double *U4,
             int mi[5] = { 0, 1 + dir, 1 + a1, 1 + a2, 4 };
             for (int s = 0; s < L; ++s)
                 for (int v = 0; v < 5; ++v) pc.U[v][s] = U[mi[v]][base + s * stride[dir]];
+            if (ge)
+                for (int s = 0; s < L; ++s) pc.U[5][s] = ge[base + s * stride[dir]];
             pencil_step(&pc, ng, dtdx, P, &st);
             for (int s = ng; s < L - ng; ++s)
                 for (int v = 0; v < 5; ++v) U[mi[v]][base + s * stride[dir]] = pc.U[v][s];
+            if (ge)
+                for (int s = ng; s < L - ng; ++s) ge[base + s * stride[dir]] = pc.U[5][s];
             if (fout) {
                 int j1 = i1 - ng, j2 = i2 - ng;
                 if (j1 >= 0 && j1 < n[a1] && j2 >= 0 && j2 < n[a2]) {
@@ -771,14 +846,14 @@ int or_sweep_fluxes(double *U0, double *U1, double *U2, double *U3, double *U4,
             tot.interfaces += st.interfaces; tot.newton_iters += st.newton_iters;
             tot.newton_nonconv += st.newton_nonconv; tot.hll_cells += st.hll_cells;
             tot.neg_after += st.neg_after; tot.rho_floor_hits += st.rho_floor_hits;
-            tot.p_floor_hits += st.p_floor_hits;
+            tot.p_floor_hits += st.p_floor_hits; tot.ge_pressure += st.ge_pressure;
         }
     }
     if (stats) {
         stats->interfaces += tot.interfaces; stats->newton_iters += tot.newton_iters;
         stats->newton_nonconv += tot.newton_nonconv; stats->hll_cells += tot.hll_cells;
         stats->neg_after += tot.neg_after; stats->rho_floor_hits += tot.rho_floor_hits;
-        stats->p_floor_hits += tot.p_floor_hits;
+        stats->p_floor_hits += tot.p_floor_hits; stats->ge_pressure += tot.ge_pressure;
     }
     return err ? -1 : 0;
 }
@@ -788,6 +863,32 @@ void or_sweep_order(int32_t step, int32_t order[3])
 {
     if (step % 2 == 0) { order[0] = 0; order[1] = 1; order[2] = 2; }
     else               { order[0] = 2; order[1] = 1; order[2] = 0; }
+}
+
+/* One full step of a periodic patch with the dual-energy gas-energy field ge:
+ * ghost fill of U and ge, then the three split sweeps with transverse coverage. */
+int or_step_periodic_dual(double *U0, double *U1, double *U2, double *U3, double *U4, double *ge,
+                          const int32_t n[3], int32_t ng, const double dx[3], double dt,
+                          int32_t step, const or_params *P, or_stats *stats)
+{
+    int32_t order[3];
+    or_sweep_order(step, order);
+    or_fill_periodic(U0, U1, U2, U3, U4, n, ng);
+    or_fill_periodic(ge, ge, ge, ge, ge, n, ng);
+    int N[3] = { n[0] + 2 * ng, n[1] + 2 * ng, n[2] + 2 * ng };
+    int done[3] = { 0, 0, 0 };
+    for (int q = 0; q < 3; ++q) {
+        int d = order[q];
+        int32_t lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            if (done[a]) { lo[a] = ng; hi[a] = ng + n[a]; }
+            else         { lo[a] = 0;  hi[a] = N[a]; }
+        }
+        int r = or_sweep_dual(U0, U1, U2, U3, U4, ge, n, ng, dx, d, dt, lo, hi, P, stats);
+        if (r) return r;
+        done[d] = 1;
+    }
+    return 0;
 }
 
 /* One full step of a single grid with external boundaries bc[3] (as in
