@@ -73,6 +73,7 @@ enum {
     ENZO_ST_GUESS_RESTARTS = 10, /* learned guess abandoned for the plain guess */
     ENZO_ST_GUESS_CALLS = 11, /* interfaces given a learned guess (those past the gate) */
     ENZO_ST_TIMEOUT = 12,     /* bounded waits that ran out (tensor-core kernels) */
+    ENZO_ST_GE_PRESSURE = 13, /* ENZO_OPT_DUAL: zone loads whose pressure came from the gas energy */
     ENZO_STATUS_WORDS = 16
 };
 
@@ -116,6 +117,10 @@ typedef struct {
     unsigned long long *status;   /* DEVICE counters [ENZO_STATUS_WORDS]; added to */
     void *stream;                 /* cudaStream_t */
     double *freg;                 /* DEVICE flux registers (see enzo_patch.freg_*), or NULL */
+    double *ge;                   /* DEVICE gas-energy field rho e (field_len elements, same
+                                     layout as U), or NULL: read and updated only by
+                                     sweeps with ENZO_OPT_DUAL, carried by the ghost fills
+                                     whenever non-NULL */
 } enzo_patch_batch;
 
 /* Interface flux solvers (Sec. 4.1.2): the two-shock Riemann solver with a
@@ -128,8 +133,19 @@ enum { ENZO_SOLVER_TWOSHOCK = 0, ENZO_SOLVER_HLL = 1, ENZO_SOLVER_HLLC = 2 };
  * steepening of the density at contacts, flattening of every variable in zones
  * that compress across a strong pressure jump (the zone's own weight: the
  * stencil stays within three ghost zones), and a flux 0.1 max(0, u_L - u_R)
- * (U_L - U_R) at compressive interfaces. */
-enum { ENZO_OPT_STEEPEN = 1, ENZO_OPT_FLATTEN = 2, ENZO_OPT_DIFFUSE = 4 };
+ * (U_L - U_R) at compressive interfaces.
+ * ENZO_OPT_DUAL: the dual energy formulation (Sec. 4.1.1): the batch's ge field
+ * (the gas energy rho e) is advected with the mass flux, eps = ge / rho
+ * reconstructed and traced like a transverse velocity and upwinded by the sign
+ * of u*, plus the source -p_j (u_{j+1/2} - u_{j-1/2}) dt/dx with the zone
+ * pressure at the start of the sweep and the Riemann interface velocities
+ * (faces re-fluxed by the HLL fallback: the HLL mass flux times the upwind zone
+ * eps, the mean zone velocity).  A zone takes its pressure from ge where
+ * E - KE < 1e-3 E (eta1), decided in FP64 in both precisions; after the update
+ * ge is reset to E - KE where that exceeds 0.1 (eta2) times the largest E of the
+ * cell and its two neighbours along the sweep.  Needs the two-shock solver, a
+ * non-NULL ge and no flux registers (ENZO_ERR_ARG otherwise). */
+enum { ENZO_OPT_STEEPEN = 1, ENZO_OPT_FLATTEN = 2, ENZO_OPT_DIFFUSE = 4, ENZO_OPT_DUAL = 8 };
 
 /* Method parameters (Sec. 4.1, 4.1.2, 9). */
 typedef struct {

@@ -448,16 +448,17 @@ static void trace_state(const pencil *pc, int s, int side, double dtdx, const or
 
 /* Advance one pencil (already gathered into pc->U) by the split update along it.
  * Active cells are [ng, L-ng).  Returns nothing; pc->U is overwritten. */
-/* Dual energy (Sec. 4.1, the dual-energy formalism: eta1 = 1e-3, eta2 = 0.1),
- * the reading taken here:
+/* Dual energy (Sec. 4.1.1: eta1 = 1e-3, eta2 = 0.1), the reading taken here:
  *   pressure: from E - KE, or from the gas energy ge where E - KE < eta1 E;
  *   ge = rho eps is carried with eps = ge / rho reconstructed, traced and
  *   upwinded (by the sign of u*) like a transverse velocity, its flux the mass
  *   flux times eps, and the source -p (u_{j+1/2} - u_{j-1/2}) dt/dx with the
- *   zone pressure and the Godunov interface velocities; faces re-fluxed by the
- *   HLL fallback carry the HLL mass flux times the upwind zone eps and the mean
- *   of the two zone velocities;
- *   after the update ge is reset to E - KE where that exceeds eta2 E. */
+ *   zone pressure at the start of the sweep and the Godunov interface
+ *   velocities (the printed update's flux-difference sign is taken as garbled,
+ *   as for the other fields); faces re-fluxed by the HLL fallback carry the HLL
+ *   mass flux times the upwind zone eps and the mean of the two zone velocities;
+ *   after the update ge is reset to E - KE where that exceeds eta2 times the
+ *   largest E of the cell and its two pencil neighbours. */
 static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_stats *st)
 {
     const int L = pc->L;
@@ -631,13 +632,18 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
         }
     }
     if (dual) {
-        /* gas energy resynchronised where E - KE is reliable */
+        /* gas energy resynchronised where E - KE is reliable (Sec. 4.1.1, the selection of e):
+         * E - KE above eta2 times the largest total energy of the cell and its two neighbours
+         * along the pencil, all after the update (the ghost neighbours keep their values) */
         for (int s = ng; s < L - ng; ++s) {
             double rho = pc->U[0][s], E = pc->U[4][s];
             if (!(rho > 0.0)) continue;
             double ke = 0.5 * ((pc->U[1][s] * pc->U[1][s] + pc->U[2][s] * pc->U[2][s]) +
                                pc->U[3][s] * pc->U[3][s]) / rho;
-            if (E - ke > 0.1 * E) pc->U[5][s] = E - ke;
+            double emax = pc->U[4][s - 1];
+            if (E > emax) emax = E;
+            if (pc->U[4][s + 1] > emax) emax = pc->U[4][s + 1];
+            if (E - ke > 0.1 * emax) pc->U[5][s] = E - ke;
         }
     }
 }

@@ -20,12 +20,12 @@ from . import _build
 FP64, FP32 = 0, 1
 GUESS_PLAIN, GUESS_MLP = 0, 1
 SOLVER_TWOSHOCK, SOLVER_HLL, SOLVER_HLLC = 0, 1, 2
-OPT_STEEPEN, OPT_FLATTEN, OPT_DIFFUSE = 1, 2, 4
+OPT_STEEPEN, OPT_FLATTEN, OPT_DIFFUSE, OPT_DUAL = 1, 2, 4, 8
 PATCH_PERIODIC = 1
 STATUS_WORDS = 16
 STATUS_NAMES = ("interfaces", "newton_iters", "newton_nonconv", "hll_cells", "neg_after",
                 "rho_floor_hits", "p_floor_hits", "nan", "bad_patch", "fp64_eke",
-                "guess_restarts", "guess_calls", "timeout")
+                "guess_restarts", "guess_calls", "timeout", "ge_pressure")
 
 PATCH_DTYPE = np.dtype([("n", "<i4", (3,)), ("ng", "<i4"), ("off", "<i8"), ("dx", "<f8", (3,)),
                         ("level", "<i4"), ("flags", "<i4"), ("freg_all", "<i8"), ("freg_bnd", "<i8")])
@@ -41,7 +41,7 @@ class _Batch(ctypes.Structure):
                 ("patches", ctypes.c_void_p), ("field_len", ctypes.c_int64),
                 ("U", ctypes.c_void_p * 5), ("workspace", ctypes.c_void_p),
                 ("ws_bytes", ctypes.c_size_t), ("status", ctypes.c_void_p),
-                ("stream", ctypes.c_void_p), ("freg", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("freg", ctypes.c_void_p), ("ge", ctypes.c_void_p)]
 
 
 class _Params(ctypes.Structure):
@@ -153,7 +153,10 @@ class PatchBatch:
     """A batch of patches sharing one timestep, with device fields, descriptors,
     workspace and status counters held in torch tensors on one CUDA device."""
 
-    def __init__(self, table: np.ndarray, fields, device="cuda", stream=None):
+    def __init__(self, table: np.ndarray, fields, device="cuda", stream=None, ge=None):
+        """fields: the five conserved fields (rho, m_x, m_y, m_z, E), flat over
+        the batch's storage; ge: optional gas-energy field rho e of the same
+        length (needed by sweeps with OPT_DUAL, carried by the ghost fills)."""
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -176,6 +179,13 @@ class PatchBatch:
         self.stream = stream
         self._ws_bytes = ws
         self.freg = None
+        self.ge = None
+        if ge is not None:
+            if isinstance(ge, torch.Tensor):
+                self.ge = ge.to(self.device, torch.float64).contiguous()
+            else:
+                self.ge = torch.from_numpy(np.ascontiguousarray(ge, dtype=np.float64)).to(self.device)
+            assert int(self.ge.numel()) == self.field_len
 
     def c(self) -> _Batch:
         b = _Batch()
@@ -190,6 +200,7 @@ class PatchBatch:
         s = self.stream if self.stream is not None else self.torch.cuda.current_stream(self.device)
         b.stream = s.cuda_stream
         b.freg = self.freg.data_ptr() if self.freg is not None else None
+        b.ge = self.ge.data_ptr() if self.ge is not None else None
         return b
 
     def read_status(self) -> dict:
@@ -206,6 +217,14 @@ class PatchBatch:
         off = int(self.table["off"][i])
         cnt = (nx + 2 * g) * (ny + 2 * g) * (nz + 2 * g)
         return [u[off:off + cnt].view(nz + 2 * g, ny + 2 * g, nx + 2 * g) for u in self.U]
+
+    def patch_ge(self, i):
+        """Device view (z, y, x) of patch i's stored gas energy (OPT_DUAL)."""
+        nx, ny, nz = (int(v) for v in self.table["n"][i])
+        g = int(self.table["ng"][i])
+        off = int(self.table["off"][i])
+        cnt = (nx + 2 * g) * (ny + 2 * g) * (nz + 2 * g)
+        return self.ge[off:off + cnt].view(nz + 2 * g, ny + 2 * g, nx + 2 * g)
 
 
 def ppm_sweep(batch: PatchBatch, direction: int, dt: float, cover_mask: int, params: Params):

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(1024) prefix_kernel(const enzo_patch *patches,
 // active cell it wraps onto, edges and corners included.
 __global__ void __launch_bounds__(kFillThreads) ghost_fill_kernel(const enzo_patch *patches, int npatch,
                                                                   double *U0, double *U1, double *U2,
-                                                                  double *U3, double *U4,
+                                                                  double *U3, double *U4, double *ge,
                                                                   const int *prefix)
 {
     const int total = prefix[npatch];
@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(kFillThreads) ghost_fill_kernel(const enzo_pat
         U2[dst] = U2[s];
         U3[dst] = U3[s];
         U4[dst] = U4[s];
+        if (ge) ge[dst] = ge[s];
     }
 }
 
@@ -137,8 +138,8 @@ __device__ __forceinline__ int bc_map(int x, int n, int bc, bool &flip)
 
 __global__ void __launch_bounds__(kFillThreads) boundary_fill_kernel(const enzo_patch *patches, int npatch,
                                                                      double *U0, double *U1, double *U2,
-                                                                     double *U3, double *U4, const int *prefix,
-                                                                     int bcx, int bcy, int bcz)
+                                                                     double *U3, double *U4, double *ge,
+                                                                     const int *prefix, int bcx, int bcy, int bcz)
 {
     double *const U[5] = {U0, U1, U2, U3, U4};
     const int bc[3] = {bcx, bcy, bcz};
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(kFillThreads) boundary_fill_kernel(const enzo_
         const int64_t s = P.off + src[0] + (int64_t)N0 * (src[1] + (int64_t)N1 * src[2]);
         U[0][dst] = U[0][s];
         U[4][dst] = U[4][s];
+        if (ge) ge[dst] = ge[s];
         for (int d = 0; d < 3; ++d) U[1 + d][dst] = flip[d] ? -U[1 + d][s] : U[1 + d][s];
     }
 }
@@ -206,8 +208,9 @@ static int resolve(const enzo_params *p, MethodParams &m)
         return ENZO_ERR_ARG;
     if (p->guess == ENZO_GUESS_MLP && p->solver != ENZO_SOLVER_TWOSHOCK) return ENZO_ERR_ARG;
     m.solver = p->solver;
-    if (p->options & ~(ENZO_OPT_STEEPEN | ENZO_OPT_FLATTEN | ENZO_OPT_DIFFUSE)) return ENZO_ERR_ARG;
+    if (p->options & ~(ENZO_OPT_STEEPEN | ENZO_OPT_FLATTEN | ENZO_OPT_DIFFUSE | ENZO_OPT_DUAL)) return ENZO_ERR_ARG;
     if (p->guess == ENZO_GUESS_MLP && p->options) return ENZO_ERR_ARG;
+    if ((p->options & ENZO_OPT_DUAL) && p->solver != ENZO_SOLVER_TWOSHOCK) return ENZO_ERR_ARG;
     m.options = p->options;
     return ENZO_OK;
 }
@@ -260,6 +263,7 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
                       int cover, const MethodParams &m, int precision, int tile_pencils, float *log = nullptr,
                       unsigned long long *log_count = nullptr, long long log_cap = 0, int log_stride = 0)
 {
+    if ((m.options & ENZO_OPT_DUAL) && (!b->ge || b->freg)) return ENZO_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
     int tile = tile_pencils > 0 ? tile_pencils : kSweepThreads;
     if (precision == ENZO_FP64 || m.guess == ENZO_GUESS_MLP || b->freg || m.options) tile = kSweepThreads;
@@ -280,6 +284,7 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
     a.tile_counter = reinterpret_cast<unsigned *>(ws(b) + kWsCounter);
     a.status = b->status;
     a.freg = b->freg;
+    a.ge = (m.options & ENZO_OPT_DUAL) ? b->ge : nullptr;
     a.log = log;
     a.log_count = log_count;
     a.log_cap = log_cap;
@@ -301,7 +306,7 @@ static int fill_impl(const enzo_patch_batch *b)
     int r = launch_prefix(b, kKindFill, 0, 0, false, s);
     if (r) return r;
     ghost_fill_kernel<<<device_sms() * 8, kFillThreads, 0, s>>>(
-        b->patches, b->npatch, b->U[0], b->U[1], b->U[2], b->U[3], b->U[4],
+        b->patches, b->npatch, b->U[0], b->U[1], b->U[2], b->U[3], b->U[4], b->ge,
         reinterpret_cast<const int *>(ws(b) + kWsPrefix));
     note_launch();
     return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
@@ -321,7 +326,7 @@ static int boundary_impl(const enzo_patch_batch *b, const int32_t *bc)
     int r = launch_prefix(b, kKindFill, 0, 0, false, s);
     if (r) return r;
     boundary_fill_kernel<<<device_sms() * 8, kFillThreads, 0, s>>>(
-        b->patches, b->npatch, b->U[0], b->U[1], b->U[2], b->U[3], b->U[4],
+        b->patches, b->npatch, b->U[0], b->U[1], b->U[2], b->U[3], b->U[4], b->ge,
         reinterpret_cast<const int *>(ws(b) + kWsPrefix), bc[0], bc[1], bc[2]);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
@@ -473,6 +478,7 @@ static int step_impl(const enzo_patch_batch *b, const enzo_params *p, int32_t st
     if (bc && !bc_ok(bc)) return ENZO_ERR_ARG;
     if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
     if (b->npatch == 0) return ENZO_OK;
+    if ((m.options & ENZO_OPT_DUAL) && (!b->ge || b->freg)) return ENZO_ERR_ARG;
     r = bc ? boundary_impl(b, bc) : fill_impl(b);
     if (r) return r;
     const int order[2][3] = {{0, 1, 2}, {2, 1, 0}};

@@ -25,6 +25,7 @@ constexpr size_t kWsPrefix = 256;      // int32 prefix[npatch + 1] of tiles per 
 // rare events are added to the caller's status words when they happen.
 struct Counters {
     unsigned iters = 0, restarts = 0, guesses = 0;
+    unsigned gep = 0;   // dual energy: zone loads that took the gas-energy pressure
     unsigned long long *st = nullptr;
 #ifdef __CUDACC__
     __device__ __forceinline__ void rare(int word) const
@@ -66,6 +67,7 @@ struct SweepArgs {
     long long log_cap = 0;
     int log_stride = 0;
     double *freg = nullptr;    // flux registers (enzo_patch.freg_all / freg_bnd)
+    double *ge = nullptr;      // gas energy of the dual-energy option, else nullptr
 };
 
 // Tiles of a sweep along dir for one patch: ceil(pencils / kSweepThreads).

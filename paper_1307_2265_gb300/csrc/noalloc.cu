@@ -93,7 +93,8 @@ extern "C" int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, do
     if (p->solver != ENZO_SOLVER_TWOSHOCK && p->solver != ENZO_SOLVER_HLL && p->solver != ENZO_SOLVER_HLLC)
         return ENZO_ERR_ARG;
     m.solver = p->solver;
-    if (p->options & ~(ENZO_OPT_STEEPEN | ENZO_OPT_FLATTEN | ENZO_OPT_DIFFUSE)) return ENZO_ERR_ARG;
+    if (p->options & ~(ENZO_OPT_STEEPEN | ENZO_OPT_FLATTEN | ENZO_OPT_DIFFUSE | ENZO_OPT_DUAL)) return ENZO_ERR_ARG;
+    if ((p->options & ENZO_OPT_DUAL) && (p->solver != ENZO_SOLVER_TWOSHOCK || !b->ge)) return ENZO_ERR_ARG;
     m.options = p->options;
 
     void *scratch = nullptr;
@@ -120,6 +121,7 @@ extern "C" int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, do
     a.prefix = reinterpret_cast<const int *>(ws + kWsPrefix);
     a.tile_counter = reinterpret_cast<unsigned *>(ws + kWsCounter);
     a.status = b->status;
+    a.ge = (m.options & ENZO_OPT_DUAL) ? b->ge : nullptr;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ENZO_ERR_CUDA;
     const cudaError_t e = f64 ? launch_sweep_fp64(a, sweep_grid_fp64(dev), s)

@@ -179,6 +179,73 @@ __device__ __forceinline__ Zone<float> prim<float, false>(double rho, double mn,
     return prim_f<false>(rho, mn, m1, m2, E, k, cnt);
 }
 
+// Primitive state with the dual-energy option (Sec. 4.1.1): the pressure comes
+// from the gas energy ge where E - KE < 1e-3 E, else from E - KE; eps = ge / rho
+// is the specific gas energy, carried like a transverse velocity.  The choice is
+// taken in FP64 in both precisions.  FP64: the same arithmetic as prim<double>.
+template <bool COUNT>
+__device__ __forceinline__ Zone<double> prim_dual(double rho, double mn, double m1, double m2, double E,
+                                                  double ge, const Consts<double> &k, Counters &cnt,
+                                                  double &eps)
+{
+    Zone<double> z;
+    if (!(rho >= k.rho_floor)) { rho = k.rho_floor; if (COUNT) cnt.rare(ENZO_ST_RHO_FLOOR); }
+    const double ke = 0.5 * ((mn * mn + m1 * m1) + m2 * m2) / rho;
+    double p;
+    if (E - ke < 1e-3 * E) {
+        p = k.gm1 * ge;
+        if (COUNT) cnt.gep++;
+    } else {
+        p = k.gm1 * (E - ke);
+    }
+    if (!(p >= k.p_floor)) { p = k.p_floor; if (COUNT) cnt.rare(ENZO_ST_P_FLOOR); }
+    z.r = rho;
+    z.u = mn / rho;
+    z.p = p;
+    z.t1 = m1 / rho;
+    z.t2 = m2 / rho;
+    z.c = sqrt(k.gamma * p / rho);
+    eps = ge / rho;
+    return z;
+}
+
+// FP32: as prim_f; a zone whose FP32 internal energy is below 5% of E (the only
+// zones where E - KE can fall under 1e-3 E) recovers E - KE in FP64 and takes
+// the gas-energy pressure where that is below 1e-3 E.
+template <bool COUNT>
+__device__ __forceinline__ Zone<float> prim_dual(double rho64, double mn64, double m164, double m264,
+                                                 double E64, double ge64, const Consts<float> &k,
+                                                 Counters &cnt, float &eps)
+{
+    Zone<float> z;
+    float rho = d2f_rz(rho64);
+    if (!(rho >= k.rho_floor)) { rho = k.rho_floor; rho64 = f2d_exact(rho); if (COUNT) cnt.rare(ENZO_ST_RHO_FLOOR); }
+    const float inv = 1.0f / rho;
+    const float mn = d2f_rz(mn64), m1 = d2f_rz(m164), m2 = d2f_rz(m264), E = d2f_rz(E64);
+    const float ke = 0.5f * ((mn * mn + m1 * m1) + m2 * m2) * inv;
+    float e = E - ke;
+    if (e < k.eta_eke * E) {
+        const double ke64 = 0.5 * ((mn64 * mn64 + m164 * m164) + m264 * m264) / rho64;
+        if (E64 - ke64 < 1e-3 * E64) {
+            e = d2f_rz(ge64);
+            if (COUNT) cnt.gep++;
+        } else {
+            e = (float)(E64 - ke64);
+        }
+        if (COUNT) cnt.rare(ENZO_ST_FP64_EKE);
+    }
+    float p = k.gm1 * e;
+    if (!(p >= k.p_floor)) { p = k.p_floor; if (COUNT) cnt.rare(ENZO_ST_P_FLOOR); }
+    z.r = rho;
+    z.u = mn * inv;
+    z.p = p;
+    z.t1 = m1 * inv;
+    z.t2 = m2 * inv;
+    z.c = sqrtf(k.gamma * p * inv);
+    eps = d2f_rz(ge64) * inv;
+    return z;
+}
+
 template <class R>
 __device__ __forceinline__ R zv(const Zone<R> &z, int v)
 {
@@ -285,6 +352,18 @@ __device__ __forceinline__ void trace(const R qL[5], const R qR[5], const R d[5]
     out[3] = r1 ? ENZO_I(s1, 3) : edge[3];
     out[4] = r1 ? ENZO_I(s1, 4) : edge[4];
 #undef ENZO_I
+}
+
+// A passive variable (eps of the dual-energy option) traced to one edge of its
+// zone as trace() takes the transverse velocities: the average over the domain
+// of the u wave where that wave reaches the edge, else the edge value.
+template <class R, int SIDE>
+__device__ __forceinline__ R trace_passive(R qL, R qR, R d, R q6, R u, R dtdx)
+{
+    const bool r1 = SIDE > 0 ? u > (R)0 : u < (R)0;
+    const R s1 = SIDE > 0 ? u * dtdx : -u * dtdx;
+    if (!r1) return SIDE > 0 ? qR : qL;
+    return SIDE > 0 ? avg_right<R>(qR, d, q6, s1) : avg_left<R>(qL, d, q6, s1);
 }
 
 // Lagrangian shock speed W and |dp/du| of the shock curve Z = 2W^3/(W^2+C^2).
@@ -780,7 +859,9 @@ struct LearnedGuess {
     }
 };
 
-template <class R, bool WRAP, int DIR, bool REG = false, bool EXT = false>
+// EXT: 0 the default kernels; 1 with the reconstruction options (steepening,
+// flattening, diffusive flux); 2 with those and dual energy.
+template <class R, bool WRAP, int DIR, bool REG = false, int EXT = 0>
 struct Marcher {
     static constexpr int A1 = DIR == 0 ? 1 : 0;
     static constexpr int A2 = DIR == 2 ? 1 : 2;
@@ -793,6 +874,32 @@ struct Marcher {
     double *reg_bnd;      // this pencil's boundary-face register pair, or nullptr
     double dt64;
     Zone<R> c0, c1, c2;   // WRAP: initial state of the first three active cells
+    R ce0, ce1, ce2;      // WRAP with dual energy: their initial eps
+
+    // Dual energy: gas-energy flux and interface velocity of one face.
+    struct GeFace {
+        R F, uf;
+    };
+    // Dual energy: the last updated cell, whose resynchronisation waits for the
+    // new E of its right neighbour (Sec. 4.1.1 compares E - KE with the largest
+    // E of the cell and its two neighbours along the sweep).
+    struct GePending {
+        int64_t idx;        // < 0: none yet
+        double ge, e, E;    // advected gas energy, E - KE and E after the update
+        double Eleft;       // E of its left neighbour (the ghost's for the first cell)
+        bool ok;            // rho > 0 after the update
+    };
+    GePending gpend;
+
+    // Write the pending cell's gas energy once the E of its right neighbour is known.
+    __device__ __forceinline__ void ge_commit(double Eright)
+    {
+        double emax = gpend.Eleft;
+        if (gpend.E > emax) emax = gpend.E;
+        if (Eright > emax) emax = Eright;
+        const double g = gpend.ok && gpend.e > 0.1 * emax ? gpend.e : gpend.ge;
+        if (active) a.ge[gpend.idx] = g;
+    }
 
     __device__ __forceinline__ const double *F(int f) const { return a.U[f]; }
 
@@ -820,13 +927,40 @@ struct Marcher {
                               __ldg(a.U[1 + A2] + idx), __ldg(a.U[4] + idx), k, cnt);
     }
 
+    // Zone at pencil position s with the dual-energy pressure choice, and its
+    // eps = ge / rho (EXT kernels with a gas-energy field only).
+    template <bool COUNT>
+    __device__ __forceinline__ Zone<R> zone_dual(int s, Counters &cnt, R &eps)
+    {
+        int64_t idx;
+        if (WRAP) {
+            const int j = s - pc.ng;
+            if (j >= pc.n) {
+                const int t = (j - pc.n) % pc.n;
+                eps = t == 0 ? ce0 : (t == 1 ? ce1 : ce2);
+                return t == 0 ? c0 : (t == 1 ? c1 : c2);
+            }
+            const int jj = j < 0 ? (pc.n - ((-j) % pc.n)) % pc.n : j;
+            idx = pc.at(pc.ng + jj);
+        } else {
+            idx = pc.at(s);
+        }
+        return prim_dual<COUNT>(__ldg(a.U[0] + idx), __ldg(a.U[1 + DIR] + idx), __ldg(a.U[1 + A1] + idx),
+                                __ldg(a.U[1 + A2] + idx), __ldg(a.U[4] + idx), __ldg(a.ge + idx), k, cnt, eps);
+    }
+
     // Density of cell s at the start of the sweep (raw, no floor).
     __device__ __forceinline__ double rho_old(int s) const { return a.U[0][pc.at(s)]; }
 
-    // Write the final state of active cell s given its two face terms.
+    // Write the final state of active cell s given its two face terms.  With
+    // dual energy (gm, gp non-null) also the gas energy: its flux difference
+    // and the source -p (u_{s+1/2} - u_{s-1/2}) dt/dx with the zone pressure pz;
+    // the cell then becomes the pending one, and the previous pending cell,
+    // whose right neighbour this is, is resynchronised and written.
     __device__ __forceinline__ void update(int s, const R Fm[5], const R Fp[5], double dtdx64,
                                            const double Gm[5], const double Gp[5], bool fb,
-                                           Counters &cnt)
+                                           Counters &cnt, const GeFace *gm = nullptr,
+                                           const GeFace *gp = nullptr, R pz = (R)0, R dtdx = (R)0)
     {
         const int64_t idx = pc.at(s);
         double u[5];
@@ -836,6 +970,35 @@ struct Marcher {
             const double U = a.U[map[v]][idx];
             if (sizeof(R) == 8) u[v] = cell_update(U, dtdx64, (double)Fm[v], (double)Fp[v]);
             else u[v] = (U + Gm[v]) - Gp[v];
+        }
+        double gnew = 0.0;
+        const bool dual = EXT == 2 && gm != nullptr;
+        if (dual) {
+            const double g0 = a.ge[idx];
+            if (sizeof(R) == 8) {
+                gnew = (g0 + dtdx64 * ((double)gm->F - (double)gp->F)) -
+                       dtdx64 * (double)pz * ((double)gp->uf - (double)gm->uf);
+            } else {
+                const double g_m = f2d_exact((float)(dtdx * gm->F));
+                const double g_p = f2d_exact((float)(dtdx * gp->F));
+                const double src = f2d_exact((float)(dtdx * pz * (gp->uf - gm->uf)));
+                gnew = ((g0 + g_m) - g_p) - src;
+            }
+            double enew = 0.0;
+            const bool ok = u[0] > 0.0;
+            if (ok) {
+                const double ke = 0.5 * ((u[1] * u[1] + u[2] * u[2]) + u[3] * u[3]) / u[0];
+                enew = u[4] - ke;
+            }
+            if (gpend.idx >= 0) {
+                ge_commit(u[4]);
+                gpend.Eleft = gpend.E;
+            }
+            gpend.idx = idx;
+            gpend.ge = gnew;
+            gpend.e = enew;
+            gpend.E = u[4];
+            gpend.ok = ok;
         }
         if (!active) return;
         if (fb && !(u[0] > 0.0)) cnt.rare(ENZO_ST_NEG_AFTER);
@@ -887,10 +1050,12 @@ struct Marcher {
     // steepening where the density has an inflection across a jump of at least
     // 1% that is a contact, not a shock; flattening where the flow compresses
     // across a pressure jump above 33%, weighted by the ratio of the 2-zone and
-    // 4-zone pressure differences.
+    // 4-zone pressure differences.  With dual energy (elx, erx non-null) the
+    // edges of eps (zone value qx) are flattened with the same weight.
     __device__ __forceinline__ void dissipate(const MethodParams &mp, const Zone<R> &zj1m, const Zone<R> &zj,
                                               const Zone<R> &zj1p, const Zone<R> &zj2p, R rj2m, R pj2m, R dm1,
-                                              R dp1, R el[5], R er[5]) const
+                                              R dp1, R el[5], R er[5], R qx = (R)0, R *elx = nullptr,
+                                              R *erx = nullptr) const
     {
         if (mp.options & ENZO_OPT_STEEPEN) {
             const R Dm = (zj.r - (R)2 * zj1m.r) + rj2m;
@@ -924,6 +1089,10 @@ struct Marcher {
                         el[v] = f * q + ((R)1 - f) * el[v];
                         er[v] = f * q + ((R)1 - f) * er[v];
                     }
+                    if (elx) {
+                        *elx = f * qx + ((R)1 - f) * *elx;
+                        *erx = f * qx + ((R)1 - f) * *erx;
+                    }
                 }
             }
         }
@@ -931,8 +1100,10 @@ struct Marcher {
 
     // Diffusive flux at the interface between zones a (left) and b (right):
     // 0.1 max(0, u_a - u_b) times the jump of the conserved state rebuilt from
-    // the zone primitives (CW84; optional in Sec. 4.1).
-    __device__ __forceinline__ void diffuse(const Zone<R> &za, const Zone<R> &zb, R F[5]) const
+    // the zone primitives (CW84; optional in Sec. 4.1).  With dual energy
+    // (Fx non-null) the gas-energy flux too, rho eps being its conserved value.
+    __device__ __forceinline__ void diffuse(const Zone<R> &za, const Zone<R> &zb, R F[5], R ea = (R)0,
+                                            R eb = (R)0, R *Fx = nullptr) const
     {
         const R du = za.u - zb.u;
         if (!(du > (R)0)) return;
@@ -950,6 +1121,7 @@ struct Marcher {
             Uz[4] = q.p / k.gm1 + (R)0.5 * q.r * ((q.u * q.u + q.t1 * q.t1) + q.t2 * q.t2);
         }
         _Pragma("unroll") for (int v = 0; v < 5; ++v) F[v] = F[v] + nu * (Ua[v] - Ub[v]);
+        if (Fx) *Fx = *Fx + nu * (za.r * ea - zb.r * eb);
     }
 
     // One pencil with the plain guess: a sliding window over the zones; march
@@ -975,20 +1147,40 @@ struct Marcher {
         // pressure of zone k-4, and the density slope of zone k-3
         Zone<R> zm3{};
         R r4 = (R)0, p4 = (R)0, ds3 = (R)0;
+        // EXT with dual energy: eps of zones k-3..k; for eps the slope of zone
+        // k-2, the interface value at (k-3)+1/2 and the left state traced there;
+        // the gas-energy face terms, Godunov at (k-4)+1/2 and final at (k-5)+1/2
+        const bool dual = EXT == 2 && a.ge != nullptr;
+        R e3 = (R)0, e2 = (R)0, e1 = (R)0, e0 = (R)0;
+        R dep = (R)0, qfep = (R)0, sLep = (R)0;
+        GeFace gg{(R)0, (R)0}, gfin2{(R)0, (R)0};
+        // E at the start of the sweep of the ghosts beside the first and last
+        // active cells (their periodic images when the pencil wraps: the last
+        // active cell is not yet updated here, the first one will be by the end)
+        double Eghost_right = 0.0;
+        if (dual) {
+            gpend.idx = -1;
+            gpend.Eleft = a.U[4][WRAP ? pc.at(pc.ng + pc.n - 1) : pc.at(pc.ng - 1)];
+            Eghost_right = a.U[4][WRAP ? pc.at(pc.ng) : pc.at(pc.ng + pc.n)];
+        }
         for (int kk = 0; kk < L; ++kk) {
             if constexpr (EXT) {
                 r4 = zm3.r;
                 p4 = zm3.p;
                 zm3 = zm2;
+                e3 = e2;
+                e2 = e1;
+                e1 = e0;
             }
             zm2 = zm1;
             zm1 = z0;
-            z0 = zone<true>(kk, cnt);
+            if (dual) z0 = zone_dual<true>(kk, cnt, e0);
+            else z0 = zone<true>(kk, cnt);
             if (WRAP) {
                 const int j = kk - pc.ng;
-                if (j == 0) c0 = z0;
-                else if (j == 1) c1 = z0;
-                else if (j == 2) c2 = z0;
+                if (j == 0) { c0 = z0; ce0 = e0; }
+                else if (j == 1) { c1 = z0; ce1 = e0; }
+                else if (j == 2) { c2 = z0; ce2 = e0; }
             }
             if (sizeof(R) == 4) {
                 rho3 = rho2;
@@ -999,11 +1191,14 @@ struct Marcher {
             if (kk < 2) continue;
             R dcur[5];
             _Pragma("unroll") for (int v = 0; v < 5; ++v) dcur[v] = limited_slope<R>(zv(zm2, v), zv(zm1, v), zv(z0, v));
+            const R dce = dual ? limited_slope<R>(e2, e1, e0) : (R)0;
             if (kk >= 3) {
                 R qfcur[5];
                 _Pragma("unroll") for (int v = 0; v < 5; ++v)
                     qfcur[v] = (R)0.5 * (zv(zm2, v) + zv(zm1, v)) - div6(dcur[v] - dprev[v]);
+                const R qfce = dual ? (R)0.5 * (e2 + e1) - div6(dce - dep) : (R)0;
                 if (kk >= 4) {
+                    R sRe = (R)0, sLen = (R)0;   // eps traced to the left / right edge of zone kk-2
                     // parabola of zone kk-2 (its edges: qfprev on the left, qfcur on the right)
                     R pL[5], pR[5], pd[5], p6[5];
                     if constexpr (EXT) {
@@ -1013,8 +1208,16 @@ struct Marcher {
                             el[v] = qfprev[v];
                             er[v] = qfcur[v];
                         }
-                        dissipate(mp, zm3, zm2, zm1, z0, r4, p4, ds3, dcur[0], el, er);
+                        R ele = qfep, ere = qfce;
+                        dissipate(mp, zm3, zm2, zm1, z0, r4, p4, ds3, dcur[0], el, er, e2, dual ? &ele : nullptr,
+                                  dual ? &ere : nullptr);
                         _Pragma("unroll") for (int v = 0; v < 5; ++v) parabola<R>(zv(zm2, v), el[v], er[v], pL[v], pR[v], pd[v], p6[v]);
+                        if (dual) {
+                            R eL, eR, ed, e6;
+                            parabola<R>(e2, ele, ere, eL, eR, ed, e6);
+                            sRe = trace_passive<R, -1>(eL, eR, ed, e6, zm2.u, dtdx);
+                            sLen = trace_passive<R, +1>(eL, eR, ed, e6, zm2.u, dtdx);
+                        }
                     } else {
                         _Pragma("unroll") for (int v = 0; v < 5; ++v) parabola<R>(zv(zm2, v), qfprev[v], qfcur[v], pL[v], pR[v], pd[v], p6[v]);
                     }
@@ -1025,6 +1228,7 @@ struct Marcher {
                         // Riemann problem at interface (kk-3)+1/2
                         if (a.log) log_states(kk, sLprev, sR);
                         R Fg[5];
+                        GeFace gcur{(R)0, (R)0};
                         if (mp.solver == ENZO_SOLVER_TWOSHOCK) {
                             const R p0 = guess(sLprev[0], sLprev[1], sLprev[2], sR[0], sR[1], sR[2]);
                             const RiemannOut<R> o = riemann<R>(sLprev[0], sLprev[1], sLprev[2], sR[0], sR[1],
@@ -1037,13 +1241,17 @@ struct Marcher {
                             const R t1 = o.ustar >= (R)0 ? sLprev[3] : sR[3];
                             const R t2 = o.ustar >= (R)0 ? sLprev[4] : sR[4];
                             phys_flux<R>(o.rho, o.u, o.p, t1, t2, k, Fg);
+                            if (dual) {
+                                gcur.F = Fg[0] * (o.ustar >= (R)0 ? sLep : sRe);
+                                gcur.uf = o.u;
+                            }
                         } else if (mp.solver == ENZO_SOLVER_HLLC) {
                             hllc_states<R>(sLprev, sR, k, Fg);
                         } else {
                             hll_states<R>(sLprev, sR, k, Fg);
                         }
                         if constexpr (EXT) {
-                            if (mp.options & ENZO_OPT_DIFFUSE) diffuse(zm3, zm2, Fg);
+                            if (mp.options & ENZO_OPT_DIFFUSE) diffuse(zm3, zm2, Fg, e3, e2, dual ? &gcur.F : nullptr);
                         }
                         if (kk >= 6) {
                             // cell c = kk-3: does the Godunov update leave rho > 0?
@@ -1065,18 +1273,18 @@ struct Marcher {
                             }
                             // final flux at face (kk-4)+1/2
                             R Fu1[5];
-                            if (badprev || bad) {
-                                Counters quiet;
-                                const Zone<R> za = zone<false>(kk - 4, quiet);
-                                const Zone<R> zb = zone<false>(kk - 3, quiet);
-                                hll_flux<R>(za, zb, k, Fu1);
-                            } else {
+                            GeFace gfin = gg;
+                            if (badprev || bad) fallback_face(kk - 4, dual, Fu1, gfin);
+                            else {
                                 _Pragma("unroll") for (int v = 0; v < 5; ++v) Fu1[v] = Fgprev[v];
                             }
                             double G1[5];
                             widen(Fu1, dtdx, G1);
                             record(kk - 6, Fu1, G1);
-                            if (kk >= 7) update(kk - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt);
+                            if (kk >= 7)
+                                update(kk - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt, dual ? &gfin2 : nullptr,
+                                       &gfin, p4, dtdx);
+                            gfin2 = gfin;
                             _Pragma("unroll") for (int v = 0; v < 5; ++v)
                             {
                                 Fuprev2[v] = Fu1[v];
@@ -1085,28 +1293,51 @@ struct Marcher {
                             badprev = bad;
                         }
                         _Pragma("unroll") for (int v = 0; v < 5; ++v) Fgprev[v] = Fg[v];
+                        gg = gcur;
                     }
                     _Pragma("unroll") for (int v = 0; v < 5; ++v) sLprev[v] = sLnew[v];
+                    sLep = sLen;
                 }
                 _Pragma("unroll") for (int v = 0; v < 5; ++v) qfprev[v] = qfcur[v];
+                qfep = qfce;
             }
             if constexpr (EXT) ds3 = dprev[0];
             _Pragma("unroll") for (int v = 0; v < 5; ++v) dprev[v] = dcur[v];
+            dep = dce;
         }
         // last active cell L-4: its right face (L-4)+1/2 borders a ghost zone
         R Fu1[5];
-        if (badprev) {
-            Counters quiet;
-            const Zone<R> za = zone<false>(L - 4, quiet);
-            const Zone<R> zb = zone<false>(L - 3, quiet);
-            hll_flux<R>(za, zb, k, Fu1);
-        } else {
+        GeFace gfin = gg;
+        if (badprev) fallback_face(L - 4, dual, Fu1, gfin);
+        else {
             _Pragma("unroll") for (int v = 0; v < 5; ++v) Fu1[v] = Fgprev[v];
         }
         double G1[5];
         widen(Fu1, dtdx, G1);
         record(pc.n, Fu1, G1);
-        update(L - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt);
+        // the pressure of zone L-4 is the last window's zone k-3
+        update(L - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt, dual ? &gfin2 : nullptr, &gfin, zm3.p, dtdx);
+        if (dual) ge_commit(Eghost_right);
+    }
+
+    // HLL re-flux (Sec. 4.1.2) of the face between zones s and s+1 from their
+    // zone states; with dual energy also its gas-energy flux (the HLL mass flux
+    // times the upwind zone eps) and interface velocity (the mean zone velocity).
+    __device__ __forceinline__ void fallback_face(int s, bool dual, R Fu[5], GeFace &g)
+    {
+        Counters quiet;
+        if (dual) {
+            R ea, eb;
+            const Zone<R> za = zone_dual<false>(s, quiet, ea);
+            const Zone<R> zb = zone_dual<false>(s + 1, quiet, eb);
+            hll_flux<R>(za, zb, k, Fu);
+            g.F = Fu[0] * (Fu[0] >= (R)0 ? ea : eb);
+            g.uf = (R)0.5 * (za.u + zb.u);
+        } else {
+            const Zone<R> za = zone<false>(s, quiet);
+            const Zone<R> zb = zone<false>(s + 1, quiet);
+            hll_flux<R>(za, zb, k, Fu);
+        }
     }
 
     // One pencil with the pipelined learned guess.  March step kk loads zone kk
@@ -1294,7 +1525,7 @@ __device__ __forceinline__ void warp_flush(unsigned long long *status, unsigned 
 // pencil march a stand-in copy of the tile's first pencil and write nothing).
 // REG: the batch has flux registers (hierarchy levels); the per-pencil register
 // rows are then tracked, otherwise the recording compiles away.
-template <class R, int DIR, bool LEARNED, int THREADS = kSweepThreads, bool REG = false, bool EXT = false>
+template <class R, int DIR, bool LEARNED, int THREADS = kSweepThreads, bool REG = false, int EXT = 0>
 __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_SWEEP_MIN_BLOCKS_FP32 * 128 / THREADS : 2))
     ppm_sweep_kernel(const __grid_constant__ SweepArgs a)
 {
@@ -1377,6 +1608,7 @@ __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_
     warp_flush(a.status, cnt.iters, ENZO_ST_NEWTON_ITERS);
     warp_flush(a.status, cnt.restarts, ENZO_ST_GUESS_RESTARTS);
     warp_flush(a.status, cnt.guesses, ENZO_ST_GUESS_CALLS);
+    if constexpr (EXT == 2) warp_flush(a.status, cnt.gep, ENZO_ST_GE_PRESSURE);
 }
 
 // CFL rate of Sec. 9 per active cell, max-reduced into *rate_bits.  A tile is
@@ -1522,20 +1754,30 @@ cudaError_t launch_tiled(const SweepArgs &a, cudaStream_t s)
 template <class R>
 cudaError_t launch_sweep_dir(const SweepArgs &a, int grid, cudaStream_t s)
 {
+    if (a.mp.options & ENZO_OPT_DUAL) {
+        // dual energy (never with flux registers) has its own instantiations
+        // too, so the option kernels without it keep their registers
+        switch (a.dir) {
+        case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, false, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
+        case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, false, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
+        default: ppm_sweep_kernel<R, 2, false, kSweepThreads, false, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
+        }
+        return cudaGetLastError();
+    }
     if (a.mp.options) {
         // the reconstruction options have their own instantiations, so the
         // default kernels stay as they are
         if (a.freg) {
             switch (a.dir) {
-            case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, true, true><<<grid, kSweepThreads, 0, s>>>(a); break;
-            case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, true, true><<<grid, kSweepThreads, 0, s>>>(a); break;
-            default: ppm_sweep_kernel<R, 2, false, kSweepThreads, true, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+            case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, true, 1><<<grid, kSweepThreads, 0, s>>>(a); break;
+            case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, true, 1><<<grid, kSweepThreads, 0, s>>>(a); break;
+            default: ppm_sweep_kernel<R, 2, false, kSweepThreads, true, 1><<<grid, kSweepThreads, 0, s>>>(a); break;
             }
         } else {
             switch (a.dir) {
-            case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, false, true><<<grid, kSweepThreads, 0, s>>>(a); break;
-            case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, false, true><<<grid, kSweepThreads, 0, s>>>(a); break;
-            default: ppm_sweep_kernel<R, 2, false, kSweepThreads, false, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+            case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, false, 1><<<grid, kSweepThreads, 0, s>>>(a); break;
+            case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, false, 1><<<grid, kSweepThreads, 0, s>>>(a); break;
+            default: ppm_sweep_kernel<R, 2, false, kSweepThreads, false, 1><<<grid, kSweepThreads, 0, s>>>(a); break;
             }
         }
         return cudaGetLastError();

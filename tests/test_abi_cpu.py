@@ -82,7 +82,7 @@ def test_validate_patches_ranges():
 
 def test_patch_struct_layout_matches_header():
     assert ez.PATCH_DTYPE.itemsize == 72
-    assert ctypes.sizeof(ez._Batch) == 4 + 4 + 8 + 8 + 40 + 8 + 8 + 8 + 8 + 8
+    assert ctypes.sizeof(ez._Batch) == 4 + 4 + 8 + 8 + 40 + 8 + 8 + 8 + 8 + 8 + 8
 
 
 def test_boundary_conditions_rejected_without_gpu():
@@ -115,6 +115,34 @@ def test_reconstruction_options_rejected_without_gpu():
     b.npatch = 0
     ok = ez.Params(options=ez.OPT_STEEPEN | ez.OPT_FLATTEN | ez.OPT_DIFFUSE).c()
     assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(ok)) == 0
-    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(ez.Params(options=8).c())) == -1
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(ez.Params(options=16).c())) == -1
     p = ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=4096, options=ez.OPT_STEEPEN).c()
     assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -1
+
+
+def test_dual_energy_arguments_rejected_without_gpu():
+    """OPT_DUAL needs the two-shock solver, a gas-energy field and no flux
+    registers; each is refused on the host before any launch (the fake device
+    pointers below are never dereferenced)."""
+    L = ez.lib()
+    b = ez._Batch()
+    b.npatch = 0
+    dual = ez.Params(options=ez.OPT_DUAL)
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(dual.c())) == 0
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0,
+                            ctypes.byref(ez.Params(options=ez.OPT_DUAL, solver=ez.SOLVER_HLLC).c())) == -1
+    b.npatch = 1
+    b.patches = 4096
+    b.field_len = 1000
+    for i in range(5):
+        b.U[i] = 8192 + 8192 * i
+    b.workspace = 65536
+    b.ws_bytes = int(L.enzo_workspace_size(1))
+    b.status = 131072
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(dual.c())) == -1      # ge missing
+    assert L.enzo_step(ctypes.byref(b), ctypes.byref(dual.c()), 0, ctypes.c_void_p(262144)) == -1
+    b.ge = 524288
+    b.freg = 1048576
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(dual.c())) == -1      # with registers
+    assert L.enzo_ppm_sweep_noalloc(ctypes.byref(b), 0, 0.1, 0,
+                                    ctypes.byref(ez.Params(options=ez.OPT_DUAL, solver=ez.SOLVER_HLL).c())) == -1

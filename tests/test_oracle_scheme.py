@@ -555,8 +555,10 @@ def _ge_of(U, g):
 def test_dual_energy_leaves_ordinary_flow_unchanged():
     """Mach-1 white noise: E - KE is well above eta1 E everywhere, so the
     pressure never comes from the gas energy and the conserved state evolves
-    bit-identically with the option on; where E - KE exceeds eta2 E the gas
-    energy is reset to it after each sweep."""
+    bit-identically with the option on; after the last sweep (x, the sixth
+    step being odd) the gas energy equals E - KE wherever that exceeds eta2
+    times the largest E of the cell and its x neighbours (interior cells,
+    whose neighbours were updated in the same sweep)."""
     g = 5.0 / 3.0
     U = _grid((12, 10, 8), seed=21)
     V = [f.copy() for f in U]
@@ -571,9 +573,11 @@ def test_dual_energy_leaves_ordinary_flow_unchanged():
     for a, b in zip(U, V):
         assert np.array_equal(_active(a), _active(b))
     e = _ge_of([_active(f) for f in V], g)
-    sync = e > 0.1 * _active(V[4])
+    E = _active(V[4])
+    emax = np.maximum(np.maximum(E[..., :-2], E[..., 1:-1]), E[..., 2:])
+    sync = e[..., 1:-1] > 0.1 * emax
     assert sync.mean() > 0.9
-    assert np.array_equal(_active(ge)[sync], e[sync])
+    assert np.array_equal(_active(ge)[..., 1:-1][sync], e[..., 1:-1][sync])
 
 
 def test_dual_energy_keeps_the_entropy_of_a_cold_compression():
@@ -612,6 +616,44 @@ def test_dual_energy_keeps_the_entropy_of_a_cold_compression():
     s_std = (g - 1.0) * _ge_of([_active(f)[0, 0] for f in V], g) / rv ** g
     assert np.max(np.abs(s_std / 1e-6 - 1.0)) > 2e-2
     assert np.max(np.abs(r - 1.0)) > 0.01                   # the gas was compressed
+
+
+def test_dual_energy_resynchronises_against_the_neighbourhood_energy():
+    """Sec. 4.1.1 resets the gas energy to E - KE only where that exceeds eta2
+    times the largest E of the cell and its two neighbours along the sweep.  A
+    uniform left-moving flow (u = -4.12, p = 1) over a density step 1 | 2
+    carries E = 10 | 18.5 with E - KE = 1.5 (a 5% pressure wave on top, so the
+    advected gas energy departs from E - KE by truncation error): cells of the
+    light gas next to the dense gas have E - KE above 0.1 of their own E but
+    below 0.1 of the neighbour's, so they keep the advected gas energy, while
+    cells clear of the step are reset to E - KE exactly.  A rule on the cell's
+    own E alone, planted in the oracle, resets those cells too and fails."""
+    g = 5.0 / 3.0
+    N = 32
+    x = (np.arange(N) + 0.5) / N
+    rho = np.where(x < 0.5, 1.0, 2.0).reshape(1, 1, N)
+    u = np.full((1, 1, N), -math.sqrt(17.0))
+    p = (1.0 + 0.05 * np.sin(2 * math.pi * x)).reshape(1, 1, N)
+    z = np.zeros_like(rho)
+    U = [synth.embed(f) for f in synth.prims_to_conserved(rho, u, z, z, p, g)]
+    ge = synth.embed(p / (g - 1.0))
+    P = oracle.Params(gamma=g, options=oracle.OPT_DUAL)
+    dx = [1.0 / N, 1e30, 1e30]
+    dt = 0.4 / oracle.cfl_rate(U, dx, P)
+    oracle.step_periodic_dual(U, ge, dx, dt, 1, P)          # odd step: z, y, then x last
+    A = [_active(f)[0, 0] for f in U]
+    e = _ge_of(A, g)
+    E = A[4]
+    emax = np.maximum(np.maximum(np.roll(E, 1), E), np.roll(E, -1))
+    gn = _active(ge)[0, 0]
+    inner = np.zeros(N, bool)
+    inner[1:-1] = True                                       # both neighbours updated in the sweep
+    synced = inner & (e > 0.1 * emax)
+    held = inner & (e > 0.1 * E) & ~(e > 0.1 * emax)
+    assert synced.sum() >= N // 3 and held.sum() >= 1, (synced.sum(), held.sum())
+    assert np.array_equal(gn[synced], e[synced])
+    assert np.all(gn[held] != e[held])
+    assert np.all(np.abs(gn[held] / e[held] - 1.0) < 0.2)   # the advected value is still close
 
 
 def test_dual_energy_removes_pressure_floors_in_cold_hypersonic_gas():
