@@ -349,11 +349,14 @@ typedef struct {        /* a box of ghost cells of patch dst copied from sibling
     int32_t lo[3], hi[3];   /* global cell box at the level, hi exclusive */
 } enzo_copy_box;
 
-typedef struct {        /* a face of a fine patch on the boundary of the refined region */
+typedef struct {        /* (part of) a face of a fine patch on the boundary of the refined region */
     int32_t fine;       /* fine patch index */
     int32_t dir;        /* axis of the face normal */
     int32_t side;       /* 0: low face, 1: high face */
-    int32_t target;     /* coarse patch holding the coarse cells outside that face */
+    int32_t target;     /* coarse patch holding the coarse cells outside that part */
+    int32_t lo[2], hi[2]; /* the part: coarse cells [lo, hi) along the face's two other
+                             axes (a1 < a2), counted from the face's first coarse cell;
+                             the whole face is [0, n_a / 2) */
 } enzo_fc_face;
 
 /* SetBoundaryValues of a refined level (Sec. 3.1): ghost cells are
@@ -372,17 +375,85 @@ int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *f
                           int32_t ninterp, const enzo_copy_box *copy_boxes, int32_t ncopy, int32_t precision,
                           int32_t r);
 
-/* Flux correction (Sec. 3.4): for each listed face of a fine patch, the coarse
- * cells just outside it get U += (dt_coarse F_coarse - mean of the fine
+/* Flux correction (Sec. 3.4): for each listed face part of a fine patch, the
+ * coarse cells just outside it get U += (dt_coarse F_coarse - mean of the fine
  * register over the r^2 fine faces) / dx_coarse on the low side (minus on the
  * high side).  F_coarse is read from the parent's all-face register, the fine
  * sums from the fine patch's boundary register.  increments != 0: the registers
  * were written by FP32-path sweeps and hold the increments the cells applied
- * (dt/dx F), and the correction is G_coarse - mean(fine sums) / r. */
+ * (dt/dx F), and the correction is G_coarse - mean(fine sums) / r.  Parts listed
+ * in one call must not share a coarse cell (the additions are unordered); a
+ * caller with parts that do (concave corners of the refined region) splits
+ * them over calls in the order the additions should happen. */
 int enzo_flux_correct(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_links,
                       const enzo_patch_batch *fine, const enzo_patch_link *fine_links,
                       const enzo_fc_face *faces, int32_t nface, double dt_coarse, int32_t r,
                       int32_t increments);
+
+/* Copy between two batches of one level (a rebuild, Sec. 3.5): the cells of
+ * each box (global cells at the level, hi exclusive) go from src patch
+ * boxes[i].src of `src` to dst patch boxes[i].dst of `dst`, all five fields.
+ * Boxes must lie in the source patch's active cells and in the destination
+ * patch's stored block; boxes with the same destination must not overlap.
+ * Runs on dst->stream.  ENZO_ERR_ARG on NULL arguments or nbox < 0. */
+int enzo_copy_level(const enzo_patch_batch *dst, const enzo_patch_link *dst_links,
+                    const enzo_patch_batch *src, const enzo_patch_link *src_links,
+                    const enzo_copy_box *boxes, int32_t nbox);
+
+/* ---- hierarchy rebuild (Sec. 3.5, 3.6) ---- */
+
+/* Refinement criteria of Sec. 3.6, each off when its threshold is <= 0. */
+typedef struct {
+    double gamma;       /* ratio of specific heats (pressure of the shock criterion) */
+    double slope;       /* slope: |q_{i+1} - q_{i-1}| / (2 |q_i|) > slope for q = rho or E
+                           along any axis (typically 0.3) */
+    double shock_dp;    /* shocks: |p_{i+1} - p_{i-1}| / min(p_{i+1}, p_{i-1}) > shock_dp
+                           (0.33) with u_{i-1} - u_{i+1} > 0 along that axis ... */
+    double shock_e;     /* ... and e_i / E_i > shock_e (0.1), e = E - KE */
+    double mass;        /* baryon mass: rho dx^3 > mass */
+} enzo_flag_params;
+
+enum { ENZO_FLAG_SLOPE = 1, ENZO_FLAG_SHOCK = 2, ENZO_FLAG_MASS = 4 };
+
+/* Flag the active cells of every patch of a batch (Sec. 3.6): flags[flag_off[i]
+ * + (k n_y + j) n_x + i] receives the ENZO_FLAG_* bits of active cell (i, j, k)
+ * of patch i (DEVICE arrays: uint8 flags, int64 flag_off[npatch]).  Neighbours
+ * come from the ghost zones, which the caller fills first, or wrap for
+ * ENZO_PATCH_PERIODIC patches.  FP64, each operation rounded once in the order
+ * written, so the flags are exact functions of the fields.  Uses the batch's
+ * workspace and stream.  ENZO_ERR_ARG on NULL arguments. */
+int enzo_flag_cells(const enzo_patch_batch *b, const enzo_flag_params *fp, uint8_t *flags,
+                    const int64_t *flag_off);
+
+/* Clustering of Sec. 3.5 (Berger & Rigoutsos).  The cell-growth and
+ * split rules: */
+typedef struct {
+    double efficiency;  /* adopt a region whose flagged fraction is >= this (0.3) ... */
+    int32_t small_cells;/* ... or that holds at most this many cells (>= 1) */
+    int32_t buffer;     /* flags are first grown by this many cells (Chebyshev distance,
+                           inside the grid), >= 0 ... */
+    int32_t margin;     /* ... and then cleared within this many cells of the grid's edge,
+                           >= 0 (keeps new grids off the domain boundary or properly
+                           nested in their parent) */
+} enzo_cluster_params;
+
+typedef struct {
+    int32_t lo[3], hi[3];   /* half-open box of active-cell indices (x, y, z) */
+} enzo_box;
+
+/* Cover the flagged cells of one grid (HOST flags [n_z][n_y][n_x], nonzero =
+ * flagged) by disjoint boxes.  The smallest box around the (grown) flags of a
+ * region is adopted when efficient or small enough; otherwise it is cut in two
+ * at the strongest inflection of the flag signature (a sign change of its
+ * second difference, strength |change|; ties to the cut nearest the centre,
+ * then the lower cut) along the longest axis, else the next longest (ties x, y,
+ * z), else the longest axis is halved, and each part is processed the same
+ * way, the low part first.  Host code, no GPU.  Writes at most cap boxes to the
+ * HOST array boxes and the number found to *nbox; ENZO_ERR_RANGE if more than
+ * cap are needed (*nbox then holds the number needed), ENZO_ERR_ARG on bad
+ * arguments. */
+int enzo_cluster_flags(const uint8_t *flags, const int32_t n[3], const enzo_cluster_params *cp,
+                       enzo_box *boxes, int32_t cap, int32_t *nbox);
 
 /* Projection (Sec. 3.3): every coarse cell covered by a fine patch becomes the
  * mean of its r^3 fine cells (r = 2). */

@@ -166,11 +166,16 @@ def copy_from_siblings(level):
 
 
 def fill_level(levels, l, parent_old, w):
-    """SetBoundaryValues of level l: periodic root, else parent interpolation
-    then sibling copies."""
+    """SetBoundaryValues of level l: the root's external boundaries (periodic
+    unless the level carries "bc", Sec. 3.1), else parent interpolation then
+    sibling copies."""
     if l == 0:
+        bc = levels[0].get("bc")
         for p in levels[0]["patches"]:
-            oracle.fill_periodic(p["U"])
+            if bc is None:
+                oracle.fill_periodic(p["U"])
+            else:
+                oracle.fill_boundary(p["U"], bc)
         return
     parents = levels[l - 1]["patches"]
     for p in levels[l]["patches"]:
@@ -284,13 +289,19 @@ def _weight(levels, l):
     return (levels[l]["t"] - par["t_old"]) / (par["t"] - par["t_old"])
 
 
-def evolve_level(levels, l, t_parent, P, cfl=0.4, log=None):
+def evolve_level(levels, l, t_parent, P, cfl=0.4, log=None, rebuild=None):
     """Advance level l until it reaches t_parent (W-cycle recursion).  Ghosts
     are set before every step (so sibling copies and coverage keep the fluxes
     of shared faces identical) and again after it, before the finer level
-    interpolates from this level's new state."""
+    interpolates from this level's new state.  With `rebuild` (a dict of
+    oracle.amr.rebuild_level's gamma, crit, clus), every step of a level with
+    children ends, after flux correction and projection, by rebuilding the
+    finer levels from flags (Sec. 3, RebuildHierarchy in EvolveLevel)."""
     L = levels[l]
     has_children = l + 1 < len(levels)
+    if not L["patches"]:
+        L["t"] = t_parent                # a level without grids has nothing to advance
+        return
     while L["t"] < t_parent * (1 - 1e-14):
         fill_level(levels, l, levels[l - 1].get("old") if l > 0 else None, _weight(levels, l))
         if l == 0:
@@ -309,17 +320,24 @@ def evolve_level(levels, l, t_parent, P, cfl=0.4, log=None):
             fill_level(levels, l, levels[l - 1].get("old") if l > 0 else None, _weight(levels, l))
             for fp in levels[l + 1]["patches"]:
                 fp.pop("Ff", None)
-            evolve_level(levels, l + 1, L["t"], P, cfl, log)
+            evolve_level(levels, l + 1, L["t"], P, cfl, log, rebuild)
             flux_correct(levels, l, dt)
             project(levels, l)
+            if rebuild is not None:
+                from . import amr
+                fill_level(levels, l, levels[l - 1].get("old") if l > 0 else None, _weight(levels, l))
+                for m in range(l, len(levels) - 1):
+                    amr.rebuild_level(levels, m, **rebuild)
+    # the loop stops within 1e-14 of the parent's time; the level has reached it
+    L["t"] = t_parent
 
 
-def root_step(levels, P, cfl=0.4, log=None):
+def root_step(levels, P, cfl=0.4, log=None, rebuild=None):
     """One root step: dt_0 from the root CFL rule, then the W-cycle."""
     rate = level_rate(levels, 0, P)
     dt0 = cfl / rate
     t_end = levels[0]["t"] + dt0
-    evolve_level(levels, 0, t_end, P, cfl, log)
+    evolve_level(levels, 0, t_end, P, cfl, log, rebuild)
     return dt0
 
 
@@ -343,9 +361,10 @@ def composite_totals(levels, r=R):
     return tot
 
 
-def make_levels(layout, fields, root_dx):
+def make_levels(layout, fields, root_dx, root_bc=None):
     """Level dicts of the reference driver from a synth.hierarchy_layout and its
-    fields (copied)."""
+    fields (copied); root_bc: external boundaries (bc_x, bc_y, bc_z) of the
+    root grid, or None for periodic."""
     levels = []
     for l, L in enumerate(layout):
         patches = []
@@ -355,4 +374,6 @@ def make_levels(layout, fields, root_dx):
                             "parent": int(L["parent"][i]),
                             "U": [f.copy() for f in fields[l][i]]})
         levels.append({"patches": patches, "dx": root_dx / R ** l, "t": 0.0, "step": 0})
+    if root_bc is not None:
+        levels[0]["bc"] = tuple(root_bc)
     return levels

@@ -8,6 +8,8 @@ Translation units and their flags:
   hierarchy.cu  ghost fill from parents/siblings, flux correction, projection (FP64,
                 --fmad=false)
   mlp.cu        learned p* guess: tcgen05 inference and training kernels
+  amr.cu        hierarchy rebuild: cell flagging (FP64, --fmad=false) and the
+                host clustering of flags into new grids
 Objects go to paper_1307_2265_gb300/_build/, the library next to this file.
 """
 from __future__ import annotations
@@ -32,6 +34,7 @@ UNITS = {
     "noalloc.cu": [],
     "mlp.cu": ["-use_fast_math"],
     "hierarchy.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
+    "amr.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
 }
 OPTIONAL_UNITS = {}
 

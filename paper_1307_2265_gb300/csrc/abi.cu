@@ -12,7 +12,6 @@ namespace enzo {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch(unsigned n) { g_launches += n; }
 
-enum { kKindSweep = 0, kKindFill = 1, kKindCells = 2 };
 
 __device__ __forceinline__ int tiles_of(const enzo_patch &P, int64_t field_len, int kind, int dir,
                                         int cover, int tile_pencils, bool &bad)

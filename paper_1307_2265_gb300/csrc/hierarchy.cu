@@ -178,15 +178,23 @@ __global__ void __launch_bounds__(128) interp_ghosts_kernel(const __grid_constan
 // Each thread loads the five fields of two cells before storing any, so that
 // enough loads are in flight to cover HBM latency (sources are active cells,
 // which this kernel never writes).
-__global__ void __launch_bounds__(128) copy_boxes_kernel(const enzo_patch *pt, const enzo_patch_link *lk,
-                                                         double *U0, double *U1, double *U2, double *U3,
-                                                         double *U4, const enzo_copy_box *boxes, int nbox)
+// The source patches may belong to another batch of the same level (a
+// rebuild copying the old grids into the new ones).
+struct CopyArgs {
+    const enzo_patch *dpt, *spt;
+    const enzo_patch_link *dlk, *slk;
+    double *D[5];
+    const double *S[5];
+    const enzo_copy_box *boxes;
+    int nbox;
+};
+
+__global__ void __launch_bounds__(128) copy_boxes_kernel(const __grid_constant__ CopyArgs a)
 {
-    double *const U[5] = {U0, U1, U2, U3, U4};
-    for (int bi = blockIdx.x; bi < nbox; bi += gridDim.x) {
-        const enzo_copy_box B = boxes[bi];
-        const enzo_patch D = pt[B.dst], S = pt[B.src];
-        const enzo_patch_link DL = lk[B.dst], SL = lk[B.src];
+    for (int bi = blockIdx.x; bi < a.nbox; bi += gridDim.x) {
+        const enzo_copy_box B = a.boxes[bi];
+        const enzo_patch D = a.dpt[B.dst], S = a.spt[B.src];
+        const enzo_patch_link DL = a.dlk[B.dst], SL = a.slk[B.src];
         const int e0 = B.hi[0] - B.lo[0], e1 = B.hi[1] - B.lo[1], e2 = B.hi[2] - B.lo[2];
         const int vol = e0 * e1 * e2, e01 = e0 * e1;
         const int D0 = D.n[0] + 2 * D.ng, D01 = D0 * (D.n[1] + 2 * D.ng);
@@ -208,13 +216,13 @@ __global__ void __launch_bounds__(128) copy_boxes_kernel(const enzo_patch *pt, c
                 si[k] = sbase + x + (int64_t)S0 * y + (int64_t)S01 * z;
                 if (c < vol)
 #pragma unroll
-                    for (int f = 0; f < 5; ++f) v[k][f] = U[f][si[k]];
+                    for (int f = 0; f < 5; ++f) v[k][f] = a.S[f][si[k]];
             }
 #pragma unroll
             for (int k = 0; k < 2; ++k)
                 if (di[k] >= 0)
 #pragma unroll
-                    for (int f = 0; f < 5; ++f) U[f][di[k]] = v[k][f];
+                    for (int f = 0; f < 5; ++f) a.D[f][di[k]] = v[k][f];
         }
     }
 }
@@ -252,7 +260,7 @@ __device__ __forceinline__ int64_t reg_bnd_block(const enzo_patch &P, int dir)
     return o;
 }
 
-// One CTA per listed fine face; threads over the coarse faces it covers.
+// One CTA per listed fine face part; threads over the coarse faces it covers.
 __global__ void __launch_bounds__(128) flux_correct_kernel(const __grid_constant__ FcArgs a)
 {
     for (int fi = blockIdx.x; fi < a.nface; fi += gridDim.x) {
@@ -267,7 +275,7 @@ __global__ void __launch_bounds__(128) flux_correct_kernel(const __grid_constant
         const int X = (FL.origin[d] + (F.side ? FP.n[d] : 0)) / 2;
         const int cell = F.side ? X : X - 1;
         const int fc = X - PL.origin[d];
-        const int m1 = FP.n[a1] / 2, m2 = FP.n[a2] / 2;
+        const int e1 = F.hi[0] - F.lo[0], e2 = F.hi[1] - F.lo[1];
         const double *creg = a.cfreg + PP.freg_all + reg_all_block(PP, d);
         const double *freg = a.ffreg + FP.freg_bnd + reg_bnd_block(FP, d);
         const int fna1 = FP.n[a1];
@@ -275,8 +283,8 @@ __global__ void __launch_bounds__(128) flux_correct_kernel(const __grid_constant
         // fields in pencil order (rho, m_n, m_t1, m_t2, E)
         double *const Uf[5] = {a.U[0], d == 0 ? a.U[1] : (d == 1 ? a.U[2] : a.U[3]),
                                a1 == 0 ? a.U[1] : a.U[2], a2 == 1 ? a.U[2] : a.U[3], a.U[4]};
-        for (int q = threadIdx.x; q < m1 * m2; q += blockDim.x) {
-            const int q1 = q % m1, q2 = q / m1;
+        for (int q = threadIdx.x; q < e1 * e2; q += blockDim.x) {
+            const int q1 = F.lo[0] + q % e1, q2 = F.lo[1] + q / e1;
             const int c1 = FL.origin[a1] / 2 + q1, c2 = FL.origin[a2] / 2 + q2;
             const double *cf = creg + (((int64_t)(c2 - PL.origin[a2]) * PP.n[a1] + (c1 - PL.origin[a1])) *
                                            (PP.n[d] + 1) + fc) * 5;
@@ -420,13 +428,43 @@ int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *f
         if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
     }
     if (ncopy > 0) {
-        copy_boxes_kernel<<<ncopy, 128, 0, s>>>(
-            fine->patches, fine_links, fine->U[0], fine->U[1], fine->U[2], fine->U[3], fine->U[4], copy_boxes,
-            ncopy);
+        CopyArgs c;
+        c.dpt = c.spt = fine->patches;
+        c.dlk = c.slk = fine_links;
+        for (int f = 0; f < 5; ++f) {
+            c.D[f] = fine->U[f];
+            c.S[f] = fine->U[f];
+        }
+        c.boxes = copy_boxes;
+        c.nbox = ncopy;
+        copy_boxes_kernel<<<ncopy, 128, 0, s>>>(c);
         note_launch();
         if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
     }
     return ENZO_OK;
+}
+
+int enzo_copy_level(const enzo_patch_batch *dst, const enzo_patch_link *dst_links, const enzo_patch_batch *src,
+                    const enzo_patch_link *src_links, const enzo_copy_box *boxes, int32_t nbox)
+{
+    if (!batch_ok(dst) || !batch_ok(src) || !dst_links || !src_links || nbox < 0 || (nbox > 0 && !boxes))
+        return ENZO_ERR_ARG;
+    if (nbox == 0) return ENZO_OK;
+    CopyArgs c;
+    c.dpt = dst->patches;
+    c.spt = src->patches;
+    c.dlk = dst_links;
+    c.slk = src_links;
+    for (int f = 0; f < 5; ++f) {
+        c.D[f] = dst->U[f];
+        c.S[f] = src->U[f];
+    }
+    c.boxes = boxes;
+    c.nbox = nbox;
+    copy_boxes_kernel<<<nbox < sm_count() * 16 ? nbox : sm_count() * 16, 128, 0,
+                        static_cast<cudaStream_t>(dst->stream)>>>(c);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
 }
 
 int enzo_flux_correct(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_links,

@@ -127,7 +127,11 @@ cudaError_t launch_riemann_fp32(const RiemannArgs &a, cudaStream_t s);
 
 void note_launch(unsigned n = 1);
 
-// Launch of the per-patch tile prefix kernel (kind 0: sweep pencils) on stream s.
+// Work-list kinds of the tile prefix: sweep pencils, ghost-fill cells (whole
+// stored block), active cells (kCflCells per tile).
+enum { kKindSweep = 0, kKindFill = 1, kKindCells = 2 };
+
+// Launch of the per-patch tile prefix kernel (kind: kKind*) on stream s.
 void launch_tile_prefix(const enzo_patch *patches, int npatch, int64_t field_len, int kind, int dir,
                         int cover, int *prefix, unsigned *counter, unsigned long long *rate_bits,
                         unsigned long long *status, cudaStream_t s, int tile_pencils = kSweepThreads);

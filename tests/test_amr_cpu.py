@@ -1,0 +1,98 @@
+"""Host logic of the hierarchy rebuild, no GPU: the library's Berger-Rigoutsos
+clustering (host C++) returns the oracle's boxes, in the oracle's order, on
+seeded flag patterns; the plans for general layouts agree with the
+tensor-tiling plans where both apply; flux-correction parts at a concave
+corner of the refined region come in separate waves in the oracle's order."""
+import numpy as np
+import pytest
+
+from oracle import amr
+from paper_1307_2265_gb300 import hierarchy as gh
+from paper_1307_2265_gb300 import synth
+
+
+def _pattern(seed):
+    rng = np.random.default_rng(seed)
+    shape = (int(rng.integers(1, 14)), int(rng.integers(1, 22)), int(rng.integers(1, 30)))
+    F = np.zeros(shape, np.uint8)
+    for _ in range(int(rng.integers(0, 6))):
+        c = [int(rng.integers(0, s)) for s in shape]
+        r = [int(rng.integers(1, 5)) for _ in shape]
+        F[max(0, c[0] - r[0]):c[0] + r[0], max(0, c[1] - r[1]):c[1] + r[1], max(0, c[2] - r[2]):c[2] + r[2]] = 1
+    F |= (rng.random(shape) < float(rng.choice([0.0, 0.005, 0.03]))).astype(np.uint8)
+    return F
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_native_clustering_equals_the_oracle(seed):
+    F = _pattern(seed)
+    for eff, small, buf, mar in ((0.3, 64, 1, 0), (0.7, 8, 0, 1), (0.9, 1, 2, 0), (0.3, 8, 1, 3)):
+        want = amr.cluster(F, efficiency=eff, small_cells=small, buffer=buf, margin=mar)
+        got = gh.cluster_flags(F, efficiency=eff, small_cells=small, buffer=buf, margin=mar)
+        assert got == [(tuple(lo), tuple(hi)) for lo, hi in want]
+
+
+def test_native_clustering_grows_its_output_array():
+    F = np.zeros((1, 1, 200), np.uint8)
+    F[0, 0, ::4] = 1                                   # 50 isolated flags
+    got = gh.cluster_flags(F, efficiency=1.0, small_cells=1, buffer=0)
+    assert got == [(tuple(lo), tuple(hi)) for lo, hi in amr.cluster(F, efficiency=1.0, small_cells=1, buffer=0)]
+    assert len(got) == 50
+
+
+def test_general_plans_match_the_tensor_plans_on_static_layouts():
+    layout = synth.hierarchy_layout(16, [(4, 12), (6, 10)], [4, 8], seed=2)
+    for l in (1, 2):
+        n, o = layout[l]["n"], layout[l]["origin"]
+        a = gh.sibling_boxes(n, o)
+        b = gh.sibling_boxes_general(n, o)
+        assert sorted(map(bytes, a)) == sorted(map(bytes, b))
+        a = gh.interp_boxes(n, o)
+        b = gh.interp_boxes_general(n, o)
+        assert sorted(map(bytes, a)) == sorted(map(bytes, b))
+        fine = {"n": n, "origin": o}
+        coarse = {"n": layout[l - 1]["n"], "origin": layout[l - 1]["origin"]}
+        fc = gh.correction_faces(fine, coarse)
+        parts, wave = gh.correction_parts(fine, coarse)
+        assert np.array_equal(fc, parts) and not wave.any()
+
+
+def test_correction_parts_order_concave_corners_in_waves():
+    """An L of two fine patches over one coarse patch: the coarse cell in the
+    inner corner lies outside a face of each, so the two parts touching it go
+    to successive waves, the lower fine patch index first; a fine face whose
+    outside spans two coarse patches is split into two parts."""
+    coarse = {"n": np.array([[8, 8, 8], [8, 8, 8]]), "origin": np.array([[0, 0, 0], [8, 0, 0]])}
+    # fine patches (in fine cells): A over coarse [2,4)x[2,6)x[2,4), B over [4,6)x[2,4)x[2,4)
+    fine = {"n": np.array([[4, 8, 4], [4, 4, 4]]), "origin": np.array([[4, 4, 4], [8, 4, 4]])}
+    parts, wave = gh.correction_parts(fine, coarse)
+    corner = np.array([4, 4, 2])                    # outside A's +x face and B's +y face (coarse cell)
+    touching = []
+    for k, p in enumerate(parts):
+        i, d, side = p["fine"], p["dir"], p["side"]
+        fo, fn = fine["origin"][i] // 2, fine["n"][i] // 2
+        a1 = 1 if d == 0 else 0
+        a2 = 1 if d == 2 else 2
+        lo, hi = fo.copy(), fo + fn
+        lo[d] = fo[d] - 1 if side == 0 else fo[d] + fn[d]
+        hi[d] = lo[d] + 1
+        lo[a1], hi[a1] = fo[a1] + p["lo"][0], fo[a1] + p["hi"][0]
+        lo[a2], hi[a2] = fo[a2] + p["lo"][1], fo[a2] + p["hi"][1]
+        if np.all((lo <= corner) & (corner < hi)):
+            touching.append(k)
+    assert len(touching) == 2
+    k0, k1 = touching
+    assert parts[k0]["fine"] == 0 and parts[k1]["fine"] == 1
+    assert wave[k1] > wave[k0]
+    # B's +x face (coarse x = 6) lies in coarse patch 0 (x < 8); make a face cross two
+    fine2 = {"n": np.array([[4, 4, 4]]), "origin": np.array([[10, 4, 4]])}     # coarse [5,7): +x face at 7
+    coarse2 = {"n": np.array([[7, 8, 8], [9, 8, 8]]), "origin": np.array([[0, 0, 0], [7, 0, 0]])}
+    p2, _ = gh.correction_parts(fine2, coarse2)
+    xs = p2[(p2["dir"] == 0) & (p2["side"] == 1)]
+    assert len(xs) == 1 and xs[0]["target"] == 1
+    fine3 = {"n": np.array([[4, 8, 4]]), "origin": np.array([[4, 4, 4]])}       # coarse y in [2, 6)
+    coarse3 = {"n": np.array([[8, 4, 8], [8, 4, 8]]), "origin": np.array([[0, 0, 0], [0, 4, 0]])}
+    p3, _ = gh.correction_parts(fine3, coarse3)
+    xs = p3[(p3["dir"] == 0) & (p3["side"] == 0)]
+    assert sorted(xs["target"]) == [0, 1]                     # split at coarse y = 4
+    assert sorted((int(a[0]), int(b[0])) for a, b in zip(xs["lo"], xs["hi"])) == [(0, 2), (2, 4)]

@@ -1,0 +1,162 @@
+"""The hierarchy rebuild on the GPU (Sec. 3.5, 3.6) against the oracle:
+- the flag kernel gives the oracle's flags bit for bit, with ghost zones and
+  with periodic wrap;
+- a rebuild gives the oracle's boxes and, in FP64, its new grids bit for bit;
+- root steps of a dynamic W-cycle (rebuild after every step of a level with
+  children, two and three levels) give the oracle's grids and fields bit for
+  bit step after step, and keep the composite totals in FP64 and in FP32."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1307_2265_gb300 as ez
+from gpu_helpers import batch_from_patches
+from oracle import amr
+from oracle import hierarchy as H
+from paper_1307_2265_gb300 import hierarchy as gh
+from paper_1307_2265_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+NG = 3
+CRIT = {"slope": 0.3, "shock_dp": 0.33, "shock_e": 0.1}
+CLUS = {"efficiency": 0.3, "small_cells": 8, "buffer": 1}
+
+
+def _rough_patch(n, seed, g):
+    """Log-normal density and pressure (sigma 0.5) and Mach ~1.5 velocities:
+    slopes, pressure jumps in converging flow and heavy cells all occur."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = n
+    sh = (nz, ny, nx)
+    rho = np.exp(rng.normal(0, 0.5, sh))
+    p = np.exp(rng.normal(0, 0.5, sh))
+    v = [rng.normal(0, 1.5 * math.sqrt(g), sh) for _ in range(3)]
+    return [synth.embed(f) for f in synth.prims_to_conserved(rho, v[0], v[1], v[2], p, g)]
+
+
+@pytest.mark.parametrize("flags", [0, ez.PATCH_PERIODIC])
+def test_flags_bit_exact(flags):
+    g = 5.0 / 3.0
+    patches = [_rough_patch(n, 800 + i, g) for i, n in enumerate([(24, 16, 12), (9, 30, 5), (1, 7, 13)])]
+    dx = [1.0 / 24] * 3
+    b = batch_from_patches(patches, dx, flags=flags)
+    if flags == 0:
+        ez.ghost_fill_periodic(b)
+    mass = float(np.median(H._active(patches[0][0]))) * dx[0] ** 3
+    got = gh.flag_cells(b, g, slope=0.3, shock_dp=0.33, shock_e=0.1, mass=mass)
+    seen = 0
+    for U, fl in zip(patches, got):
+        V = [f.copy() for f in U]
+        oracle.fill_periodic(V)
+        want = amr.flag_patch(V, dx[0], g, slope=0.3, shock_dp=0.33, shock_e=0.1, mass=mass)
+        assert np.array_equal(fl, want)
+        for bit in (amr.SLOPE, amr.SHOCK, amr.MASS):
+            seen |= bit if np.any(want & bit) else 0
+    assert seen == amr.SLOPE | amr.SHOCK | amr.MASS          # every criterion fired somewhere
+
+
+def _shock_layout(N=48, M=2.0, x0=0.3, levels=2, ny=8):
+    """Root N x ny x ny with a Mach-M shock (gamma 1.4) running right from x0 and
+    (levels - 1) nested refined patches around it, fields sampled from the
+    same profile at each level's resolution."""
+    g = 1.4
+    rho1, p1 = 1.0, 1.0
+    c1 = math.sqrt(g * p1 / rho1)
+    rho2 = rho1 * (g + 1) * M * M / ((g - 1) * M * M + 2)
+    p2 = p1 * (2 * g * M * M - (g - 1)) / (g + 1)
+    u2 = M * c1 * (1 - rho1 / rho2)
+
+    def state(n, origin, dx):
+        nx, nyy, nz = n
+        x = (origin[0] + np.arange(nx) + 0.5) * dx
+        post = np.broadcast_to(x < x0, (nz, nyy, nx))
+        z = np.zeros((nz, nyy, nx))
+        prims = (np.where(post, rho2, rho1), np.where(post, u2, 0.0), z, z, np.where(post, p2, p1))
+        return [synth.embed(f) for f in synth.prims_to_conserved(*prims, g)]
+
+    layout = [{"n": np.array([(N, ny, ny)]), "origin": np.zeros((1, 3), int), "parent": np.array([-1])}]
+    fields = [[state((N, ny, ny), (0, 0, 0), 1.0 / N)]]
+    lo, hi = [int(x0 * N) - 4, 3, 3], [int(x0 * N) + 6, ny - 3, ny - 3]
+    for l in range(1, levels):
+        n = tuple(2 * (hi[a] - lo[a]) for a in range(3))
+        o = tuple(2 * lo[a] for a in range(3))
+        layout.append({"n": np.array([n]), "origin": np.array([o]), "parent": np.array([0])})
+        fields.append([state(n, o, 1.0 / (N * 2 ** l))])
+        lo = [o[0] + 2, o[1] + 1, o[2] + 1]
+        hi = [o[0] + n[0] - 2, o[1] + n[1] - 1, o[2] + n[2] - 1]
+    return layout, fields, 1.0 / N, g
+
+
+def _assert_same(ref, hier):
+    hier.stream.synchronize()
+    for l, L in enumerate(ref):
+        lev = hier.levels[l]
+        assert len(lev["n"]) == len(L["patches"]), l
+        for i, p in enumerate(L["patches"]):
+            assert tuple(lev["n"][i]) == tuple(p["n"]) and tuple(lev["origin"][i]) == tuple(p["origin"])
+            assert int(lev["parent"][i]) == p["parent"]
+            for a, b in zip(hier.patch_fields(l, i), p["U"]):
+                assert np.array_equal(H._active(a), H._active(b)), (l, i)
+
+
+def test_rebuild_matches_the_oracle_bitwise():
+    layout, fields, dx, g = _shock_layout()
+    ref = H.make_levels(layout, fields, dx)
+    hier = gh.Hierarchy(layout, fields, dx)
+    oracle.fill_periodic(ref[0]["patches"][0]["U"])
+    want = amr.rebuild_level(ref, 0, g, CRIT, CLUS)
+    got = hier.rebuild(0, g, CRIT, CLUS)
+    assert got == want and len(got) >= 1
+    _assert_same(ref, hier)
+    for i, p in enumerate(ref[1]["patches"]):          # ghost zones too
+        for a, b in zip(hier.patch_fields(1, i), p["U"]):
+            assert np.array_equal(a, b)
+
+
+def _gpu_totals(hier):
+    lv = []
+    for l, lev in enumerate(hier.levels):
+        lv.append({"patches": [{"n": tuple(int(v) for v in lev["n"][i]),
+                                "origin": tuple(int(v) for v in lev["origin"][i]),
+                                "parent": int(lev["parent"][i]), "U": hier.patch_fields(l, i)}
+                               for i in range(len(lev["n"]))], "dx": lev["dx"]})
+    t = H.composite_totals(lv)
+    for L in lv:
+        for p in L["patches"]:
+            p["U"] = [np.abs(f) for f in p["U"]]
+    return t, H.composite_totals(lv)
+
+
+@pytest.mark.parametrize("nlev", [2, 3])
+def test_dynamic_root_steps_match_the_oracle_bitwise(nlev):
+    layout, fields, dx, g = _shock_layout(levels=nlev)
+    ref = H.make_levels(layout, fields, dx)
+    hier = gh.Hierarchy(layout, fields, dx)
+    P = oracle.Params(gamma=g)
+    params = ez.Params(precision=ez.FP64, gamma=g)
+    rb = {"gamma": g, "crit": CRIT, "clus": CLUS}
+    t0, scale = _gpu_totals(hier)
+    layouts = set()
+    for _ in range(5):
+        log_o, log_g = [], []
+        H.root_step(ref, P, log=log_o, rebuild=rb)
+        hier.root_step(params, log=log_g, rebuild=rb)
+        assert log_g == log_o
+        _assert_same(ref, hier)
+        layouts.add(tuple(map(tuple, hier.levels[1]["origin"])))
+    assert len(layouts) > 1                               # the grids moved with the shock
+    t1, _ = _gpu_totals(hier)
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale.max()), (t1 - t0) / scale.max()
+
+
+def test_dynamic_fp32_conserves_the_composite_totals():
+    layout, fields, dx, g = _shock_layout()
+    hier = gh.Hierarchy(layout, fields, dx)
+    t0, scale = _gpu_totals(hier)
+    rb = {"gamma": g, "crit": CRIT, "clus": CLUS}
+    for _ in range(5):
+        hier.root_step(ez.Params(precision=ez.FP32, gamma=g), rebuild=rb)
+    t1, _ = _gpu_totals(hier)
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale.max()), (t1 - t0) / scale.max()
