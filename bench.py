@@ -460,6 +460,217 @@ def run_hierarchy(args, rank, world):
     return res
 
 
+def run_variants(args, rank, world):
+    """The sweep's optional rows on the headline's level (periodic patches of 8..64
+    cells per axis): FP32 plain; with the reconstruction options (contact
+    steepening, flattening, diffusive flux); with HLLC and with HLL as the
+    interface solver; with dual energy (gas energy from E - KE of the initial
+    state); FP64 with the options and with dual energy.  Each runs the device
+    CFL timestep and three sweeps per step, W warm-up steps then K timed steps
+    (2 for FP64) bracketed by CUDA events on the launching stream, each sweep
+    also timed alone for the roofline: algorithmic bytes 80 per cell-sweep (5
+    FP64 fields read and written once), 96 with the gas energy."""
+    import torch
+    import paper_1307_2265_gb300 as ez
+    dev = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(dev)
+    sizes, offsets, flat = build_level(rank, args.npatch)
+    table = ez.patch_table(sizes, offsets, [1.0 / 64] * 3, flags=ez.PATCH_PERIODIC)
+    cells = int(np.prod(sizes, axis=1).sum())
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ke = 0.5 * ((flat[1] * flat[1] + flat[2] * flat[2]) + flat[3] * flat[3]) / flat[0]
+        ge = np.where(flat[0] > 0, flat[4] - ke, 0.0)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch = ez.PatchBatch(table, flat, stream=stream, ge=ge)
+    host0 = [torch.from_numpy(f).pin_memory() for f in flat] + [torch.from_numpy(ge).pin_memory()]
+    del ge, ke
+
+    def reset():
+        for u, h in zip(batch.U + [batch.ge], host0):
+            u.copy_(h, non_blocking=True)
+        torch.cuda.synchronize()
+        batch.reset_status()
+
+    def one_step(params, s, ev):
+        ez.timestep_cfl(batch, params, out=batch.dt_dev)
+        order = (0, 1, 2) if s % 2 == 0 else (2, 1, 0)
+        for q, d in enumerate(order):
+            ev[q][0].record(stream)
+            ez.ppm_sweep_dev(batch, d, batch.dt_dev, 0, params)
+            ev[q][1].record(stream)
+
+    opts = ez.OPT_STEEPEN | ez.OPT_FLATTEN | ez.OPT_DIFFUSE
+    variants = [("fp32_plain", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32), 80),
+                ("fp32_options", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, options=opts), 80),
+                ("fp32_hllc", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, solver=ez.SOLVER_HLLC), 80),
+                ("fp32_hll", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, solver=ez.SOLVER_HLL), 80),
+                ("fp32_dual", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, options=ez.OPT_DUAL), 96),
+                ("fp64_options", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP64, options=opts), 80),
+                ("fp64_dual", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP64, options=ez.OPT_DUAL), 96)]
+    peak, peak_kind = measured_peak()
+    out = {}
+    launches0 = ez.launch_count()
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
+    with clk:
+        for name, params, bpc in variants:
+            k = args.steps if params.precision == ez.FP32 else min(args.steps, 2)
+            reset()
+            ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)]
+                  for _ in range(max(args.warmup, k))]
+            with torch.cuda.stream(stream):
+                for w in range(args.warmup):
+                    one_step(params, w, ev[w])
+            reset()
+            barrier(world)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for s in range(k):
+                    one_step(params, s, ev[s])
+                e1.record(stream)
+            e1.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1), world)
+            sweep = float(np.mean([[ev[s][q][0].elapsed_time(ev[s][q][1]) for q in range(3)] for s in range(k)]))
+            st = batch.read_status()
+            achieved = cells * bpc / (sweep * 1e-3) / 1e9
+            out[name] = {"value": cells * world * k / (ms * 1e-3) / 1e6, "unit": "Mcell-updates/s",
+                         "ms_per_step": ms / k, "steps": k, "sweep_ms_avg": sweep,
+                         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                      "frac": achieved / peak, "bytes_per_cell_sweep": bpc},
+                         "newton_iters_per_interface": st["newton_iters"] / max(1, st["interfaces"]),
+                         "hll_cells": st["hll_cells"], "ge_pressure": st["ge_pressure"], "nan": st["nan"]}
+    launches = ez.launch_count() - launches0
+    head = out["fp32_options"]
+    return {"metric": METRIC, "value": head["value"], "unit": "Mcell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc",
+            "data": "synthetic",
+            "config": {"workload": f"sweep variants on the batched AMR level: {args.npatch} self-periodic patches, "
+                                   f"per-axis 8..64 cells, white-noise lognormal rho sigma 0.5, rms Mach 1, "
+                                   f"gamma 5/3, CFL 0.4, eager launches (CFL + 3 sweeps per step)",
+                       "cells_per_step": cells, "value_is": "fp32_options",
+                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+            "variants": out, "roofline": dict(head["roofline"], kernel="ppm_sweep_kernel<float, DIR, EXT=1>",
+                                              peak_source=peak_kind, traffic=None),
+            "gpu_launches": int(launches), "cpu_baseline": None, "clocks": clk.summary(dev)}
+
+
+def _blast_hierarchy(R, gamma):
+    """Root R^3 at rest (rho 1, p 1e-5) with energy 1 deposited as pressure in
+    a sphere of radius 3 root cells at the centre, and one refined patch over
+    the central (R/4)^3 root cells whose cells take their parents' values."""
+    from paper_1307_2265_gb300 import synth
+    x = (np.arange(R) + 0.5) / R - 0.5
+    z, y, xx = np.meshgrid(x, x, x, indexing="ij")
+    r = np.sqrt(xx * xx + y * y + z * z)
+    inside = r < 3.0 / R
+    vol = inside.sum() / R ** 3
+    p = np.where(inside, (gamma - 1.0) / vol, 1e-5)
+    zero = np.zeros_like(p)
+    root = [synth.embed(f) for f in synth.prims_to_conserved(np.ones_like(p), zero, zero, zero, p, gamma)]
+    lo, hi = 3 * R // 8, 5 * R // 8
+    n1 = 2 * (hi - lo)
+    act = [f[3:-3, 3:-3, 3:-3][lo:hi, lo:hi, lo:hi].repeat(2, 0).repeat(2, 1).repeat(2, 2) for f in root]
+    layout = [{"n": np.array([(R, R, R)]), "origin": np.zeros((1, 3), int), "parent": np.array([-1])},
+              {"n": np.array([(n1, n1, n1)]), "origin": np.array([(2 * lo,) * 3]), "parent": np.array([0])}]
+    return layout, [[root], [[synth.embed(a) for a in act]]]
+
+
+def run_rebuild(args, rank, world):
+    """Dynamic hierarchy: a Sedov blast in a periodic root of args.root^3 cells
+    with one refined level that is rebuilt after every root step from the slope
+    (0.3) and shock (0.33, 0.1) flags of the root (Berger-Rigoutsos, efficiency
+    0.3, buffer 1).  W warm-up root steps let the blast grow; K timed root steps
+    (the subcycled W-cycle, flux correction, projection and the rebuild) give the
+    throughput in cell updates of all levels.  The flag kernel is also timed
+    alone on the root for its roofline (41 algorithmic bytes per cell: five
+    FP64 fields read, one flag byte written), and the host clustering of the
+    root's flags on its own."""
+    import ctypes
+    import torch
+    import paper_1307_2265_gb300 as ez
+    from paper_1307_2265_gb300 import hierarchy as gh
+    dev = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(dev)
+    R = args.root
+    layout, fields = _blast_hierarchy(R, GAMMA)
+    rb = {"gamma": GAMMA, "crit": {"slope": 0.3, "shock_dp": 0.33, "shock_e": 0.1},
+          "clus": {"efficiency": 0.3, "small_cells": 64, "buffer": 1}}
+    out = {}
+    launches0 = ez.launch_count()
+    for name, prec in (("fp32_plain", ez.FP32), ("fp64_plain", ez.FP64)):
+        hier = gh.Hierarchy(layout, fields, 1.0 / R)
+        params = ez.Params(gamma=GAMMA, cfl=CFL, precision=prec)
+        for _ in range(args.warmup):
+            hier.root_step(params, rebuild=rb)
+        hier.stream.synchronize()
+        hier.timing = {}
+        c0 = hier.cell_updates
+        npatch = []
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(hier.stream)
+        t0 = time.perf_counter()
+        k = args.steps if prec == ez.FP32 else min(args.steps, 3)
+        for _ in range(k):
+            hier.root_step(params, rebuild=rb)
+            npatch.append(len(hier.levels[1]["n"]))
+        e1.record(hier.stream)
+        e1.synchronize()
+        wall = time.perf_counter() - t0
+        ms = e0.elapsed_time(e1)
+        ops = hier.timing_ms()
+        out[name] = {"value": (hier.cell_updates - c0) / (ms * 1e-3) / 1e6, "unit": "Mcell-updates/s",
+                     "ms_per_root_step": ms / k, "wall_ms_per_root_step": wall * 1e3 / k, "root_steps": k,
+                     "level1_patches": npatch,
+                     "level1_cells": int(np.prod(hier.levels[1]["n"], axis=1).sum()),
+                     "rebuild_share": ops.get("rebuild", 0.0) / ms, "ms_by_operation": ops}
+        if prec == ez.FP32:
+            # flag kernel alone on the root, and the host clustering of its flags
+            root = hier.levels[0]["batch"]
+            flags = torch.zeros(R ** 3, dtype=torch.uint8, device=root.device)
+            off = torch.zeros(1, dtype=torch.int64, device=root.device)
+            fp = gh._FlagParams(GAMMA, 0.3, 0.33, 0.1, 0.0)
+            L = gh._lib()
+            with torch.cuda.stream(hier.stream):
+                b = root.c()
+                for _ in range(3):
+                    L.enzo_flag_cells(ctypes.byref(b), ctypes.byref(fp), flags.data_ptr(), off.data_ptr())
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                nrep = 10
+                f0.record(hier.stream)
+                for _ in range(nrep):
+                    L.enzo_flag_cells(ctypes.byref(b), ctypes.byref(fp), flags.data_ptr(), off.data_ptr())
+                f1.record(hier.stream)
+            f1.synchronize()
+            fms = f0.elapsed_time(f1) / nrep
+            host = flags.cpu().numpy().reshape(R, R, R)
+            t1 = time.perf_counter()
+            boxes = gh.cluster_flags(host, margin=3, **rb["clus"])
+            cms = (time.perf_counter() - t1) * 1e3
+            peak, peak_kind = measured_peak()
+            achieved = R ** 3 * 41 / (fms * 1e-3) / 1e9
+            out["flag_kernel"] = {"ms": fms, "cells": R ** 3, "flagged_fraction": float((host != 0).mean()),
+                                  "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                               "frac": achieved / peak, "bytes_per_cell": 41,
+                                               "peak_source": peak_kind}}
+            out["clustering_host"] = {"ms": cms, "boxes": len(boxes)}
+        del hier
+        torch.cuda.empty_cache()
+    launches = ez.launch_count() - launches0
+    head = out["fp32_plain"]
+    return {"metric": METRIC, "value": head["value"], "unit": "Mcell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_root_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc",
+            "data": "synthetic",
+            "config": {"workload": f"dynamic hierarchy: Sedov blast (E = 1, rho 1, p 1e-5) in a {R}^3 periodic "
+                                   f"root, one refined level rebuilt after every root step from slope and shock "
+                                   f"flags, gamma 5/3, CFL 0.4", "value_is": "fp32_plain"},
+            "paths": out, "roofline": dict(out["flag_kernel"]["roofline"], kernel="flag_kernel", traffic=None),
+            "gpu_launches": int(launches), "cpu_baseline": None}
+
+
 def _train_net(args):
     """The learned Newton guess, trained on this GPU with the library's kernels
     on interface states logged from the white-noise and turbulent recipes."""
@@ -687,7 +898,8 @@ def main():
     ap.add_argument("--train-set", default="configs", choices=["small", "configs"],
                     help="small: ~3e6 states from reduced grids (fast); configs: ~1e8 states from the "
                          "full-size 32^3 and 256^3 single-grid recipes")
-    ap.add_argument("--workload", default="level", choices=["level", "hierarchy", "turbulence", "blast"])
+    ap.add_argument("--workload", default="level",
+                    choices=["level", "hierarchy", "turbulence", "blast", "variants", "rebuild"])
     ap.add_argument("--e2e-lanes", type=int, default=3, help="device copies of the level in the end-to-end "
                     "measurement (their copies and sweeps overlap)")
     ap.add_argument("--mlp-gate", type=float, default=0.0, help="jump-strength gate of the learned guess "
@@ -702,6 +914,10 @@ def main():
         return
     if args.workload == "hierarchy":
         res = run_hierarchy(args, rank, world)
+    elif args.workload == "variants":
+        res = run_variants(args, rank, world)
+    elif args.workload == "rebuild":
+        res = run_rebuild(args, rank, world)
     elif args.workload in ("turbulence", "blast"):
         res = run_single_grid(args, rank, world)
     else:

@@ -136,9 +136,9 @@ public:
         while (!stack.empty()) {
             Region r = stack.back();
             stack.pop_back();
-            if (!shrink(r)) continue;
+            long long cnt = 0;
+            if (!scan(r, cnt)) continue;           // r is now the bounding box of its flags
             const long long vol = (long long)(r.hi[0] - r.lo[0]) * (r.hi[1] - r.lo[1]) * (r.hi[2] - r.lo[2]);
-            const long long cnt = count(r);
             if ((double)cnt >= cp_.efficiency * (double)vol || vol <= cp_.small_cells) {
                 out.push_back(r);
                 continue;
@@ -155,7 +155,7 @@ public:
                     }
             int cut_ax = -1, cut = 0;
             for (int k = 0; k < 3 && cut_ax < 0; ++k) {
-                const int c = best_cut(r, axes[k]);
+                const int c = best_cut(axes[k]);
                 if (c > 0) {
                     cut_ax = axes[k];
                     cut = c;
@@ -178,8 +178,6 @@ public:
     }
 
 private:
-    bool at(int x, int y, int z) const { return F_[((size_t)z * ny_ + y) * nx_ + x]; }
-
     // Chebyshev growth by cp_.buffer cells: separable, x then y then z.
     void grow()
     {
@@ -203,31 +201,35 @@ private:
             }
     }
 
-    long long count(const Region &r) const
-    {
-        long long c = 0;
-        for (int z = r.lo[2]; z < r.hi[2]; ++z)
-            for (int y = r.lo[1]; y < r.hi[1]; ++y)
-                for (int x = r.lo[0]; x < r.hi[0]; ++x) c += at(x, y, z);
-        return c;
-    }
-
-    // Bounding box of the flags inside r; false when there are none.
-    bool shrink(Region &r) const
+    // One pass over region r: the count of its flags, their bounding box (r
+    // shrinks to it) and the signature along each axis over that box; false
+    // when r holds no flag.
+    bool scan(Region &r, long long &cnt)
     {
         int lo[3] = {r.hi[0], r.hi[1], r.hi[2]}, hi[3] = {r.lo[0] - 1, r.lo[1] - 1, r.lo[2] - 1};
+        for (int d = 0; d < 3; ++d) sig_[d].assign(r.hi[d] - r.lo[d], 0);
+        cnt = 0;
         for (int z = r.lo[2]; z < r.hi[2]; ++z)
-            for (int y = r.lo[1]; y < r.hi[1]; ++y)
-                for (int x = r.lo[0]; x < r.hi[0]; ++x)
-                    if (at(x, y, z)) {
-                        const int c[3] = {x, y, z};
-                        for (int d = 0; d < 3; ++d) {
-                            if (c[d] < lo[d]) lo[d] = c[d];
-                            if (c[d] > hi[d]) hi[d] = c[d];
-                        }
+            for (int y = r.lo[1]; y < r.hi[1]; ++y) {
+                const char *row = &F_[((size_t)z * ny_ + y) * nx_];
+                for (int x = r.lo[0]; x < r.hi[0]; ++x) {
+                    if (!row[x]) continue;
+                    ++cnt;
+                    sig_[0][x - r.lo[0]] += 1;
+                    sig_[1][y - r.lo[1]] += 1;
+                    sig_[2][z - r.lo[2]] += 1;
+                    const int c[3] = {x, y, z};
+                    for (int d = 0; d < 3; ++d) {
+                        if (c[d] < lo[d]) lo[d] = c[d];
+                        if (c[d] > hi[d]) hi[d] = c[d];
                     }
-        if (hi[0] < lo[0]) return false;
+                }
+            }
+        if (cnt == 0) return false;
         for (int d = 0; d < 3; ++d) {
+            // keep the signature entries inside the bounding box
+            sig_[d].erase(sig_[d].begin() + (hi[d] + 1 - r.lo[d]), sig_[d].end());
+            sig_[d].erase(sig_[d].begin(), sig_[d].begin() + (lo[d] - r.lo[d]));
             r.lo[d] = lo[d];
             r.hi[d] = hi[d] + 1;
         }
@@ -235,19 +237,12 @@ private:
     }
 
     // Cut position (cells in the low part) at the strongest inflection of the
-    // signature along ax, or 0 when there is none.
-    int best_cut(const Region &r, int ax) const
+    // signature along ax (from the last scan), or 0 when there is none.
+    int best_cut(int ax) const
     {
-        const int n = r.hi[ax] - r.lo[ax];
+        const std::vector<long long> &sig = sig_[ax];
+        const int n = (int)sig.size();
         if (n < 4) return 0;
-        std::vector<long long> sig(n, 0);
-        for (int z = r.lo[2]; z < r.hi[2]; ++z)
-            for (int y = r.lo[1]; y < r.hi[1]; ++y)
-                for (int x = r.lo[0]; x < r.hi[0]; ++x)
-                    if (at(x, y, z)) {
-                        const int c[3] = {x, y, z};
-                        sig[c[ax] - r.lo[ax]] += 1;
-                    }
         // second difference D[j] at signature index j + 1
         std::vector<long long> D(n - 2);
         for (int j = 0; j < n - 2; ++j) D[j] = sig[j] - 2 * sig[j + 1] + sig[j + 2];
@@ -267,6 +262,7 @@ private:
         return best_c;
     }
 
+    std::vector<long long> sig_[3];
     int nx_, ny_, nz_;
     enzo_cluster_params cp_;
     std::vector<char> F_;
