@@ -464,8 +464,10 @@ def run_variants(args, rank, world):
     """The sweep's optional rows on the headline's level (periodic patches of 8..64
     cells per axis): FP32 plain; with the reconstruction options (contact
     steepening, flattening, diffusive flux); with HLLC and with HLL as the
-    interface solver; with dual energy (gas energy from E - KE of the initial
-    state); FP64 with the options and with dual energy.  Each runs the device
+    interface solver; HLLC and the two-shock solver with fallback mode 2 (HLL
+    re-flux of cells whose internal energy would go negative); with dual energy
+    (gas energy from E - KE of the initial state); FP64 with the options and
+    with dual energy.  Each runs the device
     CFL timestep and three sweeps per step, W warm-up steps then K timed steps
     (2 for FP64) bracketed by CUDA events on the launching stream, each sweep
     also timed alone for the roofline: algorithmic bytes 80 per cell-sweep (5
@@ -505,6 +507,9 @@ def run_variants(args, rank, world):
                 ("fp32_options", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, options=opts), 80),
                 ("fp32_hllc", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, solver=ez.SOLVER_HLLC), 80),
                 ("fp32_hll", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, solver=ez.SOLVER_HLL), 80),
+                ("fp32_hllc_fallback2", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, solver=ez.SOLVER_HLLC,
+                                                  fallback=2), 80),
+                ("fp32_fallback2", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, fallback=2), 80),
                 ("fp32_dual", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, options=ez.OPT_DUAL), 96),
                 ("fp64_options", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP64, options=opts), 80),
                 ("fp64_dual", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP64, options=ez.OPT_DUAL), 96)]
@@ -539,7 +544,8 @@ def run_variants(args, rank, world):
                          "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                       "frac": achieved / peak, "bytes_per_cell_sweep": bpc},
                          "newton_iters_per_interface": st["newton_iters"] / max(1, st["interfaces"]),
-                         "hll_cells": st["hll_cells"], "ge_pressure": st["ge_pressure"], "nan": st["nan"]}
+                         "hll_cells": st["hll_cells"], "ge_pressure": st["ge_pressure"], "nan": st["nan"],
+                         "p_floor_hits": st["p_floor_hits"], "neg_after": st["neg_after"]}
     launches = ez.launch_count() - launches0
     head = out["fp32_options"]
     return {"metric": METRIC, "value": head["value"], "unit": "Mcell-updates/s", "n_gpus": world,

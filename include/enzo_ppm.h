@@ -64,7 +64,7 @@ enum {
     ENZO_ST_NEWTON_ITERS = 1, /* Newton updates, summed */
     ENZO_ST_NEWTON_NONCONV = 2,/* interfaces whose Newton hit the cap */
     ENZO_ST_HLL_CELLS = 3,    /* cells that went to rho <= 0 and were re-fluxed with HLL */
-    ENZO_ST_NEG_AFTER = 4,    /* cells still at rho <= 0 after the fallback */
+    ENZO_ST_NEG_AFTER = 4,    /* cells still failing the fallback's test after it */
     ENZO_ST_RHO_FLOOR = 5,    /* cell densities raised to rho_floor */
     ENZO_ST_P_FLOOR = 6,      /* cell pressures raised to p_floor */
     ENZO_ST_NAN = 7,          /* updated cells holding NaN */
@@ -155,7 +155,11 @@ typedef struct {
     int32_t guess;      /* ENZO_GUESS_PLAIN | ENZO_GUESS_MLP */
     double newton_tol;  /* residual tolerance; <= 0 selects 1e-14 (FP64) / 1e-6 (FP32) */
     int32_t newton_max; /* Newton update cap; <= 0 selects 20 (FP64) / 12 (FP32) */
-    int32_t fallback;   /* nonzero: HLL re-flux of cells that reach rho <= 0 (Sec. 4.1.2) */
+    int32_t fallback;   /* HLL re-flux (Sec. 4.1.2) of both faces of each cell whose update
+                           fails: 0 off; 1 (default) rho <= 0, the paper's trigger; 2 rho <= 0
+                           or a non-positive internal energy, 2 rho E - |m|^2 <= 0 (the paper
+                           names negative densities or energies; its own kernel instantiations,
+                           not with ENZO_GUESS_MLP).  Other values: ENZO_ERR_ARG */
     double rho_floor;   /* density floor, > 0 */
     double p_floor;     /* pressure floor, > 0 */
     const void *mlp;    /* DEVICE weight blob from enzo_mlp_pack (ENZO_GUESS_MLP only;

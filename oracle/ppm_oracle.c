@@ -59,7 +59,8 @@ typedef struct {
     double p_floor;
     double newton_tol;
     int32_t newton_max;
-    int32_t fallback;     /* 1: HLL re-flux of cells that reach rho <= 0 */
+    int32_t fallback;     /* 1: HLL re-flux of cells that reach rho <= 0; 2: also of cells that
+                             reach E - KE <= 0 (tested as 2 rho E - |m|^2 <= 0) */
     int32_t solver;       /* interface fluxes: 0 two-shock (Sec. 4.1.2), 1 HLL, 2 HLLC */
     int32_t options;      /* bit 0 contact steepening, bit 1 flattening, bit 2 diffusive flux,
                              bit 3 dual energy (a gas-energy field rides along, see pencil_step) */
@@ -70,7 +71,7 @@ typedef struct {
     int64_t newton_iters;    /* Newton updates summed over interfaces */
     int64_t newton_nonconv;  /* interfaces that hit the iteration cap */
     int64_t hll_cells;       /* cells that triggered the HLL fallback */
-    int64_t neg_after;       /* cells with rho <= 0 after the fallback */
+    int64_t neg_after;       /* cells still failing the fallback's test after it */
     int64_t rho_floor_hits;  /* cell primitives raised to rho_floor */
     int64_t p_floor_hits;    /* cell primitives raised to p_floor */
     int64_t ge_pressure;     /* dual energy: zones whose pressure came from the gas energy */
@@ -446,6 +447,20 @@ static void trace_state(const pencil *pc, int s, int side, double dtdx, const or
     }
 }
 
+/* Does updated cell s fail the fallback test?  rho <= 0, and with mode 2 also
+ * a non-positive internal energy, 2 rho E - |m|^2 <= 0 (Sec. 4.1.2 names negative
+ * densities or energies; the paper's trigger is the density). */
+static int fallback_fails(const pencil *pc, int s, const or_params *P)
+{
+    const double rho = pc->U[0][s];
+    if (!(rho > 0.0)) return 1;
+    if (P->fallback == 2) {
+        const double m2 = (pc->U[1][s] * pc->U[1][s] + pc->U[2][s] * pc->U[2][s]) + pc->U[3][s] * pc->U[3][s];
+        if (!((2.0 * rho) * pc->U[4][s] - m2 > 0.0)) return 1;
+    }
+    return 0;
+}
+
 /* Advance one pencil (already gathered into pc->U) by the split update along it.
  * Active cells are [ng, L-ng).  Returns nothing; pc->U is overwritten. */
 /* Dual energy (Sec. 4.1.1: eta1 = 1e-3, eta2 = 0.1), the reading taken here:
@@ -600,13 +615,14 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
                           dtdx * pc->q[2][s] * (pc->uface[s] - pc->uface[s - 1]);
     }
     if (P->fallback) {
-        /* HLL fallback (Sec. 4.1.2): re-flux both faces of each cell with rho <= 0 */
+        /* HLL fallback (Sec. 4.1.2): re-flux both faces of each cell with rho <= 0
+         * (mode 2: or E - KE <= 0) */
         int nbad = 0;
-        for (int s = ng; s < L - ng; ++s) if (!(pc->U[0][s] > 0.0)) nbad++;
+        for (int s = ng; s < L - ng; ++s) if (fallback_fails(pc, s, P)) nbad++;
         if (nbad) {
             char *mark = (char *)calloc((size_t)L, 1);       /* mark[s]: interface s+1/2 */
             for (int s = ng; s < L - ng; ++s)
-                if (!(pc->U[0][s] > 0.0)) { mark[s - 1] = 1; mark[s] = 1; st->hll_cells++; }
+                if (fallback_fails(pc, s, P)) { mark[s - 1] = 1; mark[s] = 1; st->hll_cells++; }
             for (int s = ng - 1; s <= L - ng - 1; ++s) {
                 if (!mark[s]) continue;
                 double F[5];
@@ -626,7 +642,7 @@ static void pencil_step(pencil *pc, int ng, double dtdx, const or_params *P, or_
                 if (dual)
                     pc->U[5][s] = (pc->Uold[5][s] + dtdx * (pc->F[5][s - 1] - pc->F[5][s])) -
                                   dtdx * pc->q[2][s] * (pc->uface[s] - pc->uface[s - 1]);
-                if (!(pc->U[0][s] > 0.0)) st->neg_after++;
+                if (fallback_fails(pc, s, P)) st->neg_after++;
             }
             free(mark);
         }

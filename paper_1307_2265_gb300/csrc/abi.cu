@@ -32,6 +32,11 @@ __device__ __forceinline__ int tiles_of(const enzo_patch &P, int64_t field_len, 
         const int64_t vol = (int64_t)(P.n[0] + 2 * P.ng) * (P.n[1] + 2 * P.ng) * (P.n[2] + 2 * P.ng);
         return (int)((vol + kFillThreads - 1) / kFillThreads);
     }
+    if (kind == kKindTiles8) {
+        const int64_t t0 = (P.n[0] + kFlagTile - 1) / kFlagTile, t1 = (P.n[1] + kFlagTile - 1) / kFlagTile,
+                      t2 = (P.n[2] + kFlagTile - 1) / kFlagTile;
+        return (int)(t0 * t1 * t2);
+    }
     const int64_t cells = (int64_t)P.n[0] * P.n[1] * P.n[2];
     return (int)((cells + kCflCells - 1) / kCflCells);
 }
@@ -198,6 +203,8 @@ static int resolve(const enzo_params *p, MethodParams &m)
     m.newton_tol = p->newton_tol > 0.0 ? p->newton_tol : (f64 ? 1e-14 : 1e-6);
     m.newton_max = p->newton_max > 0 ? p->newton_max : (f64 ? 20 : 12);
     if (m.newton_max > 200) return ENZO_ERR_ARG;
+    if (p->fallback < 0 || p->fallback > 2) return ENZO_ERR_ARG;
+    if (p->fallback == 2 && p->guess == ENZO_GUESS_MLP) return ENZO_ERR_ARG;
     m.fallback = p->fallback;
     m.guess = p->guess;
     m.mlp = p->mlp;
@@ -265,7 +272,8 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
     if ((m.options & ENZO_OPT_DUAL) && (!b->ge || b->freg)) return ENZO_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
     int tile = tile_pencils > 0 ? tile_pencils : kSweepThreads;
-    if (precision == ENZO_FP64 || m.guess == ENZO_GUESS_MLP || b->freg || m.options) tile = kSweepThreads;
+    if (precision == ENZO_FP64 || m.guess == ENZO_GUESS_MLP || b->freg || m.options || m.fallback == 2)
+        tile = kSweepThreads;
     int r = launch_prefix(b, kKindSweep, dir, cover, false, s, tile);
     if (r) return r;
     SweepArgs a;

@@ -1,9 +1,9 @@
 // Hierarchy rebuild (paper Sec. 3.5, 3.6): cell flagging on the GPU and the
 // clustering of flagged cells into new grids on the host.
 //   * flag_kernel: the slope, shock and baryon-mass criteria of Sec. 3.6 per
-//     active cell, in FP64 (built with --fmad=false and IEEE division, so each
-//     operation rounds once in the order written and the flags are exact
-//     functions of the fields);
+//     active cell, from FP32 primitives staged once per 8^3 block (built with
+//     --fmad=false and IEEE division, so each operation rounds once in the
+//     order written and the flags are exact functions of the fields);
 //   * enzo_cluster_flags: Berger & Rigoutsos as Sec. 3.5 describes it, host
 //     C++ over one grid's flags.
 #include <cstdint>
@@ -21,31 +21,28 @@ struct FlagArgs {
     const int *prefix;
     uint8_t *flags;
     const int64_t *flag_off;
-    double gamma, slope, shock_dp, shock_e, mass;
+    float g1, s2, dp, ef;      // gamma - 1, 2 slope, shock_dp, shock_e (rounded to FP32)
+    bool slope, shock;
+    double mass;
 };
 
-// Primitive pieces of one cell used by the criteria.
-struct FlagCell {
-    double rho, E, e, p, m[3];
-};
+constexpr int kHalo = kFlagTile + 2;                 // staged block edge
+constexpr int kStage = kHalo * kHalo * kHalo;        // staged cells per CTA
 
-__device__ __forceinline__ FlagCell flag_cell(const FlagArgs &a, int64_t idx)
-{
-    FlagCell c;
-    c.rho = a.U[0][idx];
-    c.m[0] = a.U[1][idx];
-    c.m[1] = a.U[2][idx];
-    c.m[2] = a.U[3][idx];
-    c.E = a.U[4][idx];
-    const double ke = 0.5 * ((c.m[0] * c.m[0] + c.m[1] * c.m[1]) + c.m[2] * c.m[2]) / c.rho;
-    c.e = c.E - ke;
-    c.p = (a.gamma - 1.0) * c.e;
-    return c;
-}
-
-// One tile = kCflCells active cells of one patch (the CFL work list).
+// One CTA per 8^3 block of active cells.  The block and its one-cell halo
+// (ghost cells, or periodic images for ENZO_PATCH_PERIODIC patches) are staged
+// in shared memory as FP32 primitives once: the conserved FP64 values are
+// rounded toward zero to FP32 on the integer pipe, then 1/rho, KE = (|m|^2 / 2)
+// (1/rho), e = E - KE, p = (gamma - 1) e and u = m (1/rho) follow in FP32 (each
+// operation rounded once: this unit is built with --fmad=false and IEEE
+// division).  The criteria then
+// compare in FP32 without division: |q_{i+1} - q_{i-1}| > 2 slope |q_i| for
+// q = rho, E; |p_{i+1} - p_{i-1}| > shock_dp min(p_{i+1}, p_{i-1}) with
+// u_{i-1} - u_{i+1} > 0 and e_i > shock_e E_i.  The baryon mass test stays in
+// FP64 (rho dx^3 > mass).
 __global__ void __launch_bounds__(256) flag_kernel(const __grid_constant__ FlagArgs a)
 {
+    __shared__ float sr[kStage], sE[kStage], se[kStage], sp[kStage], su[3][kStage];
     const int total = a.prefix[a.npatch];
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
         int lo = 0, hi = a.npatch;
@@ -55,44 +52,63 @@ __global__ void __launch_bounds__(256) flag_kernel(const __grid_constant__ FlagA
         }
         const enzo_patch P = a.patches[lo];
         const int n[3] = {P.n[0], P.n[1], P.n[2]};
+        const int nt0 = (n[0] + kFlagTile - 1) / kFlagTile, nt1 = (n[1] + kFlagTile - 1) / kFlagTile;
+        const int t = tile - a.prefix[lo];
+        const int b0[3] = {(t % nt0) * kFlagTile, ((t / nt0) % nt1) * kFlagTile, (t / (nt0 * nt1)) * kFlagTile};
         const int64_t N0 = n[0] + 2 * P.ng, N1 = n[1] + 2 * P.ng;
-        const int64_t stride[3] = {1, N0, N0 * N1};
         const bool wrap = (P.flags & ENZO_PATCH_PERIODIC) != 0;
-        const int64_t ncell = (int64_t)n[0] * n[1] * n[2];
-        const int64_t first = (int64_t)(tile - a.prefix[lo]) * kCflCells;
+        __syncthreads();                              // the previous tile's reads are done
+        for (int c = threadIdx.x; c < kStage; c += blockDim.x) {
+            const int h[3] = {c % kHalo, (c / kHalo) % kHalo, c / (kHalo * kHalo)};
+            int g[3];
+            bool need = true;
+            for (int d = 0; d < 3; ++d) {
+                g[d] = b0[d] + h[d] - 1;              // active index, -1 .. n
+                if (g[d] > n[d]) need = false;        // past the block's last needed neighbour
+                if (wrap) g[d] = g[d] < 0 ? g[d] + n[d] : (g[d] >= n[d] ? g[d] - n[d] : g[d]);
+            }
+            if (!need) continue;
+            const int64_t idx = P.off + (g[0] + P.ng) + N0 * ((g[1] + P.ng) + N1 * (int64_t)(g[2] + P.ng));
+            const float r = d2f_rz(a.U[0][idx]), m0 = d2f_rz(a.U[1][idx]), m1 = d2f_rz(a.U[2][idx]),
+                        m2 = d2f_rz(a.U[3][idx]), E = d2f_rz(a.U[4][idx]);
+            const float inv = 1.0f / r;
+            const float ke = (0.5f * ((m0 * m0 + m1 * m1) + m2 * m2)) * inv;
+            const float e = E - ke;
+            sr[c] = r;
+            sE[c] = E;
+            se[c] = e;
+            sp[c] = a.g1 * e;
+            su[0][c] = m0 * inv;
+            su[1][c] = m1 * inv;
+            su[2][c] = m2 * inv;
+        }
+        __syncthreads();
         const double vol = P.dx[0] * P.dx[0] * P.dx[0];
-        for (int t = threadIdx.x; t < kCflCells; t += blockDim.x) {
-            const int64_t cell = first + t;
-            if (cell >= ncell) break;
-            const int64_t row = cell / n[0];
-            const int c[3] = {(int)(cell - row * n[0]), (int)(row % n[1]), (int)(row / n[1])};
-            int64_t base = P.off;
-            for (int d = 0; d < 3; ++d) base += (int64_t)(c[d] + P.ng) * stride[d];
-            const FlagCell z = flag_cell(a, base);
+        for (int c = threadIdx.x; c < kFlagTile * kFlagTile * kFlagTile; c += blockDim.x) {
+            const int q[3] = {c % kFlagTile, (c / kFlagTile) % kFlagTile, c / (kFlagTile * kFlagTile)};
+            const int g[3] = {b0[0] + q[0], b0[1] + q[1], b0[2] + q[2]};
+            if (g[0] >= n[0] || g[1] >= n[1] || g[2] >= n[2]) continue;
+            const int k0 = (q[0] + 1) + kHalo * ((q[1] + 1) + kHalo * (q[2] + 1));
+            const int step[3] = {1, kHalo, kHalo * kHalo};
             uint8_t f = 0;
             for (int ax = 0; ax < 3; ++ax) {
-                // neighbours along ax: ghost cells, or the periodic images
-                int64_t im = base - stride[ax], ip = base + stride[ax];
-                if (wrap) {
-                    const int cm = c[ax] == 0 ? n[ax] - 1 : c[ax] - 1;
-                    const int cp = c[ax] == n[ax] - 1 ? 0 : c[ax] + 1;
-                    im = base + (int64_t)(cm - c[ax]) * stride[ax];
-                    ip = base + (int64_t)(cp - c[ax]) * stride[ax];
+                const int km = k0 - step[ax], kp = k0 + step[ax];
+                if (a.slope) {
+                    if (fabsf(sr[kp] - sr[km]) > a.s2 * fabsf(sr[k0])) f |= ENZO_FLAG_SLOPE;
+                    if (fabsf(sE[kp] - sE[km]) > a.s2 * fabsf(sE[k0])) f |= ENZO_FLAG_SLOPE;
                 }
-                const FlagCell zm = flag_cell(a, im), zp = flag_cell(a, ip);
-                if (a.slope > 0.0) {
-                    if (fabs(zp.rho - zm.rho) / (2.0 * fabs(z.rho)) > a.slope) f |= ENZO_FLAG_SLOPE;
-                    if (fabs(zp.E - zm.E) / (2.0 * fabs(z.E)) > a.slope) f |= ENZO_FLAG_SLOPE;
-                }
-                if (a.shock_dp > 0.0) {
-                    const double pmin = zm.p < zp.p ? zm.p : zp.p;
-                    const double um = zm.m[ax] / zm.rho, up = zp.m[ax] / zp.rho;
-                    if (fabs(zp.p - zm.p) / pmin > a.shock_dp && um - up > 0.0 && z.e / z.E > a.shock_e)
+                if (a.shock) {
+                    const float pm = sp[km], pp = sp[kp];
+                    const float pmin = pm < pp ? pm : pp;
+                    if (fabsf(pp - pm) > a.dp * pmin && su[ax][km] - su[ax][kp] > 0.0f && se[k0] > a.ef * sE[k0])
                         f |= ENZO_FLAG_SHOCK;
                 }
             }
-            if (a.mass > 0.0 && z.rho * vol > a.mass) f |= ENZO_FLAG_MASS;
-            a.flags[a.flag_off[lo] + cell] = f;
+            if (a.mass > 0.0) {
+                const int64_t idx = P.off + (g[0] + P.ng) + N0 * ((g[1] + P.ng) + N1 * (int64_t)(g[2] + P.ng));
+                if (a.U[0][idx] * vol > a.mass) f |= ENZO_FLAG_MASS;
+            }
+            a.flags[a.flag_off[lo] + g[0] + (int64_t)n[0] * (g[1] + (int64_t)n[1] * g[2])] = f;
         }
     }
 }
@@ -116,13 +132,39 @@ public:
     Clusterer(const uint8_t *flags, const int32_t n[3], const enzo_cluster_params &cp)
         : nx_(n[0]), ny_(n[1]), nz_(n[2]), cp_(cp), F_((size_t)n[0] * n[1] * n[2])
     {
-        for (size_t i = 0; i < F_.size(); ++i) F_[i] = flags[i] != 0;
+        // everything below works inside the flags' bounding box grown by the
+        // buffer (cells elsewhere are never flagged)
+        int lo[3] = {nx_, ny_, nz_}, hi[3] = {-1, -1, -1};
+        for (int z = 0; z < nz_; ++z)
+            for (int y = 0; y < ny_; ++y) {
+                const size_t row = ((size_t)z * ny_ + y) * nx_;
+                for (int x = 0; x < nx_; ++x) {
+                    const char f = flags[row + x] != 0;
+                    F_[row + x] = f;
+                    if (f) {
+                        const int c[3] = {x, y, z};
+                        for (int d = 0; d < 3; ++d) {
+                            if (c[d] < lo[d]) lo[d] = c[d];
+                            if (c[d] > hi[d]) hi[d] = c[d];
+                        }
+                    }
+                }
+            }
+        const int ext[3] = {nx_, ny_, nz_};
+        for (int d = 0; d < 3; ++d) {
+            box_.lo[d] = lo[d] - cp.buffer < 0 ? 0 : lo[d] - cp.buffer;
+            box_.hi[d] = hi[d] + 1 + cp.buffer > ext[d] ? ext[d] : hi[d] + 1 + cp.buffer;
+        }
+        if (hi[0] < 0) {
+            for (int d = 0; d < 3; ++d) box_.lo[d] = box_.hi[d] = 0;
+            return;
+        }
         grow();
         const int k = cp.margin;
         if (k > 0)
-            for (int z = 0; z < nz_; ++z)
-                for (int y = 0; y < ny_; ++y)
-                    for (int x = 0; x < nx_; ++x)
+            for (int z = box_.lo[2]; z < box_.hi[2]; ++z)
+                for (int y = box_.lo[1]; y < box_.hi[1]; ++y)
+                    for (int x = box_.lo[0]; x < box_.hi[0]; ++x)
                         if (x < k || x >= nx_ - k || y < k || y >= ny_ - k || z < k || z >= nz_ - k)
                             F_[((size_t)z * ny_ + y) * nx_ + x] = 0;
     }
@@ -132,7 +174,7 @@ public:
         // depth first, the low part before the high part: a stack popped from
         // the back with the high part pushed first
         std::vector<Region> stack;
-        stack.push_back(Region{{0, 0, 0}, {nx_, ny_, nz_}});
+        if (box_.hi[0] > box_.lo[0]) stack.push_back(box_);
         while (!stack.empty()) {
             Region r = stack.back();
             stack.pop_back();
@@ -178,26 +220,31 @@ public:
     }
 
 private:
-    // Chebyshev growth by cp_.buffer cells: separable, x then y then z.
+    // Chebyshev growth by cp_.buffer cells: separable, x then y then z, one
+    // cell per pass, inside box_ (which holds every cell the growth reaches).
     void grow()
     {
-        const int n[3] = {nx_, ny_, nz_};
+        const int e[3] = {box_.hi[0] - box_.lo[0], box_.hi[1] - box_.lo[1], box_.hi[2] - box_.lo[2]};
+        std::vector<char> G((size_t)e[0] * e[1] * e[2]);
         for (int ax = 0; ax < 3; ++ax)
             for (int it = 0; it < cp_.buffer; ++it) {
-                std::vector<char> G(F_);
-                for (int z = 0; z < nz_; ++z)
-                    for (int y = 0; y < ny_; ++y)
-                        for (int x = 0; x < nx_; ++x) {
+                for (int z = 0; z < e[2]; ++z)
+                    for (int y = 0; y < e[1]; ++y)
+                        for (int x = 0; x < e[0]; ++x)
+                            G[((size_t)z * e[1] + y) * e[0] + x] =
+                                F_[((size_t)(z + box_.lo[2]) * ny_ + y + box_.lo[1]) * nx_ + x + box_.lo[0]];
+                for (int z = 0; z < e[2]; ++z)
+                    for (int y = 0; y < e[1]; ++y)
+                        for (int x = 0; x < e[0]; ++x) {
+                            if (!G[((size_t)z * e[1] + y) * e[0] + x]) continue;
                             const int c[3] = {x, y, z};
-                            if (!F_[((size_t)z * ny_ + y) * nx_ + x]) continue;
                             for (int s = -1; s <= 1; s += 2) {
                                 int q[3] = {c[0], c[1], c[2]};
                                 q[ax] += s;
-                                if (q[ax] < 0 || q[ax] >= n[ax]) continue;
-                                G[((size_t)q[2] * ny_ + q[1]) * nx_ + q[0]] = 1;
+                                if (q[ax] < 0 || q[ax] >= e[ax]) continue;
+                                F_[((size_t)(q[2] + box_.lo[2]) * ny_ + q[1] + box_.lo[1]) * nx_ + q[0] + box_.lo[0]] = 1;
                             }
                         }
-                F_.swap(G);
             }
     }
 
@@ -263,6 +310,7 @@ private:
     }
 
     std::vector<long long> sig_[3];
+    Region box_;
     int nx_, ny_, nz_;
     enzo_cluster_params cp_;
     std::vector<char> F_;
@@ -285,8 +333,9 @@ int enzo_flag_cells(const enzo_patch_batch *b, const enzo_flag_params *fp, uint8
     if (!(fp->gamma > 1.0)) return ENZO_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
     char *ws = static_cast<char *>(b->workspace);
-    launch_tile_prefix(b->patches, b->npatch, b->field_len, kKindCells, 0, 0, reinterpret_cast<int *>(ws + kWsPrefix),
-                       reinterpret_cast<unsigned *>(ws + kWsCounter), nullptr, b->status, s);
+    launch_tile_prefix(b->patches, b->npatch, b->field_len, kKindTiles8, 0, 0,
+                       reinterpret_cast<int *>(ws + kWsPrefix), reinterpret_cast<unsigned *>(ws + kWsCounter),
+                       nullptr, b->status, s);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
     FlagArgs a;
@@ -296,12 +345,14 @@ int enzo_flag_cells(const enzo_patch_batch *b, const enzo_flag_params *fp, uint8
     a.prefix = reinterpret_cast<const int *>(ws + kWsPrefix);
     a.flags = flags;
     a.flag_off = flag_off;
-    a.gamma = fp->gamma;
-    a.slope = fp->slope;
-    a.shock_dp = fp->shock_dp;
-    a.shock_e = fp->shock_e;
+    a.g1 = (float)(fp->gamma - 1.0);
+    a.s2 = (float)(2.0 * fp->slope);
+    a.dp = (float)fp->shock_dp;
+    a.ef = (float)fp->shock_e;
+    a.slope = fp->slope > 0.0;
+    a.shock = fp->shock_dp > 0.0;
     a.mass = fp->mass;
-    flag_kernel<<<sms() * 8, 256, 0, s>>>(a);
+    flag_kernel<<<sms() * 6, 256, 0, s>>>(a);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
 }

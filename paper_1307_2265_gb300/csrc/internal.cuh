@@ -128,12 +128,29 @@ cudaError_t launch_riemann_fp32(const RiemannArgs &a, cudaStream_t s);
 void note_launch(unsigned n = 1);
 
 // Work-list kinds of the tile prefix: sweep pencils, ghost-fill cells (whole
-// stored block), active cells (kCflCells per tile).
-enum { kKindSweep = 0, kKindFill = 1, kKindCells = 2 };
+// stored block), active cells (kCflCells per tile), 8^3 blocks of active cells.
+enum { kKindSweep = 0, kKindFill = 1, kKindCells = 2, kKindTiles8 = 3 };
+constexpr int kFlagTile = 8;            // flag kernel: 8^3 active cells per CTA
 
 // Launch of the per-patch tile prefix kernel (kind: kKind*) on stream s.
 void launch_tile_prefix(const enzo_patch *patches, int npatch, int64_t field_len, int kind, int dir,
                         int cover, int *prefix, unsigned *counter, unsigned long long *rate_bits,
                         unsigned long long *status, cudaStream_t s, int tile_pencils = kSweepThreads);
+
+#ifdef __CUDACC__
+// double -> float on the integer pipe.  On GB300 the FP64 pipe retires 2
+// thread-operations per clock per SM (1/64 of FP32), and F2F conversions run
+// on it, so FP32 work converts with bit operations: round toward zero (error
+// below one FP32 ulp); values below the FP32 normal range flush to zero,
+// values above it (and NaN) become infinite.
+__device__ __forceinline__ float d2f_rz(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    const unsigned bits = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return __uint_as_float(e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : bits));
+}
+#endif
 
 }  // namespace enzo

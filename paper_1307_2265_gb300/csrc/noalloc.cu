@@ -86,6 +86,7 @@ extern "C" int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, do
     m.newton_tol = p->newton_tol > 0.0 ? p->newton_tol : (f64 ? 1e-14 : 1e-6);
     m.newton_max = p->newton_max > 0 ? p->newton_max : (f64 ? 20 : 12);
     if (m.newton_max > 200) return ENZO_ERR_ARG;
+    if (p->fallback < 0 || p->fallback > 2) return ENZO_ERR_ARG;
     m.fallback = p->fallback;
     m.guess = p->guess;
     m.mlp = nullptr;

@@ -106,20 +106,9 @@ __device__ __forceinline__ Zone<double> prim<double, false>(double rho, double m
     return prim<double, true>(rho, mn, m1, m2, E, k, quiet);
 }
 
-// float <-> double conversions on the integer pipe.  On GB300 the FP64 pipe
-// retires 2 thread-operations per clock per SM (1/64 of FP32), and F2F
-// conversions run on it, so the FP32 path converts with bit operations:
-// d2f rounds toward zero (error below one FP32 ulp; values below the FP32
-// normal range flush to zero, values above it become infinite), f2d is exact
-// for normal and zero floats (denormals are already flushed by -ftz).
-__device__ __forceinline__ float d2f_rz(double x)
-{
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
-    const unsigned bits = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-    return __uint_as_float(e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : bits));
-}
+// float <-> double conversions on the integer pipe (d2f_rz: internal.cuh).
+// f2d is exact for normal and zero floats (denormals are already flushed by
+// -ftz).
 __device__ __forceinline__ double f2d_exact(float f)
 {
     const unsigned b = __float_as_uint(f);
@@ -949,6 +938,50 @@ struct Marcher {
                                 __ldg(a.U[1 + A2] + idx), __ldg(a.U[4] + idx), __ldg(a.ge + idx), k, cnt, eps);
     }
 
+    // Fallback mode 2 (EXT kernels): does the Godunov update of cell s with face
+    // fluxes Fm, Fp leave rho <= 0 or a non-positive internal energy (tested as
+    // 2 rho E - |m|^2 <= 0)?  Decided in FP64 on the exact update the cell would
+    // get: the FP64 flux difference, or the FP32 path's widened increments.
+    __device__ __forceinline__ bool fails_full(int s, const R Fm[5], const R Fp[5], R dtdx, double dtdx64) const
+    {
+        const int64_t idx = pc.at(s);
+        const int map[5] = {0, 1 + DIR, 1 + A1, 1 + A2, 4};
+        double u[5];
+        _Pragma("unroll") for (int v = 0; v < 5; ++v)
+        {
+            const double U = a.U[map[v]][idx];
+            if (sizeof(R) == 8) u[v] = cell_update(U, dtdx64, (double)Fm[v], (double)Fp[v]);
+            else u[v] = (U + f2d_exact((float)(dtdx * Fm[v]))) - f2d_exact((float)(dtdx * Fp[v]));
+        }
+        return fails_state(u);
+    }
+
+    // FP32 screen of fallback mode 2: the zone's conserved state rebuilt from its
+    // primitives plus the two faces' FP32 increments.  True only when rho and
+    // E keep at least 1e-3 of their old values and the internal energy at
+    // least 1e-2 of E, far beyond the FP32 rounding of the estimate; a floored
+    // zone never passes (its primitives are not its conserved state).
+    __device__ __forceinline__ bool clearly_ok(const Zone<R> &z, const R Fm[5], const R Fp[5], R dtdx) const
+    {
+        if (!(z.r > (R)4 * k.rho_floor) || !(z.p > (R)4 * k.p_floor)) return false;
+        const R E0 = z.p * k.gm1inv + (R)0.5 * z.r * ((z.u * z.u + z.t1 * z.t1) + z.t2 * z.t2);
+        const R rn = z.r + dtdx * (Fm[0] - Fp[0]);
+        const R m0 = z.r * z.u + dtdx * (Fm[1] - Fp[1]);
+        const R m1 = z.r * z.t1 + dtdx * (Fm[2] - Fp[2]);
+        const R m2 = z.r * z.t2 + dtdx * (Fm[3] - Fp[3]);
+        const R En = E0 + dtdx * (Fm[4] - Fp[4]);
+        if (!(rn > (R)1e-3 * z.r) || !(En > (R)1e-3 * E0)) return false;
+        const R twoRE = (R)2 * rn * En;
+        return twoRE - ((m0 * m0 + m1 * m1) + m2 * m2) > (R)1e-2 * twoRE;
+    }
+
+    static __device__ __forceinline__ bool fails_state(const double u[5])
+    {
+        if (!(u[0] > 0.0)) return true;
+        const double m2 = (u[1] * u[1] + u[2] * u[2]) + u[3] * u[3];
+        return !((2.0 * u[0]) * u[4] - m2 > 0.0);
+    }
+
     // Density of cell s at the start of the sweep (raw, no floor).
     __device__ __forceinline__ double rho_old(int s) const { return a.U[0][pc.at(s)]; }
 
@@ -1001,7 +1034,7 @@ struct Marcher {
             gpend.ok = ok;
         }
         if (!active) return;
-        if (fb && !(u[0] > 0.0)) cnt.rare(ENZO_ST_NEG_AFTER);
+        if (fb && (EXT && a.mp.fallback == 2 ? fails_state(u) : !(u[0] > 0.0))) cnt.rare(ENZO_ST_NEG_AFTER);
         if (u[0] != u[0] || u[4] != u[4]) cnt.rare(ENZO_ST_NAN);
         _Pragma("unroll") for (int v = 0; v < 5; ++v) const_cast<double *>(a.U[map[v]])[idx] = u[v];
     }
@@ -1258,7 +1291,14 @@ struct Marcher {
                             const int c = kk - 3;
                             bool bad = false;
                             if (fb) {
-                                if (sizeof(R) == 8) {
+                                if (EXT && mp.fallback == 2) {
+                                    // FP32: a screen on the zone's own primitives with wide
+                                    // margins; only unclear cells take the exact FP64 test
+                                    // (always with dual energy: the zone pressure may come
+                                    // from the gas energy, not from E)
+                                    bad = (sizeof(R) == 8 || dual || !clearly_ok(zm3, Fgprev, Fg, dtdx))
+                                              ? fails_full(c, Fgprev, Fg, dtdx, dtdx64) : false;
+                                } else if (sizeof(R) == 8) {
                                     bad = !(cell_update(rho_old(c), dtdx64, (double)Fgprev[0], (double)Fg[0]) > 0.0);
                                 } else {
                                     // FP32 screen; cells near zero are decided in FP64
@@ -1764,9 +1804,9 @@ cudaError_t launch_sweep_dir(const SweepArgs &a, int grid, cudaStream_t s)
         }
         return cudaGetLastError();
     }
-    if (a.mp.options) {
-        // the reconstruction options have their own instantiations, so the
-        // default kernels stay as they are
+    if (a.mp.options || a.mp.fallback == 2) {
+        // the reconstruction options (and fallback mode 2) have their own
+        // instantiations, so the default kernels stay as they are
         if (a.freg) {
             switch (a.dir) {
             case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, true, 1><<<grid, kSweepThreads, 0, s>>>(a); break;

@@ -496,7 +496,8 @@ class Hierarchy:
         level above each (Sec. 3.5, 3.6): level l's ghosts are filled, its cells
         flagged on the GPU and each patch's flags clustered on the host; every
         new patch is interpolated from its parent (SecondOrderA) and overwritten
-        by the old patches of its level where they overlap.  On the root, flags
+        by the old patches of its level where they overlap (a level whose boxes
+        come out unchanged is kept as it is).  On the root, flags
         within `margin` cells of the domain boundary are dropped, on deeper
         levels those within `nest` cells of the patch's edge (the coarse cells
         outside every new fine face then lie in the parent).  The fill and
@@ -524,6 +525,13 @@ class Hierarchy:
         origin = np.array([[2 * lo[a] for a in range(3)] for _, lo, _ in boxes], dtype=np.int64).reshape(-1, 3)
         parent = np.array([b[0] for b in boxes], dtype=np.int64)
         old = self.levels[m + 1]
+        same = [(int(p), tuple(int(v) // 2 for v in o), tuple((int(v) + int(w)) // 2 for v, w in zip(o, n_)))
+                for p, o, n_ in zip(old["parent"], old["origin"], old["n"])]
+        if boxes == same:
+            # the same grids: the level stays as it is; the level above may be
+            # new, so its correction parts are planned again
+            self._plan_correction(m, general=True)
+            return boxes
         state = {k: old[k] for k in ("t", "step", "t_old")}
         new = self._build_level(m + 1, n, origin, parent, None, old["has_children"], general=True, state=state)
         if len(n):

@@ -146,3 +146,15 @@ def test_dual_energy_arguments_rejected_without_gpu():
     assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(dual.c())) == -1      # with registers
     assert L.enzo_ppm_sweep_noalloc(ctypes.byref(b), 0, 0.1, 0,
                                     ctypes.byref(ez.Params(options=ez.OPT_DUAL, solver=ez.SOLVER_HLL).c())) == -1
+
+
+def test_fallback_modes_rejected_without_gpu():
+    """fallback accepts 0, 1 and 2; mode 2 runs in the option kernels and not
+    with the learned guess.  Refused on the host before any launch."""
+    L = ez.lib()
+    b = ez._Batch()
+    b.npatch = 0
+    for mode, want in ((0, 0), (1, 0), (2, 0), (3, -1), (-1, -1)):
+        assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(ez.Params(fallback=mode).c())) == want
+    p = ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=4096, fallback=2).c()
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -1

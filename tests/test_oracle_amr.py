@@ -203,3 +203,19 @@ def test_dynamic_w_cycle_keeps_the_shock_refined_and_conserves():
         x_prev = xs.max()
     tot = H.composite_totals(levels)
     assert np.all(np.abs(tot - tot0) <= 1e-12 * np.abs(tot0).max()), (tot0, tot)
+
+
+def test_f32_round_toward_zero():
+    """FP32 rounding toward zero: the result is a float no larger in magnitude
+    than x whose successor away from zero is larger than |x|; floats map to
+    themselves; tiny values flush to zero and huge ones become infinite."""
+    rng = np.random.default_rng(5)
+    x = rng.normal(0, 1, 20000) * 10.0 ** rng.uniform(-30, 30, 20000)
+    r = amr.f32_rz(x).astype(np.float64)
+    assert np.all(np.abs(r) <= np.abs(x))
+    nxt = np.nextafter(amr.f32_rz(x), np.copysign(np.float32(np.inf), x).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(nxt) > np.abs(x))
+    f = rng.normal(0, 1, 1000).astype(np.float32)
+    assert np.array_equal(amr.f32_rz(f.astype(np.float64)), f)
+    assert np.array_equal(amr.f32_rz(np.array([1e-40, -1e-40, 1e40, -1e40])),
+                          np.array([0.0, -0.0, np.inf, -np.inf], dtype=np.float32))

@@ -684,3 +684,58 @@ def test_dual_energy_removes_pressure_floors_in_cold_hypersonic_gas():
     assert floors[0] > 1000 and floors[1] < floors[0] / 4, floors
     for f, t0 in zip(U, tot0):
         assert abs(_active(f).sum() - t0) <= 1e-13 * np.abs(_active(f)).sum()
+
+
+def _rarefaction_123(U0=6.0, N=100, g=1.4):
+    """Two streams leaving x = 0.5 at -U0 | +U0 (rho 1, p 0.4; Toro's 123
+    problem made stronger), periodic, so they also meet at x = 0."""
+    x = (np.arange(N) + 0.5) / N
+    sh = (1, 1, N)
+    u = np.where(x < 0.5, -U0, U0).reshape(sh)
+    z = np.zeros(sh)
+    return [synth.embed(f) for f in synth.prims_to_conserved(np.ones(sh), u, z, z, np.full(sh, 0.4), g)]
+
+
+def test_fallback_on_energies_removes_pressure_floors_in_a_strong_rarefaction():
+    """Sec. 4.1.2: high-order fluxes can drive densities or energies negative.
+    In a near-vacuum rarefaction the two-shock scheme leaves E - KE < 0 in a
+    few hundred cell updates over 30 steps (each floors the pressure) while
+    the density stays positive, so the density-triggered fallback (mode 1)
+    never fires; mode 2 also re-fluxes cells whose internal energy would go
+    negative, after which no pressure is floored and none fails, and the
+    periodic totals stay conserved."""
+    g = 1.4
+    dx = [1.0 / 100, 1e30, 1e30]
+    out = {}
+    for mode in (1, 2):
+        U = _rarefaction_123()
+        tot0 = [_active(f).sum() for f in U]
+        P = oracle.Params(gamma=g, p_floor=1e-10, rho_floor=1e-10, fallback=mode)
+        st_all = {}
+        for s in range(30):
+            dt = 0.4 / oracle.cfl_rate(U, dx, P)
+            st = oracle.step_periodic(U, dx, dt, s, P)
+            for k, v in st.items():
+                st_all[k] = st_all.get(k, 0) + v
+        for f, t0 in zip(U, tot0):
+            assert abs(_active(f).sum() - t0) <= 1e-13 * max(1.0, np.abs(_active(f)).sum())
+        out[mode] = st_all
+    assert out[1]["p_floor_hits"] > 100 and out[1]["hll_cells"] == 0
+    assert out[2]["p_floor_hits"] == 0 and out[2]["hll_cells"] > 0 and out[2]["neg_after"] == 0
+
+
+def test_fallback_on_energies_leaves_ordinary_flow_unchanged():
+    """Mach-1 white noise: no update fails either test, so mode 2 gives mode 1's
+    result bit for bit (a wrong energy test, e.g. rho E - |m|^2, would
+    re-flux cells here)."""
+    U = _grid((12, 10, 8), seed=31)
+    V = [f.copy() for f in U]
+    dx = [1 / 12] * 3
+    P1, P2 = oracle.Params(fallback=1), oracle.Params(fallback=2)
+    for s in range(5):
+        dt = 0.4 / oracle.cfl_rate(U, dx, P1)
+        oracle.step_periodic(U, dx, dt, s, P1)
+        st = oracle.step_periodic(V, dx, dt, s, P2)
+        assert st["hll_cells"] == 0
+    for a, b in zip(U, V):
+        assert np.array_equal(a, b)
