@@ -224,6 +224,7 @@ def run_gpu(args, rank, world):
     bytes_per_sweep = sweep_bytes(table, True)
 
     def reset():
+        torch.cuda.synchronize()          # nothing still writing the fields
         for u, h in zip(batch.U, host0):
             u.copy_(h, non_blocking=True)
         torch.cuda.synchronize()
@@ -489,6 +490,9 @@ def run_variants(args, rank, world):
     del ge, ke
 
     def reset():
+        # the launching stream is not synchronised with the current one: wait
+        # for its steps before the copies overwrite the fields they write
+        torch.cuda.synchronize()
         for u, h in zip(batch.U + [batch.ge], host0):
             u.copy_(h, non_blocking=True)
         torch.cuda.synchronize()
@@ -744,6 +748,7 @@ def run_single_grid(args, rank, world):
     cells = n ** 3
 
     def reset():
+        torch.cuda.synchronize()          # nothing still writing the fields
         for u, i in zip(batch.U, init):
             u.copy_(i)
         torch.cuda.synchronize()

@@ -1020,8 +1020,16 @@ struct Marcher {
             double enew = 0.0;
             const bool ok = u[0] > 0.0;
             if (ok) {
-                const double ke = 0.5 * ((u[1] * u[1] + u[2] * u[2]) + u[3] * u[3]) / u[0];
-                enew = u[4] - ke;
+                if (sizeof(R) == 8) {
+                    const double ke = 0.5 * ((u[1] * u[1] + u[2] * u[2]) + u[3] * u[3]) / u[0];
+                    enew = u[4] - ke;
+                } else {
+                    // FP32 path: KE in FP32 off the FP64 pipe; E - KE is only
+                    // taken where it exceeds 0.1 E, so its error stays below
+                    // 1e-6 of it
+                    const float r = d2f_rz(u[0]), m0 = d2f_rz(u[1]), m1 = d2f_rz(u[2]), m2 = d2f_rz(u[3]);
+                    enew = u[4] - f2d_exact((R)0.5 * ((m0 * m0 + m1 * m1) + m2 * m2) / r);
+                }
             }
             if (gpend.idx >= 0) {
                 ge_commit(u[4]);
@@ -1560,13 +1568,16 @@ __device__ __forceinline__ void warp_flush(unsigned long long *status, unsigned 
 #ifndef ENZO_SWEEP_MIN_BLOCKS_FP32
 #define ENZO_SWEEP_MIN_BLOCKS_FP32 4   // 128 registers per thread: 16 warps per SM
 #endif
+#ifndef ENZO_SWEEP_MIN_BLOCKS_DUAL
+#define ENZO_SWEEP_MIN_BLOCKS_DUAL 3   // dual energy (FP32): 168 registers per thread
+#endif
 // LEARNED: the CTA evaluates the learned Newton guess on the tensor cores at
 // every interface step, so all 128 threads march in step (threads without a
 // pencil march a stand-in copy of the tile's first pencil and write nothing).
 // REG: the batch has flux registers (hierarchy levels); the per-pencil register
 // rows are then tracked, otherwise the recording compiles away.
 template <class R, int DIR, bool LEARNED, int THREADS = kSweepThreads, bool REG = false, int EXT = 0>
-__global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? ENZO_SWEEP_MIN_BLOCKS_FP32 * 128 / THREADS : 2))
+__global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? (EXT == 2 ? ENZO_SWEEP_MIN_BLOCKS_DUAL : ENZO_SWEEP_MIN_BLOCKS_FP32 * 128 / THREADS) : 2))
     ppm_sweep_kernel(const __grid_constant__ SweepArgs a)
 {
     constexpr int A1 = DIR == 0 ? 1 : 0, A2 = DIR == 2 ? 1 : 2;
@@ -1796,7 +1807,20 @@ cudaError_t launch_sweep_dir(const SweepArgs &a, int grid, cudaStream_t s)
 {
     if (a.mp.options & ENZO_OPT_DUAL) {
         // dual energy (never with flux registers) has its own instantiations
-        // too, so the option kernels without it keep their registers
+        // too, so the option kernels without it keep their registers; their
+        // persistent grid follows their own occupancy
+        static int cached[64] = {0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64) dev = 0;
+        if (!cached[dev]) {
+            int sms = 0, per = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<R, 0, false, kSweepThreads, false, 2>,
+                                                          kSweepThreads, 0);
+            cached[dev] = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+        }
+        grid = cached[dev];
         switch (a.dir) {
         case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, false, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
         case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, false, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
