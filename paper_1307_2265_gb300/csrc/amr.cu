@@ -8,6 +8,7 @@
 //     C++ over one grid's flags.
 #include <cstdint>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "internal.cuh"
@@ -130,43 +131,66 @@ struct Region {
 class Clusterer {
 public:
     Clusterer(const uint8_t *flags, const int32_t n[3], const enzo_cluster_params &cp)
-        : nx_(n[0]), ny_(n[1]), nz_(n[2]), cp_(cp), F_((size_t)n[0] * n[1] * n[2])
+        : nx_(n[0]), ny_(n[1]), nz_(n[2]), cp_(cp)
     {
-        // everything below works inside the flags' bounding box grown by the
-        // buffer (cells elsewhere are never flagged)
+        // the flags' bounding box, eight flags at a time over empty stretches;
+        // everything after works inside it grown by the buffer (cells
+        // elsewhere are never flagged)
         int lo[3] = {nx_, ny_, nz_}, hi[3] = {-1, -1, -1};
         for (int z = 0; z < nz_; ++z)
             for (int y = 0; y < ny_; ++y) {
-                const size_t row = ((size_t)z * ny_ + y) * nx_;
-                for (int x = 0; x < nx_; ++x) {
-                    const char f = flags[row + x] != 0;
-                    F_[row + x] = f;
-                    if (f) {
-                        const int c[3] = {x, y, z};
-                        for (int d = 0; d < 3; ++d) {
-                            if (c[d] < lo[d]) lo[d] = c[d];
-                            if (c[d] > hi[d]) hi[d] = c[d];
+                const uint8_t *row = flags + ((size_t)z * ny_ + y) * nx_;
+                int first = -1, last = -1, x = 0;
+                for (; x + 8 <= nx_; x += 8) {
+                    uint64_t w;
+                    memcpy(&w, row + x, 8);
+                    if (!w) continue;
+                    for (int i = 0; i < 8; ++i)
+                        if (row[x + i]) {
+                            if (first < 0) first = x + i;
+                            last = x + i;
                         }
-                    }
                 }
+                for (; x < nx_; ++x)
+                    if (row[x]) {
+                        if (first < 0) first = x;
+                        last = x;
+                    }
+                if (first < 0) continue;
+                if (first < lo[0]) lo[0] = first;
+                if (last > hi[0]) hi[0] = last;
+                if (y < lo[1]) lo[1] = y;
+                if (y > hi[1]) hi[1] = y;
+                if (z < lo[2]) lo[2] = z;
+                if (z > hi[2]) hi[2] = z;
             }
+        if (hi[0] < 0) {
+            for (int d = 0; d < 3; ++d) box_.lo[d] = box_.hi[d] = bd_[d] = 0;
+            return;
+        }
         const int ext[3] = {nx_, ny_, nz_};
         for (int d = 0; d < 3; ++d) {
             box_.lo[d] = lo[d] - cp.buffer < 0 ? 0 : lo[d] - cp.buffer;
             box_.hi[d] = hi[d] + 1 + cp.buffer > ext[d] ? ext[d] : hi[d] + 1 + cp.buffer;
+            bd_[d] = box_.hi[d] - box_.lo[d];
         }
-        if (hi[0] < 0) {
-            for (int d = 0; d < 3; ++d) box_.lo[d] = box_.hi[d] = 0;
-            return;
-        }
+        F_.assign((size_t)bd_[0] * bd_[1] * bd_[2], 0);
+        for (int z = box_.lo[2]; z < box_.hi[2]; ++z)
+            for (int y = box_.lo[1]; y < box_.hi[1]; ++y) {
+                const uint8_t *row = flags + ((size_t)z * ny_ + y) * nx_;
+                char *dst = row_of(y, z);
+                for (int x = box_.lo[0]; x < box_.hi[0]; ++x) dst[x - box_.lo[0]] = row[x] != 0;
+            }
         grow();
         const int k = cp.margin;
         if (k > 0)
             for (int z = box_.lo[2]; z < box_.hi[2]; ++z)
-                for (int y = box_.lo[1]; y < box_.hi[1]; ++y)
+                for (int y = box_.lo[1]; y < box_.hi[1]; ++y) {
+                    char *row = row_of(y, z);
                     for (int x = box_.lo[0]; x < box_.hi[0]; ++x)
                         if (x < k || x >= nx_ - k || y < k || y >= ny_ - k || z < k || z >= nz_ - k)
-                            F_[((size_t)z * ny_ + y) * nx_ + x] = 0;
+                            row[x - box_.lo[0]] = 0;
+                }
     }
 
     void run(std::vector<Region> &out)
@@ -220,19 +244,21 @@ public:
     }
 
 private:
+    // Flags of the row (y, z) of the bounding box, indexed by x - box_.lo[0].
+    char *row_of(int y, int z) { return &F_[((size_t)(z - box_.lo[2]) * bd_[1] + (y - box_.lo[1])) * bd_[0]]; }
+    const char *row_of(int y, int z) const
+    {
+        return &F_[((size_t)(z - box_.lo[2]) * bd_[1] + (y - box_.lo[1])) * bd_[0]];
+    }
+
     // Chebyshev growth by cp_.buffer cells: separable, x then y then z, one
     // cell per pass, inside box_ (which holds every cell the growth reaches).
     void grow()
     {
-        const int e[3] = {box_.hi[0] - box_.lo[0], box_.hi[1] - box_.lo[1], box_.hi[2] - box_.lo[2]};
-        std::vector<char> G((size_t)e[0] * e[1] * e[2]);
+        const int *e = bd_;
         for (int ax = 0; ax < 3; ++ax)
             for (int it = 0; it < cp_.buffer; ++it) {
-                for (int z = 0; z < e[2]; ++z)
-                    for (int y = 0; y < e[1]; ++y)
-                        for (int x = 0; x < e[0]; ++x)
-                            G[((size_t)z * e[1] + y) * e[0] + x] =
-                                F_[((size_t)(z + box_.lo[2]) * ny_ + y + box_.lo[1]) * nx_ + x + box_.lo[0]];
+                const std::vector<char> G(F_);
                 for (int z = 0; z < e[2]; ++z)
                     for (int y = 0; y < e[1]; ++y)
                         for (int x = 0; x < e[0]; ++x) {
@@ -242,7 +268,7 @@ private:
                                 int q[3] = {c[0], c[1], c[2]};
                                 q[ax] += s;
                                 if (q[ax] < 0 || q[ax] >= e[ax]) continue;
-                                F_[((size_t)(q[2] + box_.lo[2]) * ny_ + q[1] + box_.lo[1]) * nx_ + q[0] + box_.lo[0]] = 1;
+                                F_[((size_t)q[2] * e[1] + q[1]) * e[0] + q[0]] = 1;
                             }
                         }
             }
@@ -258,9 +284,9 @@ private:
         cnt = 0;
         for (int z = r.lo[2]; z < r.hi[2]; ++z)
             for (int y = r.lo[1]; y < r.hi[1]; ++y) {
-                const char *row = &F_[((size_t)z * ny_ + y) * nx_];
+                const char *row = row_of(y, z);
                 for (int x = r.lo[0]; x < r.hi[0]; ++x) {
-                    if (!row[x]) continue;
+                    if (!row[x - box_.lo[0]]) continue;
                     ++cnt;
                     sig_[0][x - r.lo[0]] += 1;
                     sig_[1][y - r.lo[1]] += 1;
@@ -310,7 +336,8 @@ private:
     }
 
     std::vector<long long> sig_[3];
-    Region box_;
+    Region box_;       // the flags' bounding box grown by the buffer
+    int bd_[3];        // its extents
     int nx_, ny_, nz_;
     enzo_cluster_params cp_;
     std::vector<char> F_;
