@@ -183,6 +183,29 @@ def issue_bound(value_mcu, sm_mhz, sms=152):
             "peak_warp_instr_per_s": peak, "bound_mcell_updates_s": bound, "frac": value_mcu / bound}
 
 
+def fp64_alu_roofline(value_mcu, sm_mhz, sms=152):
+    """The plain FP64 sweep against GB300's FP64 pipe (2 thread-instructions per
+    clock per SM at the sampled SM clock): its DFMA + DMUL + DADD thread
+    instructions per cell-sweep from the committed ncu capture (null once the
+    kernel source changed) times the cell-sweeps per second."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp64_alu.json")) as f:
+            t = json.load(f)
+        with open(os.path.join(ROOT, t["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != t["source_sha256_16"]:
+                return None
+        per = float(t["fp64_arith_thread_inst_per_cell_sweep"])
+    except (OSError, KeyError, ValueError):
+        return None
+    peak = sms * 2 * sm_mhz * 1e6                     # FP64 thread instructions per second
+    achieved = per * 3 * value_mcu * 1e6
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "FP64 thread-instructions/s",
+            "frac": achieved / peak, "fp64_arith_per_cell_sweep": per,
+            "fp64_pipe_active_ncu": t.get("fp64_pipe_active"),
+            "peak_source": "recipe unit counts: 152 SMs x 2 FP64 thread-instructions per clock"}
+
+
 def sweep_bytes(table, flags):
     """Algorithmic HBM bytes of one sweep per direction: each pencil reads its
     cells once and writes its active cells once (5 float64 fields).  Periodic
@@ -396,6 +419,7 @@ def run_gpu(args, rank, world):
     }
     sm = (res["clocks"] or {}).get("sm_mhz") or 2070.0
     res["roofline"]["issue"] = issue_bound(value / world, sm)
+    res["fp64_plain"]["roofline"] = fp64_alu_roofline(res["fp64_plain"]["value"], sm)
     return res
 
 

@@ -294,6 +294,9 @@ def cluster_flags(flags, efficiency=0.3, small_cells=64, buffer=1, margin=0):
         return [(tuple(arr[i].lo), tuple(arr[i].hi)) for i in range(nb.value)]
 
 
+_PINNED = {}   # pinned host buffers for the flags, by size (reused across rebuilds)
+
+
 def flag_cells(batch, gamma, slope=0.3, shock_dp=0.33, shock_e=0.1, mass=0.0):
     """Flags (host uint8, one array (z, y, x) per patch) of a batch's active
     cells by the library's flag kernel (Sec. 3.6; ENZO_FLAG_* bits); ghost
@@ -310,7 +313,12 @@ def flag_cells(batch, gamma, slope=0.3, shock_dp=0.33, shock_e=0.1, mass=0.0):
         b = batch.c()
         _check(_lib().enzo_flag_cells(ctypes.byref(b), ctypes.byref(fp), flags.data_ptr(), offd.data_ptr()),
                "enzo_flag_cells")
-        host = flags.cpu().numpy()
+        pinned = _PINNED.get(flags.numel())
+        if pinned is None:
+            pinned = _PINNED[flags.numel()] = torch.empty(flags.numel(), dtype=torch.uint8, pin_memory=True)
+        pinned.copy_(flags, non_blocking=True)
+        stream.synchronize()
+        host = pinned.numpy().copy()
     return [host[off[i]:off[i] + cells[i]].reshape(int(n[i][2]), int(n[i][1]), int(n[i][0]))
             for i in range(len(cells))]
 
