@@ -365,6 +365,9 @@ class Hierarchy:
                                                  l + 1 < nlev, general=False))
         for l in range(nlev - 1):
             self._plan_correction(l, general=False)
+        # the uploads and zero fills above ran on the current stream; the
+        # hierarchy's own stream must not start before they are done
+        torch.cuda.synchronize(self.device)
         self.cell_updates = 0
         self.timing = None          # {op: [(start, end) events]} when profiling
 

@@ -9,6 +9,7 @@ import math
 
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import paper_1307_2265_gb300 as ez
@@ -160,3 +161,41 @@ def test_dynamic_fp32_conserves_the_composite_totals():
         hier.root_step(ez.Params(precision=ez.FP32, gamma=g), rebuild=rb)
     t1, _ = _gpu_totals(hier)
     assert np.all(np.abs(t1 - t0) <= 1e-13 * scale.max()), (t1 - t0) / scale.max()
+
+
+def test_an_emptied_level_matches_the_oracle():
+    """Level 1 empties on the first rebuild of a uniform moving state, the root
+    steps alone, and a density bump brings refinement back: grids and fields
+    bit-identical to the oracle's at every root step (FP64)."""
+    g = 1.4
+    N = 32
+    one = np.ones((8, 8, N))
+    z = np.zeros_like(one)
+    root = [synth.embed(f) for f in synth.prims_to_conserved(one, 0.3 * one, z, z, one, g)]
+    f1 = np.ones((4, 4, 16))
+    fine = [synth.embed(f) for f in synth.prims_to_conserved(f1, 0.3 * f1, 0 * f1, 0 * f1, f1, g)]
+    layout = [{"n": np.array([(N, 8, 8)]), "origin": np.zeros((1, 3), int), "parent": np.array([-1])},
+              {"n": np.array([(16, 4, 4)]), "origin": np.array([(24, 6, 6)]), "parent": np.array([0])}]
+    ref = H.make_levels(layout, [[root], [fine]], 1.0 / N)
+    hier = gh.Hierarchy(layout, [[root], [fine]], 1.0 / N)
+    P = oracle.Params(gamma=g)
+    params = ez.Params(precision=ez.FP64, gamma=g)
+    rb = {"gamma": g, "crit": CRIT, "clus": CLUS}
+    bump = 3.0 * np.exp(-((np.arange(N) - 16.0) / 1.5) ** 2)
+    for step in range(4):
+        if step == 2:
+            r = ref[0]["patches"][0]["U"]
+            for f in range(5):
+                r[f][3:-3, 3:-3, 3:-3] *= (1.0 + bump)
+            hier.stream.synchronize()
+            for f, u in enumerate(hier.levels[0]["batch"].U):
+                u.copy_(torch.from_numpy(r[f].ravel()).to(u.device))
+            torch.cuda.synchronize()                  # the copies land before the hierarchy's stream reads
+        log_o, log_g = [], []
+        H.root_step(ref, P, log=log_o, rebuild=rb)
+        hier.root_step(params, log=log_g, rebuild=rb)
+        assert log_g == log_o
+        _assert_same(ref, hier)
+        if step < 2:
+            assert len(hier.levels[1]["n"]) == 0
+    assert len(hier.levels[1]["n"]) >= 1

@@ -219,3 +219,40 @@ def test_f32_round_toward_zero():
     assert np.array_equal(amr.f32_rz(f.astype(np.float64)), f)
     assert np.array_equal(amr.f32_rz(np.array([1e-40, -1e-40, 1e40, -1e40])),
                           np.array([0.0, -0.0, np.inf, -np.inf], dtype=np.float32))
+
+
+def test_a_level_can_empty_and_refill():
+    """A uniform moving state flags nothing, so the first rebuild empties level
+    1; the W-cycle then steps the root alone (the empty level just keeps pace).
+    A density bump added afterwards is flagged and refined again, and the
+    composite totals hold throughout."""
+    g = 1.4
+    N = 32
+    shape = (8, 8, N)
+    one = np.ones(shape)
+    z = np.zeros(shape)
+    root = [synth.embed(f) for f in synth.prims_to_conserved(one, 0.3 * one, z, z, one, g)]
+    fine = [synth.embed(f) for f in synth.prims_to_conserved(np.ones((4, 4, 16)), 0.3 * np.ones((4, 4, 16)),
+                                                             np.zeros((4, 4, 16)), np.zeros((4, 4, 16)),
+                                                             np.ones((4, 4, 16)), g)]
+    layout = [{"n": np.array([(N, 8, 8)]), "origin": np.zeros((1, 3), int), "parent": np.array([-1])},
+              {"n": np.array([(16, 4, 4)]), "origin": np.array([(24, 6, 6)]), "parent": np.array([0])}]
+    levels = H.make_levels(layout, [[root], [fine]], 1.0 / N)
+    P = oracle.Params(gamma=g)
+    rb = {"gamma": g, "crit": {"slope": 0.3, "shock_dp": 0.33}, "clus": {"efficiency": 0.3, "small_cells": 8}}
+    tot0 = H.composite_totals(levels)
+    H.root_step(levels, P, rebuild=rb)
+    assert levels[1]["patches"] == []
+    H.root_step(levels, P, rebuild=rb)
+    assert levels[1]["t"] == levels[0]["t"]
+    totA = H.composite_totals(levels)
+    assert np.all(np.abs(totA - tot0) <= 1e-13 * np.abs(tot0).max())
+    r = levels[0]["patches"][0]["U"]
+    bump = 3.0 * np.exp(-((np.arange(N) - 16.0) / 1.5) ** 2)
+    for f in range(5):
+        r[f][3:-3, 3:-3, 3:-3] *= (1.0 + bump)         # rho, m, E scale together: u and p/rho kept
+    tot1 = H.composite_totals(levels)
+    H.root_step(levels, P, rebuild=rb)
+    assert len(levels[1]["patches"]) >= 1
+    tot2 = H.composite_totals(levels)
+    assert np.all(np.abs(tot2 - tot1) <= 1e-13 * np.abs(tot1).max())
