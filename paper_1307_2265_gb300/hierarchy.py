@@ -609,8 +609,9 @@ class Hierarchy:
                     self._fill(l, params.precision)
                     self._end(m)
                     child = self.levels[l + 1]
-                    lo, hi = child["bnd_sl"]
-                    child["batch"].freg[lo:hi].zero_()
+                    if child["batch"].freg is not None:         # None: a level without grids
+                        lo, hi = child["bnd_sl"]
+                        child["batch"].freg[lo:hi].zero_()
                     self.evolve_level(l + 1, lev["t"], params, cfl_params, log, rebuild)
                     m = self._mark("correct_project")
                     self._correct_and_project(l, dt, params)
