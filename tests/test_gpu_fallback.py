@@ -85,3 +85,19 @@ def test_mode2_fp32_keeps_the_rarefaction_finite(solver):
     assert float(active(g[0]).min()) > 0.0
     for f, t0 in zip(g, tot0):
         assert abs(float(active(f).sum()) - t0) <= 1e-12 * max(1.0, float(np.abs(active(f)).sum()))
+
+
+def test_mode2_noalloc_sweep_matches_the_batch_sweep():
+    U = _rarefaction()
+    dx = [1.0 / 100, 1e30, 1e30]
+    a = batch_from_patches([U], dx, flags=ez.PATCH_PERIODIC)
+    c = batch_from_patches([U], dx, flags=ez.PATCH_PERIODIC)
+    p = ez.Params(precision=ez.FP32, gamma=G, p_floor=1e-10, rho_floor=1e-10, fallback=2,
+                  options=ez.OPT_STEEPEN | ez.OPT_FLATTEN)
+    dt = 0.4 / oracle.cfl_rate(U, dx, oracle.Params(gamma=G))
+    for d in (0, 1, 2):
+        ez.ppm_sweep(a, d, dt, 0, p)
+        ez.ppm_sweep_noalloc(c, d, dt, 0, p)
+    for x, y in zip(a.U, c.U):
+        assert bool((x == y).all())
+    assert a.read_status() == c.read_status()

@@ -75,15 +75,18 @@ def test_options_on_a_strong_shock_tube_bitwise():
     assert not np.array_equal(active(ora[0]), active(plain[0]))
 
 
-def test_options_in_the_hierarchy_bitwise():
+@pytest.mark.parametrize("options,fallback", [(ALL, 1), (0, 2), (ALL, 2)])
+def test_options_in_the_hierarchy_bitwise(options, fallback):
+    """The flux-register instantiation of the option kernels (steepening,
+    flattening, diffusion, and fallback mode 2) through a subcycled root step."""
     layout = synth.hierarchy_layout(16, [(4, 12), (6, 10)], [4, 8], seed=5)
     fields = synth.hierarchy_fields(layout, config=5)
     ref = H.make_levels(layout, fields, 1.0 / 16)
     hier = gh.Hierarchy(layout, fields, 1.0 / 16)
-    P = oracle.Params(options=ALL)
+    P = oracle.Params(options=options, fallback=fallback)
     log_o, log_g = [], []
     H.root_step(ref, P, log=log_o)
-    hier.root_step(ez.Params(precision=ez.FP64, options=ALL), log=log_g)
+    hier.root_step(ez.Params(precision=ez.FP64, options=options, fallback=fallback), log=log_g)
     assert log_g == log_o
     hier.stream.synchronize()
     for l, L in enumerate(ref):
