@@ -362,7 +362,7 @@ def composite_totals(levels, r=R):
 
 
 def make_levels(layout, fields, root_dx, root_bc=None):
-    """Level dicts of the reference driver from a synth.hierarchy_layout and its
+    """Level dicts of the oracle's W-cycle driver from a synth.hierarchy_layout and its
     fields (copied); root_bc: external boundaries (bc_x, bc_y, bc_z) of the
     root grid, or None for periodic."""
     levels = []

@@ -21,7 +21,7 @@ __device__ __forceinline__ double minmod(double a, double b)
 }
 
 // SecondOrderA value of child (kz, ky, kx) of the centre of a 3x3x3 parent
-// neighbourhood Q[z][y][x] (r = 2).  T = double: the reference arithmetic;
+// neighbourhood Q[z][y][x] (r = 2).  T = double: the FP64 arithmetic (the oracle's order);
 // T = float: the same steps for the FP32 path (ghost values only feed the
 // FP32 reconstruction; conservation is kept by flux correction).
 template <class T>

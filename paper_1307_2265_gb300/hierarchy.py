@@ -1,21 +1,25 @@
-"""Static AMR hierarchy on the GPU: plans built on the host once, every step of
-the W-cycle run by the library's kernels (paper Sec. 3).
+"""AMR hierarchy on the GPU: host plans per level, every step of the W-cycle
+run by the library's kernels (paper Sec. 3), and an optional rebuild of the
+finer levels from flagged cells (Sec. 3.5, 3.6).
 
-A level is one PatchBatch.  Host plans per level:
+A level is one PatchBatch.  Host plans per level (again after a rebuild):
   * links: origin (global index of the first active cell) and parent index;
   * sibling copy boxes: ghost regions of each patch that lie in a sibling's
-    active box (the patches of a level tile boxes by tensor-product cuts, so a
-    patch's ghost region meets at most its 26 neighbours);
-  * flux-correction faces: faces of fine patches on the boundary of the refined
-    region, with the coarse patch holding the cells outside them;
+    active box.  Static levels tile boxes by tensor-product cuts, so a patch's
+    ghost region meets at most its 26 neighbours, found by a lattice lookup;
+    rebuilt levels are any disjoint boxes, and every pair of patches is
+    intersected;
+  * flux-correction face parts: the cells outside each fine face, per coarse
+    patch holding them, in waves so that corrections meeting in one coarse
+    cell add in a fixed order;
   * flux registers: all-face registers for patches with children, boundary-face
     registers for patches with a parent.
 
-W-cycle of one root step (EvolveLevel of Sec. 3, as in the reference):
+W-cycle of one root step (EvolveLevel of Sec. 3):
   fill ghosts; dt = min(CFL, t_parent - t); save the old state if the level has
   children; three sweeps (recording fluxes); t += dt; if children: fill ghosts
   at the new time, zero the children's boundary registers, advance the children
-  to t, flux correction, projection.
+  to t, flux correction, projection, and (with a rebuild) new finer levels.
 """
 from __future__ import annotations
 
