@@ -91,6 +91,10 @@ def lib():
             L.or_sweep_fluxes.argtypes = five + [_I32, ctypes.c_int32, _D, ctypes.c_int32, ctypes.c_double,
                                                  _I32, _I32, ctypes.POINTER(OrParams), ctypes.POINTER(OrStats), _D]
             L.or_sweep_fluxes.restype = ctypes.c_int
+            L.or_sweep_fluxes_dual.argtypes = five + [_D, _I32, ctypes.c_int32, _D, ctypes.c_int32, ctypes.c_double,
+                                                      _I32, _I32, ctypes.POINTER(OrParams), ctypes.POINTER(OrStats),
+                                                      _D]
+            L.or_sweep_fluxes_dual.restype = ctypes.c_int
             L.or_step_periodic.argtypes = five + [_I32, ctypes.c_int32, _D, ctypes.c_double,
                                                   ctypes.c_int32, ctypes.POINTER(OrParams),
                                                   ctypes.POINTER(OrStats)]
@@ -143,9 +147,13 @@ def _n_of(U, ng):
 
 
 def fill_periodic(U, ng=3):
+    """Periodic ghost fill of the five fields (and of a sixth, the dual-energy
+    gas energy, when U has one: a scalar, filled like the density)."""
     n = _n_of(U, ng)
     na, npn = _i32(n)
-    lib().or_fill_periodic(*_fields(U), npn, ng)
+    lib().or_fill_periodic(*_fields(U[:5]), npn, ng)
+    if len(U) == 6:
+        lib().or_fill_periodic(*_fields([U[5]] * 5), npn, ng)
 
 
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
@@ -155,7 +163,12 @@ def fill_boundary(U, bc, ng=3):
     """External boundaries of a single grid, bc = (bc_x, bc_y, bc_z)."""
     na, npn = _i32(_n_of(U, ng))
     ba, bp = _i32(bc)
-    lib().or_fill_boundary(*_fields(U), npn, ng, bp)
+    lib().or_fill_boundary(*_fields(U[:5]), npn, ng, bp)
+    if len(U) == 6:
+        # the gas energy is a scalar: it takes the density's rule (the momentum
+        # slots, whose reflection negates them, are scratch here)
+        scratch = [np.zeros_like(U[5]) for _ in range(4)]
+        lib().or_fill_boundary(*_fields([U[5]] + scratch), npn, ng, bp)
 
 
 def step_boundary(U, dx, dt, step, bc, params: Params, ng=3) -> dict:
@@ -196,9 +209,11 @@ def sweep(U, dx, direction, dt, lo, hi, params: Params, ng=3) -> dict:
     return st.as_dict()
 
 
-def sweep_fluxes(U, dx, direction, dt, lo, hi, params: Params, ng=3):
+def sweep_fluxes(U, dx, direction, dt, lo, hi, params: Params, ng=3, ge=None):
     """As sweep(), also returning the final face fluxes of the active pencils as
-    an array [n_a2, n_a1, n_dir + 1, 5] (pencil field order rho, m_n, m_t1, m_t2, E)."""
+    an array [n_a2, n_a1, n_dir + 1, 5] (pencil field order rho, m_n, m_t1, m_t2, E).
+    With ge (the dual-energy gas energy, updated in place) the array has a
+    sixth component, the gas-energy flux."""
     n = _n_of(U, ng)
     na, npn = _i32(n)
     la, lp = _i32(lo)
@@ -206,13 +221,18 @@ def sweep_fluxes(U, dx, direction, dt, lo, hi, params: Params, ng=3):
     dxa = np.ascontiguousarray(dx, dtype=np.float64)
     a1 = 1 if direction == 0 else 0
     a2 = 1 if direction == 2 else 2
-    F = np.zeros((n[a2], n[a1], n[direction] + 1, 5))
+    F = np.zeros((n[a2], n[a1], n[direction] + 1, 5 if ge is None else 6))
     p = params.c()
     st = OrStats()
-    r = lib().or_sweep_fluxes(*_fields(U), npn, ng, _dp(dxa), direction, dt, lp, hp, ctypes.byref(p),
-                              ctypes.byref(st), _dp(F))
+    if ge is None:
+        r = lib().or_sweep_fluxes(*_fields(U), npn, ng, _dp(dxa), direction, dt, lp, hp, ctypes.byref(p),
+                                  ctypes.byref(st), _dp(F))
+    else:
+        r = lib().or_sweep_fluxes_dual(*_fields(U), _dp(ge), npn, ng, _dp(dxa), direction, dt, lp, hp,
+                                       ctypes.byref(p), ctypes.byref(st), _dp(F))
     if r:
-        raise MemoryError("oracle sweep could not allocate pencil scratch")
+        raise MemoryError("oracle sweep could not allocate pencil scratch" if r == -1 else
+                          "oracle dual-energy sweep needs option bit 8 and the gas-energy field")
     return F, st.as_dict()
 
 

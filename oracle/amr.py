@@ -230,7 +230,7 @@ def fill_patch_from_parent(child, parent):
     iz = P[0][:, None, None, None] + off[None, :, None, None]
     iy = P[1][:, None, None, None] + off[None, None, :, None]
     ix = P[2][:, None, None, None] + off[None, None, None, :]
-    for f in range(5):
+    for f in range(len(child["U"])):          # five fields, a sixth with dual energy
         Q = parent["U"][f][iz, iy, ix]
         kids = H.second_order_a(Q, H.R)
         child["U"][f][k, j, i] = kids[np.arange(len(k)), kk[0], kk[1], kk[2]]
@@ -249,7 +249,7 @@ def copy_from_old(new, old_level):
             continue
         dn = [slice(lo[t] - glo[t], hi[t] - glo[t]) for t in (2, 1, 0)]
         do = [slice(lo[t] - blo[t] + NG, hi[t] - blo[t] + NG) for t in (2, 1, 0)]
-        for f in range(5):
+        for f in range(len(new["U"])):
             new["U"][f][dn[0], dn[1], dn[2]] = po["U"][f][do[0], do[1], do[2]]
 
 
@@ -263,7 +263,7 @@ def new_boxes(levels, l, gamma, crit, clus, margin=3, nest=1):
     out = []
     L = levels[l]
     for pi, p in enumerate(L["patches"]):
-        fl = flag_patch(p["U"], L["dx"], gamma, **crit)
+        fl = flag_patch(p["U"][:5], L["dx"], gamma, **crit)
         for lo, hi in cluster(fl, margin=margin if l == 0 else nest, **clus):
             o = p["origin"]
             out.append((pi, tuple(o[a] + lo[a] for a in range(3)), tuple(o[a] + hi[a] for a in range(3))))
@@ -288,7 +288,7 @@ def rebuild_level(levels, l, gamma, crit, clus, margin=3, nest=1):
         n = tuple(H.R * (hi[a] - lo[a]) for a in range(3))
         origin = tuple(H.R * lo[a] for a in range(3))
         shape = (n[2] + 2 * NG, n[1] + 2 * NG, n[0] + 2 * NG)
-        p = {"n": n, "origin": origin, "parent": pi, "U": [np.zeros(shape) for _ in range(5)]}
+        p = {"n": n, "origin": origin, "parent": pi, "U": [np.zeros(shape) for _ in par[pi]["U"]]}
         fill_patch_from_parent(p, par[pi])
         copy_from_old(p, old)
         new.append(p)

@@ -24,11 +24,17 @@ Readings where the paper is silent or garbled (listed in the design doc):
   * parent values are interpolated linearly in time between the parent's state
     at the start and end of its step before the spatial interpolation;
   * the sum of each corner's 8 cells runs z-major, then y, then x, and is
-    scaled by 1/8; child values add the x, y, z terms in that order.
+    scaled by 1/8; child values add the x, y, z terms in that order;
+  * with dual energy (Sec. 4.1.1) the gas energy rho e is a sixth field that
+    is interpolated, copied, projected and flux-corrected like the conserved
+    ones; its correction swaps only its advected flux (the -p div v source is a
+    zone term, not a face flux), and neither the time step nor the composite
+    totals use it.
 
 Data model: a level is a list of patches, each a dict with
   n (nx, ny, nz), origin (global index of the first active cell at this level),
-  U (five ghost-zoned arrays, (z, y, x)), parent (index into the parent level or -1).
+  U (five ghost-zoned arrays, (z, y, x), and the gas energy as a sixth when the
+  dual-energy option is on), parent (index into the parent level or -1).
 """
 from __future__ import annotations
 
@@ -137,7 +143,7 @@ def fill_from_parent(child, parent, parent_old, w, r=R):
     iz = P[0][:, None, None, None] + off[None, :, None, None]
     iy = P[1][:, None, None, None] + off[None, None, :, None]
     ix = P[2][:, None, None, None] + off[None, None, None, :]
-    for f in range(5):
+    for f in range(len(child["U"])):          # five fields, a sixth with dual energy
         old = parent_old["U"][f][iz, iy, ix]
         new = parent["U"][f][iz, iy, ix]
         Q = old + w * (new - old)
@@ -161,7 +167,7 @@ def copy_from_siblings(level):
             # storage slices (z, y, x)
             da = [slice(lo[t] - glo[t], hi[t] - glo[t]) for t in (2, 1, 0)]
             db = [slice(lo[t] - blo[t] + NG, hi[t] - blo[t] + NG) for t in (2, 1, 0)]
-            for f in range(5):
+            for f in range(len(pa["U"])):
                 pa["U"][f][da[0], da[1], da[2]] = pb["U"][f][db[0], db[1], db[2]]
 
 
@@ -185,7 +191,7 @@ def fill_level(levels, l, parent_old, w):
 
 def level_rate(levels, l, P):
     dx = levels[l]["dx"]
-    return max(oracle.cfl_rate(p["U"], [dx] * 3, P) for p in levels[l]["patches"])
+    return max(oracle.cfl_rate(p["U"][:5], [dx] * 3, P) for p in levels[l]["patches"])
 
 
 def step_level(levels, l, dt, step_index, P, has_children):
@@ -201,13 +207,14 @@ def step_level(levels, l, dt, step_index, P, has_children):
         for d in order:
             lo = [NG if done[a] else 0 for a in range(3)]
             hi = [NG + n[a] if done[a] else N[a] for a in range(3)]
-            F, _ = oracle.sweep_fluxes(p["U"], [dx] * 3, d, dt, lo, hi, P)
+            ge = p["U"][5] if len(p["U"]) == 6 else None
+            F, _ = oracle.sweep_fluxes(p["U"][:5], [dx] * 3, d, dt, lo, hi, P, ge=ge)
             if has_children:
                 p.setdefault("Fc", {})[d] = F
             if p["parent"] >= 0:
                 reg = p.setdefault("Ff", {})
                 if d not in reg:
-                    reg[d] = np.zeros((F.shape[0], F.shape[1], 2, 5))
+                    reg[d] = np.zeros((F.shape[0], F.shape[1], 2, F.shape[3]))
                 reg[d][:, :, 0, :] += dt * F[:, :, 0, :]
                 reg[d][:, :, 1, :] += dt * F[:, :, -1, :]
             done[d] = True
@@ -217,7 +224,7 @@ def _field_of(d, v):
     """Conserved-field index of pencil component v for a sweep along d."""
     a1 = 1 if d == 0 else 0
     a2 = 1 if d == 2 else 2
-    return (0, 1 + d, 1 + a1, 1 + a2, 4)[v]
+    return (0, 1 + d, 1 + a1, 1 + a2, 4, 5)[v]
 
 
 def flux_correct(levels, l, dt_c, r=R):
@@ -232,8 +239,8 @@ def flux_correct(levels, l, dt_c, r=R):
         for d in range(3):
             a1 = 1 if d == 0 else 0
             a2 = 1 if d == 2 else 2
-            Fc = par["Fc"][d]           # [n_a2, n_a1, n_d + 1, 5] of the parent
-            Ff = fp["Ff"][d]            # [fn_a2, fn_a1, 2, 5]
+            Fc = par["Fc"][d]           # [n_a2, n_a1, n_d + 1, 5 or 6] of the parent
+            Ff = fp["Ff"][d]            # [fn_a2, fn_a1, 2, 5 or 6]
             for side in (0, 1):
                 X = (fo[d] + (fn[d] if side else 0)) // r      # coarse face index (global)
                 cell = X - 1 if side == 0 else X                # coarse cell outside the fine patch
@@ -253,7 +260,7 @@ def flux_correct(levels, l, dt_c, r=R):
                             lo, hi = _box_of(tp)
                             if all(lo[t] <= g[t] < hi[t] for t in range(3)):
                                 s = [g[t] - lo[t] + NG for t in range(3)]
-                                for v in range(5):
+                                for v in range(len(delta)):
                                     f = _field_of(d, v)
                                     if side == 0:
                                         tp["U"][f][s[2], s[1], s[0]] += delta[v]
@@ -271,7 +278,7 @@ def project(levels, l, r=R):
         po = np.array(par["origin"])
         nx, ny, nz = fp["n"]
         c0 = fo // r - po + NG
-        for f in range(5):
+        for f in range(len(fp["U"])):
             a = _active(fp["U"][f])
             s = np.zeros((nz // r, ny // r, nx // r))
             for kz in range(r):

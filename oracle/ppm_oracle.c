@@ -802,6 +802,19 @@ int or_sweep_fluxes(double *U0, double *U1, double *U2, double *U3, double *U4,
     return sweep_ge(U0, U1, U2, U3, U4, NULL, n, ng, dx, dir, dt, lo, hi, P, stats, fout);
 }
 
+/* As or_sweep_fluxes, with the gas-energy field ge of the dual-energy option:
+ * fout then holds six components per face, the sixth the gas-energy flux
+ * (the mass flux times the upwind eps, Sec. 4.1.1), at
+ * fout[((j2 * n[a1] + j1) * (n[dir] + 1) + f) * 6 + v]. */
+int or_sweep_fluxes_dual(double *U0, double *U1, double *U2, double *U3, double *U4, double *ge,
+                         const int32_t n[3], int32_t ng, const double dx[3], int32_t dir, double dt,
+                         const int32_t lo[3], const int32_t hi[3], const or_params *P, or_stats *stats,
+                         double *fout)
+{
+    if (!ge || !(P->options & 8)) return -2;
+    return sweep_ge(U0, U1, U2, U3, U4, ge, n, ng, dx, dir, dt, lo, hi, P, stats, fout);
+}
+
 /* As or_sweep, with the gas-energy field ge of the dual-energy option (may be
  * NULL when the option is off). */
 int or_sweep_dual(double *U0, double *U1, double *U2, double *U3, double *U4, double *ge,
@@ -856,9 +869,10 @@ static int sweep_ge(double *U0, double *U1, double *U2, double *U3, double *U4, 
             if (fout) {
                 int j1 = i1 - ng, j2 = i2 - ng;
                 if (j1 >= 0 && j1 < n[a1] && j2 >= 0 && j2 < n[a2]) {
-                    double *o = fout + ((int64_t)j2 * n[a1] + j1) * (int64_t)(n[dir] + 1) * 5;
+                    const int nf = ge ? 6 : 5;    /* with ge: the gas-energy flux too */
+                    double *o = fout + ((int64_t)j2 * n[a1] + j1) * (int64_t)(n[dir] + 1) * nf;
                     for (int f = 0; f <= n[dir]; ++f)
-                        for (int v = 0; v < 5; ++v) o[f * 5 + v] = pc.F[v][ng - 1 + f];
+                        for (int v = 0; v < nf; ++v) o[f * nf + v] = pc.F[v][ng - 1 + f];
                 }
             }
         }

@@ -292,3 +292,28 @@ def hierarchy_fields(layout, config=5, gamma=5.0 / 3.0, ng=NG):
             fields.append(fl)
         out.append(fields)
     return out
+
+
+def cold_contact_fields(layout, root_n, gamma=1.4, eps=2.0, v=(8.0, 6.0, 5.0), ng=NG):
+    """A density wave rho = 1 + 0.5 sin(2 pi x) cos(2 pi y) sin(2 pi (z + 0.1))
+    at uniform pressure 1 carried by the uniform velocity v (Mach 6.7 to 11.6
+    for gamma 1.4: internal energy 2.6% to 7.3% of E), sampled at each patch's
+    cell centres on every level of `layout` (root cell size 1 / root_n).  A
+    sixth field, the gas energy, is eps * rho.  Per level a list of per-patch
+    field lists (ghost zones zero)."""
+    out = []
+    for l, L in enumerate(layout):
+        dx = 1.0 / (root_n * 2 ** l)
+        per = []
+        for i in range(len(L["n"])):
+            nx, ny, nz = (int(c) for c in L["n"][i])
+            o = L["origin"][i]
+            z, y, x = np.meshgrid((o[2] + np.arange(nz) + 0.5) * dx, (o[1] + np.arange(ny) + 0.5) * dx,
+                                  (o[0] + np.arange(nx) + 0.5) * dx, indexing="ij")
+            rho = 1.0 + 0.5 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) * np.sin(2 * np.pi * (z + 0.1))
+            one = np.ones_like(rho)
+            U = [embed(f, ng) for f in prims_to_conserved(rho, v[0] * one, v[1] * one, v[2] * one, one, gamma)]
+            U.append(embed(eps * rho, ng))
+            per.append(U)
+        out.append(per)
+    return out

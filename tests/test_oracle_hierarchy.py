@@ -99,3 +99,112 @@ def test_uniform_state_preserved_through_the_hierarchy():
         for p, r in zip(L["patches"], ref):
             for a, b in zip(p["U"], r):
                 assert np.allclose(H._active(a), H._active(b), rtol=1e-14, atol=1e-14)
+
+
+# Dual energy through the hierarchy (Sec. 4.1.1 with Sec. 3): the gas energy is
+# a sixth field that every hierarchy operation carries like the conserved ones.
+G_COLD = 1.4
+EPS_COLD = 2.0
+
+
+def _ge_deviation(levels):
+    worst = 0.0
+    for L in levels:
+        for p in L["patches"]:
+            worst = max(worst, float(np.max(np.abs(H._active(p["U"][5]) / H._active(p["U"][0]) - EPS_COLD))))
+    return worst
+
+
+def test_dual_cold_contact_window():
+    """The cold contact keeps every cell's internal energy between the two
+    thresholds: above 1e-3 E (the pressure comes from E - KE) and below 0.1 E
+    (no resynchronisation), so the gas energy is a passive density."""
+    layout = synth.hierarchy_layout(16, [(4, 12), (6, 10)], [4, 8], seed=1)
+    for lev in synth.cold_contact_fields(layout, 16, gamma=G_COLD, eps=EPS_COLD):
+        for U in lev:
+            A = [H._active(f) for f in U]
+            frac = (A[4] - 0.5 * ((A[1] ** 2 + A[2] ** 2) + A[3] ** 2) / A[0]) / A[4]
+            assert 2e-2 < frac.min() and frac.max() < 8e-2
+
+
+@pytest.mark.slow
+def test_dual_gas_energy_follows_the_density_in_a_cold_contact():
+    """With uniform pressure and velocity the Riemann problems are contacts
+    (p* = p, u* = u), the -p div v source vanishes and eps is uniform, so the
+    traced eps is eps and the gas-energy flux is eps times the mass flux; with
+    eps a power of two every hierarchy operation (time and SecondOrderA
+    interpolation, sibling copies, flux registers and correction, projection)
+    maps rho to eps rho exactly.  So ge = eps rho stays bit-exact in every cell
+    of three levels over a root step with subcycling."""
+    layout = synth.hierarchy_layout(16, [(4, 12), (6, 10)], [4, 8], seed=1)
+    levels = H.make_levels(layout, synth.cold_contact_fields(layout, 16, gamma=G_COLD, eps=EPS_COLD), 1.0 / 16)
+    log = []
+    H.root_step(levels, oracle.Params(gamma=G_COLD, options=8), log=log)
+    assert sum(1 for l, _ in log if l == 2) >= 2
+    assert _ge_deviation(levels) == 0.0
+
+
+def _keep_ge(fn, patches_of):
+    """`fn` with the gas energy of the patches it touches restored afterwards
+    (a planted mistake: the operation skips the sixth field)."""
+    def wrapped(*args, **kw):
+        keep = [p["U"][5].copy() for p in patches_of(*args)]
+        fn(*args, **kw)
+        for p, k in zip(patches_of(*args), keep):
+            p["U"][5][...] = k
+    return wrapped
+
+
+@pytest.mark.parametrize("op", ["flux_correct", "project", "copy_from_siblings"])
+def test_dual_pin_catches_a_skipped_gas_energy_operation(op, monkeypatch):
+    """The cold-contact pin fails (by more than 1e-3) when the flux correction,
+    the projection or the sibling copies leave the gas energy out (mistakes
+    planted in the oracle; two levels, one root step)."""
+    layout = synth.hierarchy_layout(16, [(4, 12)], [4, 8], seed=1)
+    levels = H.make_levels(layout, synth.cold_contact_fields(layout, 16, gamma=G_COLD, eps=EPS_COLD), 1.0 / 16)
+    target = {"flux_correct": lambda levels, l, *a: levels[l]["patches"],
+              "project": lambda levels, l, *a: levels[l]["patches"],
+              "copy_from_siblings": lambda level: level}[op]
+    monkeypatch.setattr(H, op, _keep_ge(getattr(H, op), target))
+    H.root_step(levels, oracle.Params(gamma=G_COLD, options=8))
+    assert _ge_deviation(levels) > 1e-3
+
+
+@pytest.mark.slow
+def test_dual_hierarchy_at_low_mach_leaves_the_five_fields_as_without_it():
+    """Where no cell is cold enough to take its pressure from the gas energy,
+    the dual-energy hierarchy steps the five conserved fields bit-identically
+    to the run without the option (the sixth field feeds nothing else)."""
+    layout, plain = _small(seed=3)
+    fields = synth.hierarchy_fields(layout, config=5)
+    six = []
+    for lev in fields:
+        per = []
+        for U in lev:
+            A = [H._active(f) for f in U]
+            per.append([f.copy() for f in U] +
+                       [synth.embed(A[4] - 0.5 * ((A[1] ** 2 + A[2] ** 2) + A[3] ** 2) / A[0])])
+        six.append(per)
+    dual = H.make_levels(layout, six, 1.0 / 16)
+    H.root_step(plain, oracle.Params())
+    H.root_step(dual, oracle.Params(options=8))
+    for La, Lb in zip(plain, dual):
+        for pa, pb in zip(La["patches"], Lb["patches"]):
+            for f in range(5):
+                assert np.array_equal(pa["U"][f], pb["U"][f])
+
+
+@pytest.mark.slow
+def test_dual_gas_energy_follows_the_density_through_rebuilds():
+    """The cold-contact pin with the hierarchy rebuilt after every root step
+    (new grids interpolated by SecondOrderA, then copied from the old ones):
+    ge = eps rho stays bit-exact and the grids change."""
+    layout = synth.hierarchy_layout(16, [(4, 12)], [4, 8], seed=1)
+    levels = H.make_levels(layout, synth.cold_contact_fields(layout, 16, gamma=G_COLD, eps=EPS_COLD), 1.0 / 16)
+    rb = {"gamma": G_COLD, "crit": {"slope": 0.05, "shock_dp": 0.33, "shock_e": 0.1},
+          "clus": {"efficiency": 0.3, "small_cells": 8, "buffer": 1}}
+    before = [p["origin"] for p in levels[1]["patches"]]
+    for _ in range(2):
+        H.root_step(levels, oracle.Params(gamma=G_COLD, options=8), rebuild=rb)
+    assert [p["origin"] for p in levels[1]["patches"]] != before and levels[1]["patches"]
+    assert _ge_deviation(levels) == 0.0
