@@ -92,13 +92,16 @@ typedef struct {
                            freg buffer, or -1.  FP64 sweeps store the final flux of every face
                            (FP32 sweeps the increment dt/dx F the cells applied, in FP64)
                            bounding an active cell: for axis d (x, y, z in order) a block
-                           of (n_d+1) n_a1 n_a2 x 5 doubles at
-                           ((j2 n_a1 + j1)(n_d+1) + f) 5 + v, a1 < a2 the other axes, f the
-                           face left of active cell f, v = rho, m_normal, m_a1, m_a2, E. */
+                           of (n_d+1) n_a1 n_a2 x C doubles at
+                           ((j2 n_a1 + j1)(n_d+1) + f) C + v, a1 < a2 the other axes, f the
+                           face left of active cell f, v = rho, m_normal, m_a1, m_a2, E.
+                           C = 5, or 6 when the batch has a gas-energy field (ge): v = 5
+                           is then the gas-energy flux (ENZO_OPT_DUAL, whose sweeps alone
+                           may write such registers). */
     int64_t freg_bnd;   /* offset of the boundary-face register, or -1: sweeps ADD dt x flux
                            (FP32 sweeps: the applied increment)
                            of the two faces bounding the patch along d, block of 2 n_a1 n_a2
-                           x 5 doubles per axis at ((j2 n_a1 + j1) 2 + side) 5 + v.  Used by
+                           x C doubles per axis at ((j2 n_a1 + j1) 2 + side) C + v.  Used by
                            flux correction (Sec. 3.4); the caller zeroes it before a
                            parent step's subcycles. */
 } enzo_patch;
@@ -143,8 +146,11 @@ enum { ENZO_SOLVER_TWOSHOCK = 0, ENZO_SOLVER_HLL = 1, ENZO_SOLVER_HLLC = 2 };
  * eps, the mean zone velocity).  A zone takes its pressure from ge where
  * E - KE < 1e-3 E (eta1), decided in FP64 in both precisions; after the update
  * ge is reset to E - KE where that exceeds 0.1 (eta2) times the largest E of the
- * cell and its two neighbours along the sweep.  Needs the two-shock solver, a
- * non-NULL ge and no flux registers (ENZO_ERR_ARG otherwise). */
+ * cell and its two neighbours along the sweep.  Needs the two-shock solver and
+ * a non-NULL ge (ENZO_ERR_ARG otherwise).  Flux registers then get the
+ * gas-energy flux as a sixth component per face; conversely a batch with
+ * both ge and flux registers must be swept with this option (ENZO_ERR_ARG
+ * otherwise). */
 enum { ENZO_OPT_STEEPEN = 1, ENZO_OPT_FLATTEN = 2, ENZO_OPT_DIFFUSE = 4, ENZO_OPT_DUAL = 8 };
 
 /* Method parameters (Sec. 4.1, 4.1.2, 9). */
@@ -372,10 +378,16 @@ typedef struct {        /* (part of) a face of a fine patch on the boundary of t
  * sibling copies.  parent_old and parent_new share the parent level's
  * descriptors (parent_new->patches) and differ in U.  precision ENZO_FP64: the
  * interpolation arithmetic in FP64; ENZO_FP32: in FP32 (for the FP32 path,
- * whose reconstruction reads the ghosts in FP32).  Refinement factor r = 2. */
+ * whose reconstruction reads the ghosts in FP32).  Refinement factor r = 2.
+ * Gas energy (dual energy, Sec. 4.1.1): when fine->ge is non-NULL it is a sixth
+ * field, interpolated and copied like the others; parent_new->ge and
+ * parent_old_ge (DEVICE, the parent's ge at the start of its step) must then
+ * be non-NULL too, and both NULL when fine->ge is (ENZO_ERR_ARG otherwise;
+ * parent_old_ge is not read when ninterp is 0). */
 int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *fine_links,
                           const enzo_patch_batch *parent_new, const enzo_patch_link *parent_links,
-                          double *const parent_old_U[5], double w, const enzo_copy_box *interp_boxes,
+                          double *const parent_old_U[5], const double *parent_old_ge, double w,
+                          const enzo_copy_box *interp_boxes,
                           int32_t ninterp, const enzo_copy_box *copy_boxes, int32_t ncopy, int32_t precision,
                           int32_t r);
 
@@ -388,7 +400,10 @@ int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *f
  * (dt/dx F), and the correction is G_coarse - mean(fine sums) / r.  Parts listed
  * in one call must not share a coarse cell (the additions are unordered); a
  * caller with parts that do (concave corners of the refined region) splits
- * them over calls in the order the additions should happen. */
+ * them over calls in the order the additions should happen.  When the batches
+ * carry gas energy (coarse->ge and fine->ge both non-NULL; one alone is
+ * ENZO_ERR_ARG) the registers have six components and ge is corrected with
+ * the sixth, its advected flux. */
 int enzo_flux_correct(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_links,
                       const enzo_patch_batch *fine, const enzo_patch_link *fine_links,
                       const enzo_fc_face *faces, int32_t nface, double dt_coarse, int32_t r,
@@ -396,7 +411,8 @@ int enzo_flux_correct(const enzo_patch_batch *coarse, const enzo_patch_link *coa
 
 /* Copy between two batches of one level (a rebuild, Sec. 3.5): the cells of
  * each box (global cells at the level, hi exclusive) go from src patch
- * boxes[i].src of `src` to dst patch boxes[i].dst of `dst`, all five fields.
+ * boxes[i].src of `src` to dst patch boxes[i].dst of `dst`, all five fields
+ * (six when both batches carry gas energy; one alone is ENZO_ERR_ARG).
  * Boxes must lie in the source patch's active cells and in the destination
  * patch's stored block; boxes with the same destination must not overlap.
  * Runs on dst->stream.  ENZO_ERR_ARG on NULL arguments or nbox < 0. */
@@ -460,7 +476,8 @@ int enzo_cluster_flags(const uint8_t *flags, const int32_t n[3], const enzo_clus
                        enzo_box *boxes, int32_t cap, int32_t *nbox);
 
 /* Projection (Sec. 3.3): every coarse cell covered by a fine patch becomes the
- * mean of its r^3 fine cells (r = 2). */
+ * mean of its r^3 fine cells (r = 2), in every field, the gas energy too when
+ * both batches carry it (one alone is ENZO_ERR_ARG). */
 int enzo_project(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_links,
                  const enzo_patch_batch *fine, const enzo_patch_link *fine_links, int32_t r);
 

@@ -269,7 +269,10 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
                       int cover, const MethodParams &m, int precision, int tile_pencils, float *log = nullptr,
                       unsigned long long *log_count = nullptr, long long log_cap = 0, int log_stride = 0)
 {
-    if ((m.options & ENZO_OPT_DUAL) && (!b->ge || b->freg)) return ENZO_ERR_ARG;
+    if ((m.options & ENZO_OPT_DUAL) && !b->ge) return ENZO_ERR_ARG;
+    // flux registers of a batch with a gas-energy field hold six components
+    // per face, which only the dual-energy sweep writes
+    if (b->freg && b->ge && !(m.options & ENZO_OPT_DUAL)) return ENZO_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
     int tile = tile_pencils > 0 ? tile_pencils : kSweepThreads;
     if (precision == ENZO_FP64 || m.guess == ENZO_GUESS_MLP || b->freg || m.options || m.fallback == 2)
@@ -485,7 +488,8 @@ static int step_impl(const enzo_patch_batch *b, const enzo_params *p, int32_t st
     if (bc && !bc_ok(bc)) return ENZO_ERR_ARG;
     if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
     if (b->npatch == 0) return ENZO_OK;
-    if ((m.options & ENZO_OPT_DUAL) && (!b->ge || b->freg)) return ENZO_ERR_ARG;
+    if ((m.options & ENZO_OPT_DUAL) && !b->ge) return ENZO_ERR_ARG;
+    if (b->freg && b->ge && !(m.options & ENZO_OPT_DUAL)) return ENZO_ERR_ARG;
     r = bc ? boundary_impl(b, bc) : fill_impl(b);
     if (r) return r;
     const int order[2][3] = {{0, 1, 2}, {2, 1, 0}};

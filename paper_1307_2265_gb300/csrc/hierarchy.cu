@@ -2,6 +2,7 @@
 //   ghost fill of refined levels (parent interpolation by SecondOrderA,
 //   Appendix A, after linear interpolation in time; then sibling copies),
 //   flux correction at coarse-fine faces (Sec. 3.4) and projection (Sec. 3.3).
+//   With dual energy (Sec. 4.1.1) the gas energy is a sixth field of each.
 // FP64 throughout; built with --fmad=false so every operation rounds once in
 // the order written.
 #include <cstdint>
@@ -111,14 +112,19 @@ template <> __device__ __forceinline__ float from_d<float>(double x) { return h_
 
 __device__ __forceinline__ int floordiv2(int g) { return g >= 0 ? g / 2 : -((1 - g) / 2); }
 
+// Fields carried by the hierarchy operations: the five conserved ones, and the
+// gas energy as a sixth when the batches have it (dual energy, Sec. 4.1.1).
+constexpr int kMaxFields = 6;
+
 struct InterpArgs {
     const enzo_patch *fine;
     const enzo_patch_link *flink;
-    double *U[5];
+    double *U[kMaxFields];
     const enzo_patch *par;
     const enzo_patch_link *plink;
-    const double *Pn[5];
-    const double *Po[5];
+    const double *Pn[kMaxFields];
+    const double *Po[kMaxFields];
+    int nf;
     double w;
     const enzo_copy_box *boxes;   // ghost regions no sibling covers (src unused)
     int nbox;
@@ -155,7 +161,7 @@ __global__ void __launch_bounds__(128) interp_ghosts_kernel(const __grid_constan
             const int64_t dst = P.off + (g[0] - L.origin[0] + P.ng) +
                                 (int64_t)N0 * ((g[1] - L.origin[1] + P.ng) + (int64_t)N1 * (g[2] - L.origin[2] + P.ng));
             const int64_t base = PP.off + (ps[0] - 1) + (int64_t)M0 * ((ps[1] - 1) + (int64_t)M1 * (ps[2] - 1));
-            for (int f = 0; f < 5; ++f) {
+            for (int f = 0; f < a.nf; ++f) {
                 T Q[3][3][3];
 #pragma unroll
                 for (int dz = 0; dz < 3; ++dz)
@@ -183,8 +189,9 @@ __global__ void __launch_bounds__(128) interp_ghosts_kernel(const __grid_constan
 struct CopyArgs {
     const enzo_patch *dpt, *spt;
     const enzo_patch_link *dlk, *slk;
-    double *D[5];
-    const double *S[5];
+    double *D[kMaxFields];
+    const double *S[kMaxFields];
+    int nf;
     const enzo_copy_box *boxes;
     int nbox;
 };
@@ -206,7 +213,7 @@ __global__ void __launch_bounds__(128) copy_boxes_kernel(const __grid_constant__
                               (int64_t)S01 * (B.lo[2] - SL.origin[2] + S.ng);
         for (int c0 = 0; c0 < vol; c0 += 2 * blockDim.x) {
             int64_t di[2], si[2];
-            double v[2][5];
+            double v[2][kMaxFields];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int c = c0 + threadIdx.x + k * blockDim.x;
@@ -216,13 +223,15 @@ __global__ void __launch_bounds__(128) copy_boxes_kernel(const __grid_constant__
                 si[k] = sbase + x + (int64_t)S0 * y + (int64_t)S01 * z;
                 if (c < vol)
 #pragma unroll
-                    for (int f = 0; f < 5; ++f) v[k][f] = a.S[f][si[k]];
+                    for (int f = 0; f < kMaxFields; ++f)
+                        if (f < a.nf) v[k][f] = a.S[f][si[k]];
             }
 #pragma unroll
             for (int k = 0; k < 2; ++k)
                 if (di[k] >= 0)
 #pragma unroll
-                    for (int f = 0; f < 5; ++f) a.D[f][di[k]] = v[k][f];
+                    for (int f = 0; f < kMaxFields; ++f)
+                        if (f < a.nf) a.D[f][di[k]] = v[k][f];
         }
     }
 }
@@ -230,7 +239,8 @@ __global__ void __launch_bounds__(128) copy_boxes_kernel(const __grid_constant__
 struct FcArgs {
     const enzo_patch *cp;
     const enzo_patch_link *cl;
-    double *U[5];
+    double *U[kMaxFields];
+    int nc;                   // register components per face (5, 6 with gas energy)
     const double *cfreg;
     const enzo_patch *fp;
     const enzo_patch_link *fl;
@@ -241,21 +251,21 @@ struct FcArgs {
     int increments;
 };
 
-__device__ __forceinline__ int64_t reg_all_block(const enzo_patch &P, int dir)
+__device__ __forceinline__ int64_t reg_all_block(const enzo_patch &P, int dir, int nc)
 {
     int64_t o = 0;
     for (int d = 0; d < dir; ++d) {
         const int b1 = d == 0 ? 1 : 0, b2 = d == 2 ? 1 : 2;
-        o += (int64_t)(P.n[d] + 1) * P.n[b1] * P.n[b2] * 5;
+        o += (int64_t)(P.n[d] + 1) * P.n[b1] * P.n[b2] * nc;
     }
     return o;
 }
-__device__ __forceinline__ int64_t reg_bnd_block(const enzo_patch &P, int dir)
+__device__ __forceinline__ int64_t reg_bnd_block(const enzo_patch &P, int dir, int nc)
 {
     int64_t o = 0;
     for (int d = 0; d < dir; ++d) {
         const int b1 = d == 0 ? 1 : 0, b2 = d == 2 ? 1 : 2;
-        o += (int64_t)2 * P.n[b1] * P.n[b2] * 5;
+        o += (int64_t)2 * P.n[b1] * P.n[b2] * nc;
     }
     return o;
 }
@@ -276,22 +286,23 @@ __global__ void __launch_bounds__(128) flux_correct_kernel(const __grid_constant
         const int cell = F.side ? X : X - 1;
         const int fc = X - PL.origin[d];
         const int e1 = F.hi[0] - F.lo[0], e2 = F.hi[1] - F.lo[1];
-        const double *creg = a.cfreg + PP.freg_all + reg_all_block(PP, d);
-        const double *freg = a.ffreg + FP.freg_bnd + reg_bnd_block(FP, d);
+        const int nc = a.nc;
+        const double *creg = a.cfreg + PP.freg_all + reg_all_block(PP, d, nc);
+        const double *freg = a.ffreg + FP.freg_bnd + reg_bnd_block(FP, d, nc);
         const int fna1 = FP.n[a1];
         const int T0 = TP.n[0] + 2 * TP.ng, T1 = TP.n[1] + 2 * TP.ng;
-        // fields in pencil order (rho, m_n, m_t1, m_t2, E)
-        double *const Uf[5] = {a.U[0], d == 0 ? a.U[1] : (d == 1 ? a.U[2] : a.U[3]),
-                               a1 == 0 ? a.U[1] : a.U[2], a2 == 1 ? a.U[2] : a.U[3], a.U[4]};
+        // fields in pencil order (rho, m_n, m_t1, m_t2, E, then the gas energy)
+        double *const Uf[kMaxFields] = {a.U[0], d == 0 ? a.U[1] : (d == 1 ? a.U[2] : a.U[3]),
+                                        a1 == 0 ? a.U[1] : a.U[2], a2 == 1 ? a.U[2] : a.U[3], a.U[4], a.U[5]};
         for (int q = threadIdx.x; q < e1 * e2; q += blockDim.x) {
             const int q1 = F.lo[0] + q % e1, q2 = F.lo[1] + q / e1;
             const int c1 = FL.origin[a1] / 2 + q1, c2 = FL.origin[a2] / 2 + q2;
             const double *cf = creg + (((int64_t)(c2 - PL.origin[a2]) * PP.n[a1] + (c1 - PL.origin[a1])) *
-                                           (PP.n[d] + 1) + fc) * 5;
-            const double *f00 = freg + (((int64_t)(2 * q2) * fna1 + 2 * q1) * 2 + F.side) * 5;
-            const double *f01 = freg + (((int64_t)(2 * q2) * fna1 + 2 * q1 + 1) * 2 + F.side) * 5;
-            const double *f10 = freg + (((int64_t)(2 * q2 + 1) * fna1 + 2 * q1) * 2 + F.side) * 5;
-            const double *f11 = freg + (((int64_t)(2 * q2 + 1) * fna1 + 2 * q1 + 1) * 2 + F.side) * 5;
+                                           (PP.n[d] + 1) + fc) * nc;
+            const double *f00 = freg + (((int64_t)(2 * q2) * fna1 + 2 * q1) * 2 + F.side) * nc;
+            const double *f01 = freg + (((int64_t)(2 * q2) * fna1 + 2 * q1 + 1) * 2 + F.side) * nc;
+            const double *f10 = freg + (((int64_t)(2 * q2 + 1) * fna1 + 2 * q1) * 2 + F.side) * nc;
+            const double *f11 = freg + (((int64_t)(2 * q2 + 1) * fna1 + 2 * q1 + 1) * 2 + F.side) * nc;
             int g[3];
             g[d] = cell;
             g[a1] = c1;
@@ -299,7 +310,8 @@ __global__ void __launch_bounds__(128) flux_correct_kernel(const __grid_constant
             const int64_t idx = TP.off + (g[0] - TL.origin[0] + TP.ng) +
                                 (int64_t)T0 * ((g[1] - TL.origin[1] + TP.ng) + (int64_t)T1 * (g[2] - TL.origin[2] + TP.ng));
 #pragma unroll
-            for (int v = 0; v < 5; ++v) {
+            for (int v = 0; v < kMaxFields; ++v) {
+                if (v >= nc) break;
                 double delta;
                 if (a.increments) {
                     // registers hold applied increments (U units): the fine ones
@@ -318,10 +330,11 @@ __global__ void __launch_bounds__(128) flux_correct_kernel(const __grid_constant
 struct ProjArgs {
     const enzo_patch *cp;
     const enzo_patch_link *cl;
-    double *U[5];
+    double *U[kMaxFields];
     const enzo_patch *fp;
     const enzo_patch_link *fl;
-    const double *F[5];
+    const double *F[kMaxFields];
+    int nf;
     int nfine;
 };
 
@@ -343,19 +356,21 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Pr
             const int64_t pidx = PP.off + (FL.origin[0] / 2 + x - PL.origin[0] + PP.ng) +
                                  (int64_t)P0 * ((FL.origin[1] / 2 + y - PL.origin[1] + PP.ng) +
                                                 (int64_t)P1 * (FL.origin[2] / 2 + z - PL.origin[2] + PP.ng));
-            // all 40 loads before the five stores (coarse and fine fields are
-            // distinct arrays, but the compiler cannot know that)
-            double v[5][8];
+            // all loads (8 per field) before the stores (coarse and fine fields
+            // are distinct arrays, but the compiler cannot know that)
+            double v[kMaxFields][8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
                 const int64_t fidx = FP.off + (2 * x + kx + FP.ng) +
                                      (int64_t)F0 * ((2 * y + ky + FP.ng) + (int64_t)F1 * (2 * z + kz + FP.ng));
 #pragma unroll
-                for (int f = 0; f < 5; ++f) v[f][k] = a.F[f][fidx];
+                for (int f = 0; f < kMaxFields; ++f)
+                    if (f < a.nf) v[f][k] = a.F[f][fidx];
             }
 #pragma unroll
-            for (int f = 0; f < 5; ++f) {
+            for (int f = 0; f < kMaxFields; ++f) {
+                if (f >= a.nf) break;
                 double s = 0.0;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) s = s + v[f][k];
@@ -391,12 +406,18 @@ extern "C" {
 
 int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *fine_links,
                           const enzo_patch_batch *parent_new, const enzo_patch_link *parent_links,
-                          double *const parent_old_U[5], double w, const enzo_copy_box *interp_boxes,
-                          int32_t ninterp, const enzo_copy_box *copy_boxes, int32_t ncopy, int32_t precision,
-                          int32_t r)
+                          double *const parent_old_U[5], const double *parent_old_ge, double w,
+                          const enzo_copy_box *interp_boxes, int32_t ninterp, const enzo_copy_box *copy_boxes,
+                          int32_t ncopy, int32_t precision, int32_t r)
 {
     if (r != 2 || !batch_ok(fine) || !batch_ok(parent_new) || !fine_links || !parent_links || !parent_old_U)
         return ENZO_ERR_ARG;
+    // the gas energy goes with the level: fine, parent and the parent's old
+    // state all carry it or none does
+    const bool ge = fine->ge != nullptr;
+    if ((parent_new->ge != nullptr) != ge || (ge && ninterp > 0 && !parent_old_ge) || (!ge && parent_old_ge))
+        return ENZO_ERR_ARG;
+    const int nf = ge ? 6 : 5;
     if (!(w >= 0.0) || !(w <= 1.0) || ninterp < 0 || ncopy < 0 || (ninterp > 0 && !interp_boxes) ||
         (ncopy > 0 && !copy_boxes))
         return ENZO_ERR_ARG;
@@ -414,6 +435,10 @@ int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *f
             a.Pn[f] = parent_new->U[f];
             a.Po[f] = parent_old_U[f];
         }
+        a.U[5] = fine->ge;
+        a.Pn[5] = parent_new->ge;
+        a.Po[5] = parent_old_ge;
+        a.nf = nf;
         a.par = parent_new->patches;
         a.plink = parent_links;
         a.w = w;
@@ -435,6 +460,9 @@ int enzo_ghost_fill_level(const enzo_patch_batch *fine, const enzo_patch_link *f
             c.D[f] = fine->U[f];
             c.S[f] = fine->U[f];
         }
+        c.D[5] = fine->ge;
+        c.S[5] = fine->ge;
+        c.nf = nf;
         c.boxes = copy_boxes;
         c.nbox = ncopy;
         copy_boxes_kernel<<<ncopy, 128, 0, s>>>(c);
@@ -449,6 +477,7 @@ int enzo_copy_level(const enzo_patch_batch *dst, const enzo_patch_link *dst_link
 {
     if (!batch_ok(dst) || !batch_ok(src) || !dst_links || !src_links || nbox < 0 || (nbox > 0 && !boxes))
         return ENZO_ERR_ARG;
+    if ((dst->ge != nullptr) != (src->ge != nullptr)) return ENZO_ERR_ARG;
     if (nbox == 0) return ENZO_OK;
     CopyArgs c;
     c.dpt = dst->patches;
@@ -459,6 +488,9 @@ int enzo_copy_level(const enzo_patch_batch *dst, const enzo_patch_link *dst_link
         c.D[f] = dst->U[f];
         c.S[f] = src->U[f];
     }
+    c.D[5] = dst->ge;
+    c.S[5] = src->ge;
+    c.nf = dst->ge ? 6 : 5;
     c.boxes = boxes;
     c.nbox = nbox;
     copy_boxes_kernel<<<nbox < sm_count() * 16 ? nbox : sm_count() * 16, 128, 0,
@@ -473,12 +505,15 @@ int enzo_flux_correct(const enzo_patch_batch *coarse, const enzo_patch_link *coa
 {
     if (r != 2 || !batch_ok(coarse) || !batch_ok(fine) || !coarse_links || !fine_links) return ENZO_ERR_ARG;
     if (nface < 0 || (nface > 0 && !faces) || !(dt_coarse >= 0.0)) return ENZO_ERR_ARG;
+    if ((coarse->ge != nullptr) != (fine->ge != nullptr)) return ENZO_ERR_ARG;
     if (nface == 0) return ENZO_OK;
     if (!coarse->freg || !fine->freg) return ENZO_ERR_ARG;
     FcArgs a;
     a.cp = coarse->patches;
     a.cl = coarse_links;
     for (int f = 0; f < 5; ++f) a.U[f] = coarse->U[f];
+    a.U[5] = coarse->ge;
+    a.nc = coarse->ge ? 6 : 5;
     a.cfreg = coarse->freg;
     a.fp = fine->patches;
     a.fl = fine_links;
@@ -497,6 +532,7 @@ int enzo_project(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_l
                  const enzo_patch_link *fine_links, int32_t r)
 {
     if (r != 2 || !batch_ok(coarse) || !batch_ok(fine) || !coarse_links || !fine_links) return ENZO_ERR_ARG;
+    if ((coarse->ge != nullptr) != (fine->ge != nullptr)) return ENZO_ERR_ARG;
     if (fine->npatch == 0) return ENZO_OK;
     ProjArgs a;
     a.cp = coarse->patches;
@@ -505,6 +541,9 @@ int enzo_project(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_l
         a.U[f] = coarse->U[f];
         a.F[f] = fine->U[f];
     }
+    a.U[5] = coarse->ge;
+    a.F[5] = fine->ge;
+    a.nf = coarse->ge ? 6 : 5;
     a.fp = fine->patches;
     a.fl = fine_links;
     a.nfine = fine->npatch;

@@ -1070,15 +1070,21 @@ struct Marcher {
     // the flux F (all faces) and dt F summed over steps (boundary faces).  FP32
     // path: the increment G = dt/dx F exactly as the cells applied it, and its
     // sum, so a flux correction cancels the applied coarse increment exactly.
-    __device__ __forceinline__ void record(int f, const R Fv[5], const double G[5])
+    // With dual energy (EXT == 2) a face has a sixth entry, the gas-energy
+    // flux gF (FP32 path: its applied increment gG); the -p div v source is a
+    // zone term and has none.
+    static constexpr int NC = EXT == 2 ? 6 : 5;
+    __device__ __forceinline__ void record(int f, const R Fv[5], const double G[5], R gF = (R)0, double gG = 0.0)
     {
         if (!REG) return;
         if (reg_all) {
-            _Pragma("unroll") for (int v = 0; v < 5; ++v) reg_all[f * 5 + v] = sizeof(R) == 8 ? (double)Fv[v] : G[v];
+            _Pragma("unroll") for (int v = 0; v < 5; ++v) reg_all[f * NC + v] = sizeof(R) == 8 ? (double)Fv[v] : G[v];
+            if constexpr (EXT == 2) reg_all[f * NC + 5] = sizeof(R) == 8 ? (double)gF : gG;
         }
         if (reg_bnd && (f == 0 || f == pc.n)) {
-            double *o = reg_bnd + (f == 0 ? 0 : 5);
+            double *o = reg_bnd + (f == 0 ? 0 : NC);
             _Pragma("unroll") for (int v = 0; v < 5; ++v) o[v] = o[v] + (sizeof(R) == 8 ? dt64 * (double)Fv[v] : G[v]);
+            if constexpr (EXT == 2) o[5] = o[5] + (sizeof(R) == 8 ? dt64 * (double)gF : gG);
         }
     }
 
@@ -1328,7 +1334,9 @@ struct Marcher {
                             }
                             double G1[5];
                             widen(Fu1, dtdx, G1);
-                            record(kk - 6, Fu1, G1);
+                            if constexpr (REG && EXT == 2)
+                                record(kk - 6, Fu1, G1, gfin.F, sizeof(R) == 4 ? f2d_exact((float)(dtdx * gfin.F)) : 0.0);
+                            else record(kk - 6, Fu1, G1);
                             if (kk >= 7)
                                 update(kk - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt, dual ? &gfin2 : nullptr,
                                        &gfin, p4, dtdx);
@@ -1362,7 +1370,9 @@ struct Marcher {
         }
         double G1[5];
         widen(Fu1, dtdx, G1);
-        record(pc.n, Fu1, G1);
+        if constexpr (REG && EXT == 2)
+            record(pc.n, Fu1, G1, gfin.F, sizeof(R) == 4 ? f2d_exact((float)(dtdx * gfin.F)) : 0.0);
+        else record(pc.n, Fu1, G1);
         // the pressure of zone L-4 is the last window's zone k-3
         update(L - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt, dual ? &gfin2 : nullptr, &gfin, zm3.p, dtdx);
         if (dual) ge_commit(Eghost_right);
@@ -1630,15 +1640,17 @@ __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? (EXT 
             const int j1 = i1 - P.ng, j2 = i2 - P.ng;
             const int na1 = P.n[A1], na2 = P.n[A2];
             if (a.freg && valid && j1 >= 0 && j1 < na1 && j2 >= 0 && j2 < na2) {
+                // components per face: five, six with dual energy
+                constexpr int NC = EXT == 2 ? 6 : 5;
                 int64_t oall = 0, obnd = 0;
                 for (int d = 0; d < DIR; ++d) {
                     const int b1 = d == 0 ? 1 : 0, b2 = d == 2 ? 1 : 2;
-                    oall += (int64_t)(P.n[d] + 1) * P.n[b1] * P.n[b2] * 5;
-                    obnd += (int64_t)2 * P.n[b1] * P.n[b2] * 5;
+                    oall += (int64_t)(P.n[d] + 1) * P.n[b1] * P.n[b2] * NC;
+                    obnd += (int64_t)2 * P.n[b1] * P.n[b2] * NC;
                 }
                 const int64_t row = (int64_t)j2 * na1 + j1;
-                if (P.freg_all >= 0) reg_all = a.freg + P.freg_all + oall + row * (P.n[DIR] + 1) * 5;
-                if (P.freg_bnd >= 0) reg_bnd = a.freg + P.freg_bnd + obnd + row * 2 * 5;
+                if (P.freg_all >= 0) reg_all = a.freg + P.freg_all + oall + row * (P.n[DIR] + 1) * NC;
+                if (P.freg_bnd >= 0) reg_bnd = a.freg + P.freg_bnd + obnd + row * 2 * NC;
             }
         }
         if (P.flags & ENZO_PATCH_PERIODIC) {
@@ -1806,21 +1818,34 @@ template <class R>
 cudaError_t launch_sweep_dir(const SweepArgs &a, int grid, cudaStream_t s)
 {
     if (a.mp.options & ENZO_OPT_DUAL) {
-        // dual energy (never with flux registers) has its own instantiations
-        // too, so the option kernels without it keep their registers; their
-        // persistent grid follows their own occupancy
-        static int cached[64] = {0};
+        // dual energy has its own instantiations too (with and without flux
+        // registers), so the option kernels without it keep their registers;
+        // their persistent grid follows their own occupancy
+        static int cached[2][64] = {{0}};
         int dev = 0;
         cudaGetDevice(&dev);
         if (dev < 0 || dev >= 64) dev = 0;
-        if (!cached[dev]) {
+        const int withreg = a.freg ? 1 : 0;
+        if (!cached[withreg][dev]) {
             int sms = 0, per = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<R, 0, false, kSweepThreads, false, 2>,
-                                                          kSweepThreads, 0);
-            cached[dev] = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+            if (withreg)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per, ppm_sweep_kernel<R, 0, false, kSweepThreads, true, 2>, kSweepThreads, 0);
+            else
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per, ppm_sweep_kernel<R, 0, false, kSweepThreads, false, 2>, kSweepThreads, 0);
+            cached[withreg][dev] = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
         }
-        grid = cached[dev];
+        grid = cached[withreg][dev];
+        if (a.freg) {
+            switch (a.dir) {
+            case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, true, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
+            case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, true, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
+            default: ppm_sweep_kernel<R, 2, false, kSweepThreads, true, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
+            }
+            return cudaGetLastError();
+        }
         switch (a.dir) {
         case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, false, 2><<<grid, kSweepThreads, 0, s>>>(a); break;
         case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, false, 2><<<grid, kSweepThreads, 0, s>>>(a); break;

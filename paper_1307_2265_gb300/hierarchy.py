@@ -56,7 +56,7 @@ def _lib():
     L = lib()
     if not getattr(L, "_hier_ready", False):
         vp, i32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
-        L.enzo_ghost_fill_level.argtypes = [vp, vp, vp, vp, vp, d, vp, i32, vp, i32, i32, i32]
+        L.enzo_ghost_fill_level.argtypes = [vp, vp, vp, vp, vp, vp, d, vp, i32, vp, i32, i32, i32]
         L.enzo_flux_correct.argtypes = [vp, vp, vp, vp, vp, i32, d, i32, i32]
         L.enzo_project.argtypes = [vp, vp, vp, vp, i32]
         L.enzo_copy_level.argtypes = [vp, vp, vp, vp, vp, i32]
@@ -327,12 +327,13 @@ def flag_cells(batch, gamma, slope=0.3, shock_dp=0.33, shock_e=0.1, mass=0.0):
             for i in range(len(cells))]
 
 
-def register_sizes(n):
-    """(all-face, boundary-face) register sizes in doubles of patches of sizes n."""
+def register_sizes(n, nc=5):
+    """(all-face, boundary-face) register sizes in doubles of patches of sizes n,
+    nc components per face (5, or 6 with the dual-energy gas energy)."""
     n = np.asarray(n, dtype=np.int64)
     nx, ny, nz = n[:, 0], n[:, 1], n[:, 2]
-    all_f = ((nx + 1) * ny * nz + (ny + 1) * nx * nz + (nz + 1) * nx * ny) * 5
-    bnd = 2 * (ny * nz + nx * nz + nx * ny) * 5
+    all_f = ((nx + 1) * ny * nz + (ny + 1) * nx * nz + (nz + 1) * nx * ny) * nc
+    bnd = 2 * (ny * nz + nx * nz + nx * ny) * nc
     return all_f, bnd
 
 
@@ -342,9 +343,13 @@ class Hierarchy:
     3.6)."""
 
     def __init__(self, layout, fields, root_dx, device="cuda", stream=None, root_bc=None):
-        """root_bc: external boundaries (bc_x, bc_y, bc_z) of the root grid
-        (BC_PERIODIC, BC_REFLECT, BC_OUTFLOW; its ghosts are then filled before
-        each step), or None: a periodic root that wraps inside its sweeps."""
+        """fields: per level, per patch, the five ghost-zoned fields, or six with
+        the gas energy of the dual-energy option (Sec. 4.1.1; every patch then
+        carries it, it goes through every hierarchy operation, and the level
+        sweeps need OPT_DUAL).  root_bc: external boundaries (bc_x, bc_y, bc_z)
+        of the root grid (BC_PERIODIC, BC_REFLECT, BC_OUTFLOW; its ghosts are
+        then filled before each step), or None: a periodic root that wraps
+        inside its sweeps."""
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -352,6 +357,9 @@ class Hierarchy:
         self.root_dx = root_dx
         self.root_bc = None if root_bc is None else tuple(int(v) for v in root_bc)
         self.levels = []
+        self.nf = len(fields[0][0])
+        if self.nf not in (5, 6):
+            raise ValueError("a patch has five fields, or six with the gas energy")
         nlev = len(layout)
         if nlev > 1:
             self._check_root_margin(np.asarray(layout[0]["n"][0]), np.asarray(layout[1]["origin"]),
@@ -360,9 +368,9 @@ class Hierarchy:
             n = np.asarray(L["n"], dtype=np.int64)
             vols = np.prod(n + 2 * NG, axis=1)
             offs = np.concatenate([[0], np.cumsum(vols)[:-1]]).astype(np.int64)
-            flat = [np.zeros(int(vols.sum())) for _ in range(5)]
+            flat = [np.zeros(int(vols.sum())) for _ in range(self.nf)]
             for i in range(len(n)):
-                for f in range(5):
+                for f in range(self.nf):
                     blk = np.asarray(fields[l][i][f])
                     flat[f][offs[i]:offs[i] + blk.size] = blk.ravel()
             self.levels.append(self._build_level(l, n, np.asarray(L["origin"]), np.asarray(L["parent"]), flat,
@@ -384,8 +392,9 @@ class Hierarchy:
             raise ValueError("level 1 must stay 3 root cells away from the domain boundary")
 
     def _build_level(self, l, n, origin, parent, flat, has_children, general, state=None):
-        """Device state of level l from its layout; flat: five flat host
-        fields, or None for zeros.  state: time bookkeeping to keep."""
+        """Device state of level l from its layout; flat: the five (six with
+        gas energy) flat host fields, or None for zeros.  state: time
+        bookkeeping to keep."""
         torch = self.torch
         n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
         vols = np.prod(n + 2 * NG, axis=1)
@@ -394,7 +403,7 @@ class Hierarchy:
         wrap = l == 0 and self.root_bc is None
         table = patch_table(n, offs, [dx] * 3, flags=PATCH_PERIODIC if wrap else 0, level=l)
         has_parent = l > 0
-        a_sz, b_sz = register_sizes(n)
+        a_sz, b_sz = register_sizes(n, self.nf)
         reg = 0
         if has_children:
             table["freg_all"] = np.concatenate([[0], np.cumsum(a_sz)[:-1]]) + reg
@@ -403,9 +412,11 @@ class Hierarchy:
             table["freg_bnd"] = np.concatenate([[0], np.cumsum(b_sz)[:-1]]) + reg
             reg += int(b_sz.sum())
         if flat is None:
-            flat = [torch.zeros(max(int(vols.sum()), 1), dtype=torch.float64, device=self.device) for _ in range(5)]
+            flat = [torch.zeros(max(int(vols.sum()), 1), dtype=torch.float64, device=self.device)
+                    for _ in range(self.nf)]
         with torch.cuda.stream(self.stream):
-            batch = PatchBatch(table, flat, device=self.device, stream=self.stream)
+            batch = PatchBatch(table, flat[:5], device=self.device, stream=self.stream,
+                               ge=flat[5] if self.nf == 6 else None)
         if reg:
             batch.freg = torch.zeros(reg, dtype=torch.float64, device=self.device)
         links = np.zeros(len(n), dtype=LINK_DTYPE)
@@ -427,8 +438,12 @@ class Hierarchy:
             lo = int(table["freg_bnd"].min()) if len(n) else 0
             lev["bnd_sl"] = (lo, lo + int(b_sz.sum()))
         if has_children:
-            lev["old"] = [torch.empty_like(u) for u in batch.U]
+            lev["old"] = [torch.empty_like(u) for u in self._fields(batch)]
         return lev
+
+    def _fields(self, batch):
+        """The fields a hierarchy operation carries: U, and ge with dual energy."""
+        return list(batch.U) + ([batch.ge] if self.nf == 6 else [])
 
     def _plan_correction(self, l, general):
         """Flux-correction parts of level l (coarse) against level l + 1, as
@@ -477,9 +492,10 @@ class Hierarchy:
         par = self.levels[l - 1]
         w = (lev["t"] - par["t_old"]) / (par["t"] - par["t_old"])
         b, pb = lev["batch"].c(), par["batch"].c()
-        old = (ctypes.c_void_p * 5)(*[u.data_ptr() for u in par["old"]])
+        old = (ctypes.c_void_p * 5)(*[u.data_ptr() for u in par["old"][:5]])
+        old_ge = par["old"][5].data_ptr() if self.nf == 6 else None
         _check(_lib().enzo_ghost_fill_level(ctypes.byref(b), lev["links"].data_ptr(), ctypes.byref(pb),
-                                            par["links"].data_ptr(), old, w, lev["ibox"].data_ptr(),
+                                            par["links"].data_ptr(), old, old_ge, w, lev["ibox"].data_ptr(),
                                             lev["nibox"], lev["boxes"].data_ptr(), lev["nbox"], precision, 2),
                "enzo_ghost_fill_level")
 
@@ -555,8 +571,10 @@ class Hierarchy:
             fb = _to_dev(full, self.device)
             nb, pb = new["batch"].c(), lev["batch"].c()
             cur = (ctypes.c_void_p * 5)(*[u.data_ptr() for u in lev["batch"].U])
+            cur_ge = lev["batch"].ge.data_ptr() if self.nf == 6 else None
             _check(L.enzo_ghost_fill_level(ctypes.byref(nb), new["links"].data_ptr(), ctypes.byref(pb),
-                                           lev["links"].data_ptr(), cur, 0.0, fb.data_ptr(), len(full), None, 0,
+                                           lev["links"].data_ptr(), cur, cur_ge, 0.0, fb.data_ptr(), len(full),
+                                           None, 0,
                                            precision, 2), "enzo_ghost_fill_level")
             # cells of the new patches (ghosts included) lying in an old patch
             olo, ohi = old["origin"], old["origin"] + old["n"]
@@ -598,7 +616,7 @@ class Hierarchy:
                     self._end(m)
                 if lev["has_children"]:
                     m = self._mark("save_old")
-                    for u, o in zip(lev["batch"].U, lev["old"]):
+                    for u, o in zip(self._fields(lev["batch"]), lev["old"]):
                         o.copy_(u)
                     self._end(m)
                     lev["t_old"] = lev["t"]
@@ -638,4 +656,8 @@ class Hierarchy:
         return dt0
 
     def patch_fields(self, l, i):
-        return [f.cpu().numpy() for f in self.levels[l]["batch"].patch_fields(i)]
+        """Host copies of patch i of level l: the five fields, and the gas
+        energy as a sixth with dual energy."""
+        b = self.levels[l]["batch"]
+        views = b.patch_fields(i) + ([b.patch_ge(i)] if self.nf == 6 else [])
+        return [f.cpu().numpy() for f in views]

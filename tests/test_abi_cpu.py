@@ -121,9 +121,10 @@ def test_reconstruction_options_rejected_without_gpu():
 
 
 def test_dual_energy_arguments_rejected_without_gpu():
-    """OPT_DUAL needs the two-shock solver, a gas-energy field and no flux
-    registers; each is refused on the host before any launch (the fake device
-    pointers below are never dereferenced)."""
+    """OPT_DUAL needs the two-shock solver and a gas-energy field, and a batch
+    with both a gas-energy field and flux registers (six components per face)
+    needs OPT_DUAL; each is refused on the host before any launch (the fake
+    device pointers below are never dereferenced)."""
     L = ez.lib()
     b = ez._Batch()
     b.npatch = 0
@@ -143,7 +144,9 @@ def test_dual_energy_arguments_rejected_without_gpu():
     assert L.enzo_step(ctypes.byref(b), ctypes.byref(dual.c()), 0, ctypes.c_void_p(262144)) == -1
     b.ge = 524288
     b.freg = 1048576
-    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(dual.c())) == -1      # with registers
+    plain = ez.Params()
+    assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(plain.c())) == -1     # registers, no option
+    assert L.enzo_step(ctypes.byref(b), ctypes.byref(plain.c()), 0, ctypes.c_void_p(262144)) == -1
     assert L.enzo_ppm_sweep_noalloc(ctypes.byref(b), 0, 0.1, 0,
                                     ctypes.byref(ez.Params(options=ez.OPT_DUAL, solver=ez.SOLVER_HLL).c())) == -1
 
@@ -158,3 +161,40 @@ def test_fallback_modes_rejected_without_gpu():
         assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(ez.Params(fallback=mode).c())) == want
     p = ez.Params(precision=ez.FP32, guess=ez.GUESS_MLP, mlp=4096, fallback=2).c()
     assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -1
+
+
+def _fake_batch(ge):
+    """A one-patch batch of fake device pointers (never dereferenced)."""
+    b = ez._Batch()
+    b.npatch = 1
+    b.patches = 4096
+    b.field_len = 1000
+    for i in range(5):
+        b.U[i] = 8192 + 8192 * i
+    b.freg = 1048576
+    b.ge = 524288 if ge else None
+    return b
+
+
+def test_hierarchy_gas_energy_pairing_rejected_without_gpu():
+    """The hierarchy calls carry the gas energy only when every batch involved
+    has it: a coarse/fine (or source/destination) pair where one side alone
+    has ge, or a ghost fill of a level with ge whose parent's old ge is
+    missing, is refused on the host before any launch."""
+    from paper_1307_2265_gb300 import hierarchy as gh
+    L = gh._lib()
+    a, n = _fake_batch(True), _fake_batch(False)
+    links, boxes = ctypes.c_void_p(2048), ctypes.c_void_p(3072)
+    old = (ctypes.c_void_p * 5)(*[16384 + 8192 * i for i in range(5)])
+    for x, y in ((a, n), (n, a)):
+        assert L.enzo_flux_correct(ctypes.byref(x), links, ctypes.byref(y), links, boxes, 1, 0.1, 2, 0) == -1
+        assert L.enzo_project(ctypes.byref(x), links, ctypes.byref(y), links, 2) == -1
+        assert L.enzo_copy_level(ctypes.byref(x), links, ctypes.byref(y), links, boxes, 1) == -1
+        assert L.enzo_ghost_fill_level(ctypes.byref(x), links, ctypes.byref(y), links, old, 32768, 0.5,
+                                       boxes, 1, None, 0, 0, 2) == -1
+    # ge on both levels, but no old ge of the parent for the interpolation
+    assert L.enzo_ghost_fill_level(ctypes.byref(a), links, ctypes.byref(a), links, old, None, 0.5,
+                                   boxes, 1, None, 0, 0, 2) == -1
+    # no ge anywhere, yet an old ge given
+    assert L.enzo_ghost_fill_level(ctypes.byref(n), links, ctypes.byref(n), links, old, 32768, 0.5,
+                                   boxes, 1, None, 0, 0, 2) == -1

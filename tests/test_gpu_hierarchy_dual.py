@@ -1,0 +1,152 @@
+"""Dual energy (Sec. 4.1.1) through the hierarchy (Sec. 3) on the GPU: the gas
+energy is a sixth field of the ghost fill, the sibling copies, the flux
+registers and correction, the projection and the rebuild.
+- FP64: root steps of a three-level static hierarchy, and of a dynamic one
+  rebuilt after every step, give the oracle's six fields bit for bit; the
+  state has cold cells (pressure from the gas energy) and a gas energy out of
+  step with E - KE (resynchronised where warm).
+- FP32: in the cold contact (uniform pressure and velocity, Mach 6.7 to 11.6,
+  ge = 2 rho) ge / rho stays 2 to the FP32 rounding of the -p div v source
+  and the five conserved composite totals are kept."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1307_2265_gb300 as ez
+from oracle import hierarchy as H
+from paper_1307_2265_gb300 import hierarchy as gh
+from paper_1307_2265_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _with_gas_energy(layout, fields, root_n):
+    """Five-field hierarchy fields plus a gas energy: the internal energy of
+    cells with global x in [0.55, 0.8) (root units) is cut to 1e-5 of itself
+    (E - KE < 1e-3 E there: cold), and ge = (E - KE) (1 + 0.2 sin(2 pi (x + 2 y)))."""
+    out = []
+    for l, (L, lev) in enumerate(zip(layout, fields)):
+        dx = 1.0 / (root_n * 2 ** l)
+        per = []
+        for i, U in enumerate(lev):
+            V = [f.copy() for f in U]
+            nx, ny, nz = (int(v) for v in L["n"][i])
+            o = L["origin"][i]
+            A = [H._active(f) for f in V]
+            x = (o[0] + np.arange(nx) + 0.5) * dx
+            y = (o[1] + np.arange(ny) + 0.5) * dx
+            ke = 0.5 * ((A[1] ** 2 + A[2] ** 2) + A[3] ** 2) / A[0]
+            cold = ((x >= 0.55) & (x < 0.8))[None, None, :]
+            e = np.where(cold, 1e-5, 1.0) * (A[4] - ke)
+            A[4][...] = ke + e
+            wave = 1.0 + 0.2 * np.sin(2 * math.pi * (x[None, None, :] + 2 * y[None, :, None]))
+            V.append(synth.embed(e * wave))
+            per.append(V)
+        out.append(per)
+    return out
+
+
+def _assert_same(ref, hier):
+    hier.stream.synchronize()
+    for l, L in enumerate(ref):
+        assert len(hier.levels[l]["n"]) == len(L["patches"]), l
+        for i, p in enumerate(L["patches"]):
+            g = hier.patch_fields(l, i)
+            assert len(g) == 6
+            for f, (a, b) in enumerate(zip(g, p["U"])):
+                assert np.array_equal(H._active(a), H._active(b)), (l, i, f)
+
+
+def test_fp64_dual_root_steps_match_the_oracle_bitwise():
+    layout = synth.hierarchy_layout(16, [(4, 12), (6, 10)], [4, 8], seed=1)
+    fields = _with_gas_energy(layout, synth.hierarchy_fields(layout, config=5), 16)
+    ref = H.make_levels(layout, fields, 1.0 / 16)
+    hier = gh.Hierarchy(layout, fields, 1.0 / 16)
+    P = oracle.Params(options=oracle.OPT_DUAL)
+    params = ez.Params(precision=ez.FP64, options=ez.OPT_DUAL)
+    for _ in range(2):
+        log_o, log_g = [], []
+        H.root_step(ref, P, log=log_o)
+        hier.root_step(params, log=log_g)
+        assert log_g == log_o
+        _assert_same(ref, hier)
+    # the cold cells took their pressure from the gas energy
+    assert sum(lev["batch"].read_status()["ge_pressure"] for lev in hier.levels) > 0
+
+
+def _shock_fields(N=48, M=2.0, x0=0.3, ny=8):
+    """Root N x ny x ny with a Mach-M shock (gamma 1.4) and one refined patch
+    around it, with the gas energy E - KE (in step)."""
+    g = 1.4
+    rho2 = (g + 1) * M * M / ((g - 1) * M * M + 2)
+    p2 = (2 * g * M * M - (g - 1)) / (g + 1)
+    u2 = M * math.sqrt(g) * (1 - 1 / rho2)
+
+    def state(n, origin, dx):
+        nx, nyy, nz = n
+        x = (origin[0] + np.arange(nx) + 0.5) * dx
+        post = np.broadcast_to(x < x0, (nz, nyy, nx))
+        z = np.zeros((nz, nyy, nx))
+        prims = (np.where(post, rho2, 1.0), np.where(post, u2, 0.0), z, z, np.where(post, p2, 1.0))
+        U = [synth.embed(f) for f in synth.prims_to_conserved(*prims, g)]
+        return U + [synth.embed(prims[4] / (g - 1))]
+
+    layout = [{"n": np.array([(N, ny, ny)]), "origin": np.zeros((1, 3), int), "parent": np.array([-1])}]
+    lo, hi = [int(x0 * N) - 4, 3, 3], [int(x0 * N) + 6, ny - 3, ny - 3]
+    n1 = tuple(2 * (hi[a] - lo[a]) for a in range(3))
+    o1 = tuple(2 * lo[a] for a in range(3))
+    layout.append({"n": np.array([n1]), "origin": np.array([o1]), "parent": np.array([0])})
+    return layout, [[state((N, ny, ny), (0, 0, 0), 1.0 / N)], [state(n1, o1, 0.5 / N)]], 1.0 / N, g
+
+
+def test_fp64_dual_dynamic_root_steps_match_the_oracle_bitwise():
+    layout, fields, dx, g = _shock_fields()
+    ref = H.make_levels(layout, fields, dx)
+    hier = gh.Hierarchy(layout, fields, dx)
+    P = oracle.Params(gamma=g, options=oracle.OPT_DUAL)
+    params = ez.Params(precision=ez.FP64, gamma=g, options=ez.OPT_DUAL)
+    cfl = ez.Params(precision=ez.FP64, gamma=g)
+    rb = {"gamma": g, "crit": {"slope": 0.3, "shock_dp": 0.33, "shock_e": 0.1},
+          "clus": {"efficiency": 0.3, "small_cells": 8, "buffer": 1}}
+    origins = {tuple(map(tuple, hier.levels[1]["origin"]))}
+    for _ in range(4):
+        log_o, log_g = [], []
+        H.root_step(ref, P, log=log_o, rebuild=rb)
+        hier.root_step(params, cfl, log=log_g, rebuild=rb)
+        assert log_g == log_o
+        _assert_same(ref, hier)
+        origins.add(tuple(map(tuple, hier.levels[1]["origin"])))
+    assert len(origins) > 1                        # a rebuild replaced the grids
+
+
+def test_fp32_dual_cold_contact_keeps_ge_with_rho():
+    layout = synth.hierarchy_layout(16, [(4, 12), (6, 10)], [4, 8], seed=1)
+    fields = synth.cold_contact_fields(layout, 16, gamma=1.4, eps=2.0)
+    hier = gh.Hierarchy(layout, fields, 1.0 / 16)
+    params = ez.Params(precision=ez.FP32, gamma=1.4, options=ez.OPT_DUAL)
+
+    def totals():
+        lv = [{"patches": [{"n": tuple(int(v) for v in lev["n"][i]),
+                            "origin": tuple(int(v) for v in lev["origin"][i]),
+                            "parent": int(lev["parent"][i]), "U": hier.patch_fields(l, i)[:5]}
+                           for i in range(len(lev["n"]))], "dx": lev["dx"]} for l, lev in enumerate(hier.levels)]
+        t = H.composite_totals(lv)
+        for L in lv:
+            for p in L["patches"]:
+                p["U"] = [np.abs(f) for f in p["U"]]
+        return t, H.composite_totals(lv)
+
+    t0, scale = totals()
+    for _ in range(3):
+        hier.root_step(params, ez.Params(precision=ez.FP32, gamma=1.4))
+    hier.stream.synchronize()
+    worst = 0.0
+    for l, lev in enumerate(hier.levels):
+        for i in range(len(lev["n"])):
+            U = hier.patch_fields(l, i)
+            worst = max(worst, float(np.max(np.abs(H._active(U[5]) / H._active(U[0]) - 2.0))))
+    assert worst < 1e-4, worst
+    t1, _ = totals()
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale.max()), (t1 - t0) / scale.max()
