@@ -423,13 +423,21 @@ def run_gpu(args, rank, world):
     return res
 
 
+def _internal_energy(A):
+    """E - KE of conserved active-cell arrays (rho, m_x, m_y, m_z, E)."""
+    return A[4] - 0.5 * ((A[1] * A[1] + A[2] * A[2]) + A[3] * A[3]) / A[0]
+
+
 def run_hierarchy(args, rank, world):
     """Full hierarchy: 256^3 periodic root and three nested levels refined by 2
     (central 192^3, 128^3 and 64^3 root cells; patches from guillotine cuts with
     per-axis sizes 16..32), white-noise initial state on the root inherited by
     the finer levels.  One root step is the subcycled W-cycle (level l takes
     about 2^l steps), with ghost fill from parents and siblings, flux
-    correction and projection.  Times one root step of each path."""
+    correction and projection.  Times one root step of each path: FP32 with
+    the learned guess, FP32 plain, FP32 with dual energy (the gas energy, E - KE
+    of the initial state, a sixth field of every hierarchy operation) and FP64
+    plain."""
     import torch
     import paper_1307_2265_gb300 as ez
     from paper_1307_2265_gb300 import hierarchy as gh
@@ -448,8 +456,17 @@ def run_hierarchy(args, rank, world):
     for name, params in (("fp32_learned", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, guess=ez.GUESS_MLP,
                                                     mlp=net.blob, mlp_gate=args.mlp_gate)),
                          ("fp32_plain", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32)),
+                         ("fp32_dual", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP32, options=ez.OPT_DUAL)),
                          ("fp64_plain", ez.Params(gamma=GAMMA, cfl=CFL, precision=ez.FP64))):
-        hier = gh.Hierarchy(layout, fields, 1.0 / args.root)
+        if name == "fp32_dual":
+            # the gas energy as a sixth field of every patch: E - KE of the initial state
+            ng = synth.NG
+            hf = [[U + [synth.embed(_internal_energy([f[ng:-ng, ng:-ng, ng:-ng] for f in U]))] for U in lev]
+                  for lev in fields]
+        else:
+            hf = fields
+        hier = gh.Hierarchy(layout, hf, 1.0 / args.root)
+        del hf
         hier.timing = {}
         cflp = ez.Params(gamma=GAMMA, cfl=CFL, precision=params.precision)
         torch.cuda.synchronize()
