@@ -251,6 +251,20 @@ int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, double dt, in
  * are left alone (their sweeps wrap). */
 int enzo_ghost_fill_periodic(const enzo_patch_batch *b);
 
+/* Active cells of every patch to (enzo_pack_active) or from (enzo_unpack_active)
+ * a packed layout without ghost zones, e.g. a staging copy of a level's state in
+ * host memory: patch i's active cells, x fastest, then y, then z, occupy
+ * packed[f][act_off[i] ...] for the five fields f (DEVICE arrays; act_off:
+ * DEVICE int64 [npatch], chosen by the caller, blocks must not overlap).
+ * packed_ge: the same for the gas energy (DEVICE, needs b->ge), or NULL to
+ * leave it out.  Unpacking writes active cells only; ghost zones are left as
+ * they are (a sweep or a ghost fill derives them).  Uses the batch's workspace
+ * and stream.  ENZO_ERR_ARG on NULL arrays. */
+int enzo_pack_active(const enzo_patch_batch *b, double *const packed[5], double *packed_ge,
+                     const int64_t *act_off);
+int enzo_unpack_active(const enzo_patch_batch *b, double *const packed[5], double *packed_ge,
+                       const int64_t *act_off);
+
 /* External boundary conditions of a grid (Sec. 3.1 lists reflecting, outflow,
  * inflow and periodic; inflow is not provided). */
 enum {

@@ -87,6 +87,8 @@ def lib():
             L.enzo_step_boundary.argtypes = [ctypes.POINTER(_Batch), ctypes.POINTER(_Params), i32, vp,
                                              ctypes.POINTER(i32)]
             L.enzo_riemann_solve.argtypes = [ctypes.POINTER(_Riemann), ctypes.POINTER(_Params)]
+            L.enzo_pack_active.argtypes = [ctypes.POINTER(_Batch), vp, vp, vp]
+            L.enzo_unpack_active.argtypes = [ctypes.POINTER(_Batch), vp, vp, vp]
             L.enzo_strerror.argtypes = [ctypes.c_int]
             L.enzo_strerror.restype = ctypes.c_char_p
             L.enzo_launch_count.argtypes = []
@@ -94,7 +96,8 @@ def lib():
             for name in ("enzo_validate_patches", "enzo_ppm_sweep", "enzo_ppm_sweep_dev", "enzo_ppm_sweep_noalloc",
                          "enzo_ghost_fill_periodic", "enzo_ppm_sweep_logged",
                          "enzo_timestep_cfl", "enzo_step", "enzo_riemann_solve",
-                         "enzo_ghost_fill_boundary", "enzo_step_boundary"):
+                         "enzo_ghost_fill_boundary", "enzo_step_boundary", "enzo_pack_active",
+                         "enzo_unpack_active"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
         return _lib
@@ -263,6 +266,35 @@ def ppm_sweep_logged(batch: PatchBatch, direction: int, dt: float, cover_mask: i
 def ghost_fill_periodic(batch: PatchBatch):
     b = batch.c()
     _check(lib().enzo_ghost_fill_periodic(ctypes.byref(b)), "enzo_ghost_fill_periodic")
+
+
+def active_offsets(table) -> np.ndarray:
+    """Offsets of each patch's block in the packed active-cell layout of
+    pack_active / unpack_active (blocks in patch order, no gaps)."""
+    cells = np.prod(np.asarray(table["n"], dtype=np.int64), axis=1)
+    return np.concatenate([[0], np.cumsum(cells)[:-1]]).astype(np.int64)
+
+
+def _pack(batch: PatchBatch, packed, act_off, packed_ge, name):
+    if len(packed) != 5:
+        raise ValueError("five packed fields")
+    b = batch.c()
+    arr = (ctypes.c_void_p * 5)(*[t.data_ptr() for t in packed])
+    _check(getattr(lib(), name)(ctypes.byref(b), arr, packed_ge.data_ptr() if packed_ge is not None else None,
+                                act_off.data_ptr()), name)
+
+
+def pack_active(batch: PatchBatch, packed, act_off, packed_ge=None):
+    """Copy every patch's active cells into the packed device arrays `packed`
+    (five float64 tensors; patch i's cells, x fastest, from act_off[i], a
+    device int64 tensor), and the gas energy into packed_ge when given."""
+    _pack(batch, packed, act_off, packed_ge, "enzo_pack_active")
+
+
+def unpack_active(batch: PatchBatch, packed, act_off, packed_ge=None):
+    """The reverse of pack_active: active cells from the packed arrays; ghost
+    zones are left as they are."""
+    _pack(batch, packed, act_off, packed_ge, "enzo_unpack_active")
 
 
 def timestep_cfl(batch: PatchBatch, params: Params, out=None):

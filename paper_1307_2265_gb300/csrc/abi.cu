@@ -342,6 +342,74 @@ static int boundary_impl(const enzo_patch_batch *b, const int32_t *bc)
     return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
 }
 
+// Active cells of every patch to (PACK) or from a packed layout: patch p's
+// active cells, x fastest, then y, then z, start at act_off[p] of each packed
+// array.  Threads walk the stored cells with the ghost-fill tiles and skip the
+// ghosts, so rows of a patch stay contiguous on both sides.
+struct PackArgs {
+    double *U[6];             // the batch's fields (U[5]: ge, or nullptr)
+    double *packed[6];        // the packed arrays (packed[5]: ge, or nullptr)
+    const int64_t *act_off;
+    int nf;                   // 5, or 6 with the gas energy
+};
+
+template <bool PACK>
+__global__ void __launch_bounds__(kFillThreads) pack_kernel(const enzo_patch *patches, int npatch,
+                                                            const __grid_constant__ PackArgs a, const int *prefix)
+{
+    const int total = prefix[npatch];
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        int lo = 0, hi = npatch;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= tile) lo = mid; else hi = mid;
+        }
+        const enzo_patch P = patches[lo];
+        const int N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng, N2 = P.n[2] + 2 * P.ng;
+        const int64_t cell = (int64_t)(tile - prefix[lo]) * kFillThreads + threadIdx.x;
+        if (cell >= (int64_t)N0 * N1 * N2) continue;
+        const int x = (int)(cell % N0) - P.ng, y = (int)((cell / N0) % N1) - P.ng,
+                  z = (int)(cell / ((int64_t)N0 * N1)) - P.ng;
+        if (x < 0 || x >= P.n[0] || y < 0 || y >= P.n[1] || z < 0 || z >= P.n[2]) continue;
+        const int64_t q = a.act_off[lo] + x + (int64_t)P.n[0] * (y + (int64_t)P.n[1] * z);
+        const int64_t u = P.off + cell;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            if (f >= a.nf) break;
+            if (PACK) a.packed[f][q] = a.U[f][u];
+            else a.U[f][u] = a.packed[f][q];
+        }
+    }
+}
+
+static int pack_impl(const enzo_patch_batch *b, double *const packed[5], double *packed_ge, const int64_t *act_off,
+                     bool pack)
+{
+    int r = check_batch(b);
+    if (r) return r;
+    if (!packed || !act_off || (packed_ge && !b->ge)) return ENZO_ERR_ARG;
+    for (int f = 0; f < 5; ++f)
+        if (!packed[f]) return ENZO_ERR_ARG;
+    if (b->npatch == 0) return ENZO_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(b->stream);
+    r = launch_prefix(b, kKindFill, 0, 0, false, s);
+    if (r) return r;
+    PackArgs a;
+    for (int f = 0; f < 5; ++f) {
+        a.U[f] = b->U[f];
+        a.packed[f] = packed[f];
+    }
+    a.U[5] = packed_ge ? b->ge : nullptr;
+    a.packed[5] = packed_ge;
+    a.nf = packed_ge ? 6 : 5;
+    a.act_off = act_off;
+    const int *prefix = reinterpret_cast<const int *>(ws(b) + kWsPrefix);
+    if (pack) pack_kernel<true><<<device_sms() * 8, kFillThreads, 0, s>>>(b->patches, b->npatch, a, prefix);
+    else pack_kernel<false><<<device_sms() * 8, kFillThreads, 0, s>>>(b->patches, b->npatch, a, prefix);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
+}
+
 }  // namespace enzo
 
 using namespace enzo;
@@ -421,6 +489,17 @@ int enzo_ghost_fill_periodic(const enzo_patch_batch *b)
     if (r) return r;
     if (b->npatch == 0) return ENZO_OK;
     return fill_impl(b);
+}
+
+int enzo_pack_active(const enzo_patch_batch *b, double *const packed[5], double *packed_ge, const int64_t *act_off)
+{
+    return pack_impl(b, packed, packed_ge, act_off, true);
+}
+
+int enzo_unpack_active(const enzo_patch_batch *b, double *const packed[5], double *packed_ge,
+                       const int64_t *act_off)
+{
+    return pack_impl(b, packed, packed_ge, act_off, false);
 }
 
 int enzo_ghost_fill_boundary(const enzo_patch_batch *b, const int32_t bc[3])

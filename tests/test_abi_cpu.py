@@ -198,3 +198,23 @@ def test_hierarchy_gas_energy_pairing_rejected_without_gpu():
     # no ge anywhere, yet an old ge given
     assert L.enzo_ghost_fill_level(ctypes.byref(n), links, ctypes.byref(n), links, old, 32768, 0.5,
                                    boxes, 1, None, 0, 0, 2) == -1
+
+
+def test_pack_arguments_rejected_without_gpu():
+    """enzo_pack_active / enzo_unpack_active refuse NULL packed arrays or
+    offsets, and a packed gas energy for a batch without one, before any
+    launch; an empty batch is a no-op."""
+    L = ez.lib()
+    b = _fake_batch(False)
+    b.workspace = 65536
+    b.ws_bytes = int(L.enzo_workspace_size(1))
+    b.status = 131072
+    packed = (ctypes.c_void_p * 5)(*[2 ** 20 + 8192 * i for i in range(5)])
+    off = ctypes.c_void_p(4096)
+    for fn in (L.enzo_pack_active, L.enzo_unpack_active):
+        assert fn(ctypes.byref(b), packed, None, None) == -1
+        assert fn(ctypes.byref(b), None, None, off) == -1
+        assert fn(ctypes.byref(b), packed, ctypes.c_void_p(8192), off) == -1      # ge packed, batch has none
+        e = ez._Batch()
+        e.npatch = 0
+        assert fn(ctypes.byref(e), packed, None, off) == 0
