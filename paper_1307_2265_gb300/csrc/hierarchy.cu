@@ -181,9 +181,9 @@ __global__ void __launch_bounds__(128) interp_ghosts_kernel(const __grid_constan
 
 // Ghost boxes copied from siblings: one CTA per box (boxes are the face, edge
 // and corner slabs of a patch's ghost shell, 27 to a few thousand cells).
-// Each thread loads the five fields of two cells before storing any, so that
-// enough loads are in flight to cover HBM latency (sources are active cells,
-// which this kernel never writes).
+// Each thread loads the fields (five, six with the gas energy) of two cells
+// before storing any, so that enough loads are in flight to cover HBM latency
+// (sources are active cells, which this kernel never writes).
 // The source patches may belong to another batch of the same level (a
 // rebuild copying the old grids into the new ones).
 struct CopyArgs {
