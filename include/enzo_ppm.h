@@ -122,8 +122,9 @@ typedef struct {
     double *freg;                 /* DEVICE flux registers (see enzo_patch.freg_*), or NULL */
     double *ge;                   /* DEVICE gas-energy field rho e (field_len elements, same
                                      layout as U), or NULL: read and updated only by
-                                     sweeps with ENZO_OPT_DUAL, carried by the ghost fills
-                                     whenever non-NULL */
+                                     sweeps with ENZO_OPT_DUAL; carried whenever non-NULL
+                                     by the ghost fills and the hierarchy calls (a sixth
+                                     field there, and a sixth flux-register component) */
 } enzo_patch_batch;
 
 /* Interface flux solvers (Sec. 4.1.2): the two-shock Riemann solver with a
