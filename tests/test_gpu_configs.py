@@ -124,3 +124,79 @@ def test_blast_grid_512_learned_and_plain(trained):
     assert sl["interfaces"] == sp["interfaces"] and sl["guess_calls"] < sl["interfaces"]
     assert sl["newton_iters"] <= sp["newton_iters"]
     assert sp["nan"] == 0 and sl["nan"] == 0 and sl["newton_nonconv"] == 0
+
+
+def test_config3_full_level_sampled_patches_match_the_oracle():
+    """The batched level at full size (4000 self-periodic patches of 8..64
+    cells per axis, 1.89e8 cells), in the bench's launch configuration: one
+    persistent launch per sweep over the whole level, the FP32 + learned step
+    replayed from a CUDA graph.  The level dt is the oracle's CFL rule over
+    every patch (the GPU's FP64 reduction gives the same value).  On sampled
+    patches (the first, the last, the largest, the smallest and four seeded
+    ones), which the oracle steps one by one with that dt: the FP64 step is
+    bit-identical, the FP32 + learned step within L1 1e-4 per field."""
+    import torch
+    sizes = synth.patch_sizes(4000, config=3)
+    sizes, offsets, flat = synth.batched_level(4000, config=3, sizes=sizes)
+    dx = [1.0 / 64] * 3
+    table = ez.patch_table(sizes, offsets, dx, flags=ez.PATCH_PERIODIC)
+    P = oracle.Params(gamma=G)
+    rate = max(oracle.cfl_rate([synth.patch_view(f, offsets[i], sizes[i]) for f in flat], dx, P)
+               for i in range(len(sizes)))
+    dt = 0.4 / rate
+    cells = np.prod(sizes, axis=1)
+    rng = np.random.default_rng(77)
+    sample = sorted({0, len(sizes) - 1, int(np.argmax(cells)), int(np.argmin(cells)),
+                     *rng.choice(len(sizes), 4, replace=False).tolist()})
+    ref = {}
+    for i in sample:
+        U = [synth.patch_view(f, offsets[i], sizes[i]).copy() for f in flat]
+        oracle.step_periodic(U, dx, dt, 0, P)
+        ref[i] = U
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch = ez.PatchBatch(table, flat, stream=stream)
+    host = [torch.from_numpy(f) for f in flat]
+
+    def reset():
+        torch.cuda.synchronize()
+        for u, h in zip(batch.U, host):
+            u.copy_(h)
+        torch.cuda.synchronize()
+
+    p64 = ez.Params(gamma=G, precision=ez.FP64)
+    with torch.cuda.stream(stream):
+        assert ez.timestep_cfl(batch, ez.Params(gamma=G, cfl=0.4, precision=ez.FP64)) == dt
+        batch.dt_dev.fill_(dt)
+        for d in (0, 1, 2):
+            ez.ppm_sweep_dev(batch, d, batch.dt_dev, 0, p64)
+    stream.synchronize()
+    for i in sample:
+        for a, b in zip(batch.patch_fields(i), ref[i]):
+            assert np.array_equal(a.cpu().numpy()[3:-3, 3:-3, 3:-3], b[3:-3, 3:-3, 3:-3]), i
+
+    net = ez.MLP(seed=4)
+    pml = ez.Params(gamma=G, precision=ez.FP32, guess=ez.GUESS_MLP, mlp=net.blob)
+    reset()
+    with torch.cuda.stream(stream):                      # warm-up outside the capture
+        batch.dt_dev.fill_(dt)
+        for d in (0, 1, 2):
+            ez.ppm_sweep_dev(batch, d, batch.dt_dev, 0, pml)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for d in (0, 1, 2):
+            ez.ppm_sweep_dev(batch, d, batch.dt_dev, 0, pml)
+    reset()
+    batch.reset_status()
+    with torch.cuda.stream(stream):
+        batch.dt_dev.fill_(dt)
+        g.replay()
+    stream.synchronize()
+    assert batch.read_status()["nan"] == 0
+    for i in sample:
+        for f, (a, b) in enumerate(zip(batch.patch_fields(i), ref[i])):
+            A = a.cpu().numpy()[3:-3, 3:-3, 3:-3]
+            B = b[3:-3, 3:-3, 3:-3]
+            l1 = float(np.sum(np.abs(A - B)) / np.sum(np.abs(B)))
+            assert l1 <= 1e-4, (i, f, l1)
