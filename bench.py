@@ -379,6 +379,15 @@ def run_gpu(args, rank, world):
         ends.append(e)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(max(ee0.elapsed_time(e) for e in ends) / ke, world)
+    # the copy-out of lane 0's last step holds that lane's state: check the
+    # first and last patches against the device fields directly
+    for i in (0, len(sizes) - 1):
+        o, c = int(act_off_h[i]), int(np.prod(sizes[i]))
+        for f in range(5):
+            got = host_out[0][f][o:o + c].numpy()
+            want = lanes[0][0].patch_fields(i)[f][3:-3, 3:-3, 3:-3].cpu().numpy().ravel()
+            if not np.array_equal(got, want):
+                raise RuntimeError(f"end-to-end copy-out differs from the device state (patch {i}, field {f})")
     del lanes, host_out, dev_act, host_act
     torch.cuda.empty_cache()
 

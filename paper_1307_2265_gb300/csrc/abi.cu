@@ -27,8 +27,9 @@ __device__ __forceinline__ int tiles_of(const enzo_patch &P, int64_t field_len, 
         const int64_t pen = (int64_t)(hi[a1] - lo[a1]) * (hi[a2] - lo[a2]);
         return (int)((pen + tile_pencils - 1) / tile_pencils);
     }
-    if (kind == kKindFill) {
-        if (P.flags & ENZO_PATCH_PERIODIC) return 0;
+    if (kind == kKindFill || kind == kKindStored) {
+        // ghost fills leave periodic patches alone; packing visits every patch
+        if (kind == kKindFill && (P.flags & ENZO_PATCH_PERIODIC)) return 0;
         const int64_t vol = (int64_t)(P.n[0] + 2 * P.ng) * (P.n[1] + 2 * P.ng) * (P.n[2] + 2 * P.ng);
         return (int)((vol + kFillThreads - 1) / kFillThreads);
     }
@@ -344,8 +345,9 @@ static int boundary_impl(const enzo_patch_batch *b, const int32_t *bc)
 
 // Active cells of every patch to (PACK) or from a packed layout: patch p's
 // active cells, x fastest, then y, then z, start at act_off[p] of each packed
-// array.  Threads walk the stored cells with the ghost-fill tiles and skip the
-// ghosts, so rows of a patch stay contiguous on both sides.
+// array.  Threads walk the stored cells of every patch (periodic ones too) in
+// tiles of the ghost-fill size and skip the ghosts, so rows of a patch stay
+// contiguous on both sides.
 struct PackArgs {
     double *U[6];             // the batch's fields (U[5]: ge, or nullptr)
     double *packed[6];        // the packed arrays (packed[5]: ge, or nullptr)
@@ -392,7 +394,7 @@ static int pack_impl(const enzo_patch_batch *b, double *const packed[5], double 
         if (!packed[f]) return ENZO_ERR_ARG;
     if (b->npatch == 0) return ENZO_OK;
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
-    r = launch_prefix(b, kKindFill, 0, 0, false, s);
+    r = launch_prefix(b, kKindStored, 0, 0, false, s);
     if (r) return r;
     PackArgs a;
     for (int f = 0; f < 5; ++f) {

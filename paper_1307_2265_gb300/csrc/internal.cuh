@@ -128,8 +128,9 @@ cudaError_t launch_riemann_fp32(const RiemannArgs &a, cudaStream_t s);
 void note_launch(unsigned n = 1);
 
 // Work-list kinds of the tile prefix: sweep pencils, ghost-fill cells (whole
-// stored block), active cells (kCflCells per tile), 8^3 blocks of active cells.
-enum { kKindSweep = 0, kKindFill = 1, kKindCells = 2, kKindTiles8 = 3 };
+// stored block, non-periodic patches), active cells (kCflCells per tile), 8^3
+// blocks of active cells, stored cells of every patch (packing).
+enum { kKindSweep = 0, kKindFill = 1, kKindCells = 2, kKindTiles8 = 3, kKindStored = 4 };
 constexpr int kFlagTile = 8;            // flag kernel: 8^3 active cells per CTA
 
 // Launch of the per-patch tile prefix kernel (kind: kKind*) on stream s.

@@ -1,5 +1,6 @@
 """Packed active-cell layout on the GPU (enzo_pack_active / enzo_unpack_active):
-on a ragged batch (1-cell axes, patches of one to several fill tiles) the
+on a ragged batch (1-cell axes, patches of one to several fill tiles, with and
+without the periodic flag) the
 packed arrays hold each patch's active cells x fastest in its block, with the
 gas energy when asked; unpacking writes exactly the active cells back and
 leaves the ghost zones untouched.  Pure data movement: bit-exact."""
@@ -14,19 +15,20 @@ pytestmark = pytest.mark.gpu
 SIZES = [(1, 1, 1), (7, 1, 3), (16, 9, 5), (33, 20, 17), (1, 40, 2), (64, 8, 8)]
 
 
-def _batch(seed=0):
+def _batch(seed=0, flags=0):
     patches = [white_patch(n, seed + i) for i, n in enumerate(SIZES)]
     ges = [np.random.default_rng(50 + i).normal(size=U[0].shape) for i, U in enumerate(patches)]
     offs = np.concatenate([[0], np.cumsum([U[0].size for U in patches])[:-1]])
-    table = ez.patch_table([(n[0], n[1], n[2]) for n in SIZES], offs, [0.1] * 3)
+    table = ez.patch_table([(n[0], n[1], n[2]) for n in SIZES], offs, [0.1] * 3, flags=flags)
     flat = [np.concatenate([U[f].ravel() for U in patches]) for f in range(5)]
     b = ez.PatchBatch(table, flat, ge=np.concatenate([g.ravel() for g in ges]))
     return b, patches, ges
 
 
+@pytest.mark.parametrize("flags", [0, ez.PATCH_PERIODIC])
 @pytest.mark.parametrize("with_ge", [False, True])
-def test_pack_then_unpack_round_trip(with_ge):
-    b, patches, ges = _batch()
+def test_pack_then_unpack_round_trip(with_ge, flags):
+    b, patches, ges = _batch(flags=flags)
     act_off_h = ez.active_offsets(b.table)
     cells = int(sum(np.prod(n) for n in SIZES))
     act_off = torch.from_numpy(act_off_h).to(b.device)
