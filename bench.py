@@ -388,7 +388,18 @@ def run_gpu(args, rank, world):
             want = lanes[0][0].patch_fields(i)[f][3:-3, 3:-3, 3:-3].cpu().numpy().ravel()
             if not np.array_equal(got, want):
                 raise RuntimeError(f"end-to-end copy-out differs from the device state (patch {i}, field {f})")
-    del lanes, host_out, dev_act, host_act
+    # the packing kernels alone (one launch each, on lane 0)
+    b0, s0 = lanes[0]
+    pk_ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with torch.cuda.stream(s0):
+        pk_ev[0].record(s0)
+        ez.unpack_active(b0, dev_act[0], act_off)
+        pk_ev[1].record(s0)
+        ez.pack_active(b0, dev_act[0], act_off)
+        pk_ev[2].record(s0)
+    s0.synchronize()
+    unpack_ms, pack_ms = pk_ev[0].elapsed_time(pk_ev[1]), pk_ev[1].elapsed_time(pk_ev[2])
+    del lanes, host_out, dev_act, host_act, b0
     torch.cuda.empty_cache()
 
     # --- sampled parity + CPU baseline (rank 0, N=1): one learned step of the
@@ -435,7 +446,8 @@ def run_gpu(args, rank, world):
                 "overlap": f"{nl} device copies of the level on their own streams: copy-in, sweeps and "
                            "copy-out of consecutive steps overlap",
                 "host_layout": "active cells packed per patch (enzo_unpack_active / enzo_pack_active on "
-                               "the device each step)"},
+                               "the device each step)",
+                "unpack_ms": unpack_ms, "pack_ms": pack_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": measured_traffic(cells, "ppm_sweep_kernel<float, DIR, true>"),
                      "kernel": "ppm_sweep_kernel<float, DIR, LEARNED=true>",

@@ -27,11 +27,14 @@ __device__ __forceinline__ int tiles_of(const enzo_patch &P, int64_t field_len, 
         const int64_t pen = (int64_t)(hi[a1] - lo[a1]) * (hi[a2] - lo[a2]);
         return (int)((pen + tile_pencils - 1) / tile_pencils);
     }
-    if (kind == kKindFill || kind == kKindStored) {
-        // ghost fills leave periodic patches alone; packing visits every patch
-        if (kind == kKindFill && (P.flags & ENZO_PATCH_PERIODIC)) return 0;
+    if (kind == kKindFill) {
+        if (P.flags & ENZO_PATCH_PERIODIC) return 0;
         const int64_t vol = (int64_t)(P.n[0] + 2 * P.ng) * (P.n[1] + 2 * P.ng) * (P.n[2] + 2 * P.ng);
         return (int)((vol + kFillThreads - 1) / kFillThreads);
+    }
+    if (kind == kKindActive) {
+        const int64_t cells = (int64_t)P.n[0] * P.n[1] * P.n[2];
+        return (int)((cells + kFillThreads - 1) / kFillThreads);
     }
     if (kind == kKindTiles8) {
         const int64_t t0 = (P.n[0] + kFlagTile - 1) / kFlagTile, t1 = (P.n[1] + kFlagTile - 1) / kFlagTile,
@@ -345,9 +348,10 @@ static int boundary_impl(const enzo_patch_batch *b, const int32_t *bc)
 
 // Active cells of every patch to (PACK) or from a packed layout: patch p's
 // active cells, x fastest, then y, then z, start at act_off[p] of each packed
-// array.  Threads walk the stored cells of every patch (periodic ones too) in
-// tiles of the ghost-fill size and skip the ghosts, so rows of a patch stay
-// contiguous on both sides.
+// array.  Each thread takes one active cell of every patch (periodic ones
+// too), consecutive threads consecutive packed cells, so rows stay contiguous
+// on both sides; the cell's coordinates come from 32-bit divisions (64-bit
+// only for patches of more than 2^31 cells).
 struct PackArgs {
     double *U[6];             // the batch's fields (U[5]: ge, or nullptr)
     double *packed[6];        // the packed arrays (packed[5]: ge, or nullptr)
@@ -367,14 +371,24 @@ __global__ void __launch_bounds__(kFillThreads) pack_kernel(const enzo_patch *pa
             if (prefix[mid] <= tile) lo = mid; else hi = mid;
         }
         const enzo_patch P = patches[lo];
-        const int N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng, N2 = P.n[2] + 2 * P.ng;
-        const int64_t cell = (int64_t)(tile - prefix[lo]) * kFillThreads + threadIdx.x;
-        if (cell >= (int64_t)N0 * N1 * N2) continue;
-        const int x = (int)(cell % N0) - P.ng, y = (int)((cell / N0) % N1) - P.ng,
-                  z = (int)(cell / ((int64_t)N0 * N1)) - P.ng;
-        if (x < 0 || x >= P.n[0] || y < 0 || y >= P.n[1] || z < 0 || z >= P.n[2]) continue;
-        const int64_t q = a.act_off[lo] + x + (int64_t)P.n[0] * (y + (int64_t)P.n[1] * z);
-        const int64_t u = P.off + cell;
+        const int64_t ncell = (int64_t)P.n[0] * P.n[1] * P.n[2];
+        const int64_t c = (int64_t)(tile - prefix[lo]) * kFillThreads + threadIdx.x;
+        if (c >= ncell) continue;
+        int x, y, z;
+        if (ncell <= 0x7fffffff) {
+            const unsigned cc = (unsigned)c, t = cc / (unsigned)P.n[0];
+            x = (int)(cc - t * (unsigned)P.n[0]);
+            z = (int)(t / (unsigned)P.n[1]);
+            y = (int)(t - (unsigned)z * (unsigned)P.n[1]);
+        } else {
+            const int64_t t = c / P.n[0];
+            x = (int)(c - t * P.n[0]);
+            z = (int)(t / P.n[1]);
+            y = (int)(t - (int64_t)z * P.n[1]);
+        }
+        const int N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng;
+        const int64_t q = a.act_off[lo] + c;
+        const int64_t u = P.off + (x + P.ng) + (int64_t)N0 * ((y + P.ng) + (int64_t)N1 * (z + P.ng));
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
             if (f >= a.nf) break;
@@ -394,7 +408,7 @@ static int pack_impl(const enzo_patch_batch *b, double *const packed[5], double 
         if (!packed[f]) return ENZO_ERR_ARG;
     if (b->npatch == 0) return ENZO_OK;
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
-    r = launch_prefix(b, kKindStored, 0, 0, false, s);
+    r = launch_prefix(b, kKindActive, 0, 0, false, s);
     if (r) return r;
     PackArgs a;
     for (int f = 0; f < 5; ++f) {

@@ -129,8 +129,9 @@ void note_launch(unsigned n = 1);
 
 // Work-list kinds of the tile prefix: sweep pencils, ghost-fill cells (whole
 // stored block, non-periodic patches), active cells (kCflCells per tile), 8^3
-// blocks of active cells, stored cells of every patch (packing).
-enum { kKindSweep = 0, kKindFill = 1, kKindCells = 2, kKindTiles8 = 3, kKindStored = 4 };
+// blocks of active cells, active cells of every patch (kFillThreads per tile;
+// packing).
+enum { kKindSweep = 0, kKindFill = 1, kKindCells = 2, kKindTiles8 = 3, kKindActive = 4 };
 constexpr int kFlagTile = 8;            // flag kernel: 8^3 active cells per CTA
 
 // Launch of the per-patch tile prefix kernel (kind: kKind*) on stream s.
