@@ -208,3 +208,24 @@ def test_dual_gas_energy_follows_the_density_through_rebuilds():
         H.root_step(levels, oracle.Params(gamma=G_COLD, options=8), rebuild=rb)
     assert [p["origin"] for p in levels[1]["patches"]] != before and levels[1]["patches"]
     assert _ge_deviation(levels) == 0.0
+
+
+def test_gas_energy_fills_as_a_scalar():
+    """The oracle's ghost fills treat a sixth field (the gas energy) as a
+    scalar: periodic wrap like the density, and under a reflecting boundary
+    the mirror image without the sign change the normal momentum gets."""
+    rng = np.random.default_rng(5)
+    U = [synth.embed(rng.uniform(0.5, 2.0, (4, 5, 6))) for _ in range(6)]
+    V = [f.copy() for f in U]
+    oracle.fill_periodic(V)
+    ref = U[5].copy()                  # the density's fill applied to the gas energy
+    oracle.fill_periodic([ref, U[1].copy(), U[2].copy(), U[3].copy(), U[4].copy()])
+    assert np.array_equal(V[5], ref)
+    B = [f.copy() for f in U]
+    oracle.fill_boundary(B, (oracle.BC_REFLECT, oracle.BC_OUTFLOW, oracle.BC_PERIODIC))
+    ge, mx = B[5], B[1]
+    # x faces: ghost layer g mirrors active cell g - 1 (storage: ghost 2 - k <-> active 3 + k)
+    for k in range(3):
+        assert np.array_equal(ge[3:-3, 3:-3, 2 - k], ge[3:-3, 3:-3, 3 + k])
+        assert np.array_equal(mx[3:-3, 3:-3, 2 - k], -mx[3:-3, 3:-3, 3 + k])
+    assert np.all(ge[3:-3, 3:-3, :3] > 0)
