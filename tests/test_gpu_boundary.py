@@ -31,6 +31,27 @@ def test_boundary_fill_bitwise(bc):
             assert np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("bc", [(ez.BC_REFLECT, ez.BC_OUTFLOW, ez.BC_PERIODIC),
+                                (ez.BC_OUTFLOW, ez.BC_REFLECT, ez.BC_REFLECT)])
+def test_boundary_fill_carries_the_gas_energy(bc):
+    """With a gas-energy field the boundary fill gives it the oracle's scalar
+    fill (mirrored, never negated), bit for bit."""
+    import torch
+    patches = [white_patch(n, seed=60 + i, mach=2.0) for i, n in enumerate([(7, 5, 3), (3, 9, 4)])]
+    ges = [synth.embed(np.random.default_rng(70 + i).uniform(0.5, 2.0, active(U[0]).shape))
+           for i, U in enumerate(patches)]
+    ref = [[f.copy() for f in U] + [g.copy()] for U, g in zip(patches, ges)]
+    for U in ref:
+        oracle.fill_boundary(U, bc)
+    b = batch_from_patches(patches, [0.1] * 3)
+    b.ge = torch.from_numpy(np.concatenate([g.ravel() for g in ges])).to(b.device)
+    ez.ghost_fill_boundary(b, bc)
+    for i, o in enumerate(ref):
+        got = [f.cpu().numpy() for f in b.patch_fields(i)] + [b.patch_ge(i).cpu().numpy()]
+        for a, c in zip(got, o):
+            assert np.array_equal(a, c)
+
+
 def _box(nx=24, ny=10, nz=6, seed=11):
     rng = np.random.default_rng(seed)
     shape = (nz, ny, nx)
