@@ -96,3 +96,22 @@ def test_correction_parts_order_concave_corners_in_waves():
     xs = p3[(p3["dir"] == 0) & (p3["side"] == 0)]
     assert sorted(xs["target"]) == [0, 1]                     # split at coarse y = 4
     assert sorted((int(a[0]), int(b[0])) for a, b in zip(xs["lo"], xs["hi"])) == [(0, 2), (2, 4)]
+
+
+def test_register_sizes_count_components_per_face():
+    """Flux-register sizes: every face bounding an active cell along each axis
+    (all-face register) and the two end faces of each pencil (boundary
+    register), times the components per face (5, or 6 with the gas energy)."""
+    n = np.array([(3, 4, 5), (1, 1, 1), (16, 8, 2)])
+    for nc in (5, 6):
+        a, b = gh.register_sizes(n, nc)
+        for i, (nx, ny, nz) in enumerate(n):
+            assert a[i] == nc * ((nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1))
+            assert b[i] == nc * 2 * (ny * nz + nx * nz + nx * ny)
+
+
+def test_active_offsets_are_consecutive_blocks():
+    import paper_1307_2265_gb300 as ez
+    sizes = [(3, 4, 5), (1, 1, 1), (16, 8, 2)]
+    t = ez.patch_table(sizes, [0, 1000, 2000], [0.1] * 3)
+    assert list(ez.active_offsets(t)) == [0, 60, 61]
