@@ -80,6 +80,12 @@ def build_level(rank, npatch=NPATCH):
     return sizes, offsets, flat
 
 
+def _clocks_path():
+    """Where the nvidia-smi samples go: $ENZO_BENCH_CLOCKS, else a temporary file."""
+    import tempfile
+    return os.environ.get("ENZO_BENCH_CLOCKS") or os.path.join(tempfile.gettempdir(), "bench_clocks.csv")
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
@@ -285,7 +291,7 @@ def run_gpu(args, rank, world):
         return t0.elapsed_time(t1), graphs
 
     # --- headline: batched FP32 + learned guess, graph replay
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
+    clk = ClockSampler(_clocks_path())
     with clk:
         ms, graphs = timed_graph(pml, args.steps, args.warmup)
     ms = max_over_ranks(ms, world)
@@ -602,7 +608,7 @@ def run_variants(args, rank, world):
     peak, peak_kind = measured_peak()
     out = {}
     launches0 = ez.launch_count()
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
+    clk = ClockSampler(_clocks_path())
     with clk:
         for name, params, bpc in variants:
             k = args.steps if params.precision == ez.FP32 else min(args.steps, 2)

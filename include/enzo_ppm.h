@@ -42,7 +42,7 @@ extern "C" {
 #define ENZO_ERR_CUDA (-2)       /* a CUDA runtime call or launch failed */
 #define ENZO_ERR_RANGE (-3)      /* a patch descriptor is out of range */
 #define ENZO_ERR_WORKSPACE (-4)  /* workspace missing or smaller than required */
-#define ENZO_ERR_UNSUPPORTED (-5)/* option not available in this build */
+#define ENZO_ERR_UNSUPPORTED (-5)/* option not available in this library */
 
 /* ---- precision modes ---- */
 #define ENZO_FP64 0  /* every step in FP64, no FMA contraction (parity path) */

@@ -20,7 +20,7 @@ Follows the paper:
     overwritten by the old grids of the same level where they overlap
     (Sec. 3.1 uses the same interpolate-then-copy order for ghost zones).
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * the slope criterion takes |q_{i+1} - q_{i-1}| / (2 |q_i|) for q = rho and
     E (the conserved densities), the shock criterion the absolute pressure
     jump (shocks moving either way), p = (gamma - 1)(E - KE) and e = E - KE;

@@ -15,7 +15,7 @@ Follows the paper:
     dt_l = min(CFL_l, t_parent - t_l); after the fine level catches up, flux
     correction then projection.
 
-Readings where the paper is silent or garbled (listed in the design doc):
+Readings where the paper is silent or garbled:
   * the printed adjustment factor f has the sign that would make the adjusted
     diagonal slopes imply -s' dQ0; the sign that makes them imply s' dQ0 is
     taken: f = (s' dQ0 - sum (1-chi_n) dQ_n) / (sum chi_n dQ_n + eps), eps = 1e-300;

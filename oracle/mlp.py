@@ -2,7 +2,7 @@
 
 Not in the paper: the two-shock Riemann solver of Sec. 4.1.2 iterates on p*,
 and this small network predicts the starting point.  The plain guess and the
-converged Newton iteration stay the judge of the answer.
+converged Newton iteration still decide the answer.
 
 Network: 6 -> 64 -> 64 -> 1 with SiLU activations, predicting
 y = ln(p* / p_ref).  Inputs use the Riemann problem's invariances under

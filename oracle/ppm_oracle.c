@@ -23,7 +23,7 @@
  *                 the HLL fallback for cells that go to negative density.
  *   Sec. 9        hydro CFL timestep, harmonic form over axes, min over level.
  *
- * Readings where the paper is silent or garbled (each listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - update sign: U_j += dt/dx (F_{j-1/2} - F_{j+1/2}), momentum uses rho^n v^n
  *     (the printed difference equations carry a flipped sign and rho^{n+1}).
  *   - E is the total energy DENSITY; specific values appear only in fluxes.
@@ -144,7 +144,7 @@ static int newton(double rl, double ul, double pl, double rr, double ur, double 
 
 /* Full two-shock solve and sampling at x/t = 0.  If p_guess > 0 it is used as
  * the starting guess; a guess that does not converge is retried from the
- * plain guess (the plain solver stays the judge). */
+ * plain guess (the plain solver still decides the answer). */
 static void riemann_twoshock(double rl, double ul, double pl, double rr, double ur, double pr,
                              double p_guess, const or_params *P, or_riemann_out *o)
 {

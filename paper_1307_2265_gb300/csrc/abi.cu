@@ -644,7 +644,7 @@ const char *enzo_strerror(int code)
     case ENZO_ERR_CUDA: return "CUDA error";
     case ENZO_ERR_RANGE: return "patch descriptor out of range";
     case ENZO_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
-    case ENZO_ERR_UNSUPPORTED: return "option not supported by this build";
+    case ENZO_ERR_UNSUPPORTED: return "option not supported by this library";
     default: return "unknown error";
     }
 }

@@ -1,5 +1,5 @@
 // Learned Newton starting guess for the two-shock p* (not in the paper; the
-// Riemann solver of Sec. 4.1.2 stays the judge).  MLP 6 -> 64 -> 64 -> 1 with
+// Riemann solver of Sec. 4.1.2 still decides the answer).  MLP 6 -> 64 -> 64 -> 1 with
 // SiLU, BF16 weights and activations, FP32 accumulation in tensor memory,
 // predicting y = ln(p* / sqrt(p_L p_R)) from Riemann-invariant features.
 //
