@@ -81,9 +81,12 @@ def build_level(rank, npatch=NPATCH):
 
 
 def _clocks_path():
-    """Where the nvidia-smi samples go: $ENZO_BENCH_CLOCKS, else a temporary file."""
+    """Where this rank's nvidia-smi samples go: $ENZO_BENCH_CLOCKS, else a
+    temporary file (ranks other than 0 add their local rank to the name)."""
     import tempfile
-    return os.environ.get("ENZO_BENCH_CLOCKS") or os.path.join(tempfile.gettempdir(), "bench_clocks.csv")
+    r = _env_int("LOCAL_RANK", 0)
+    base = os.environ.get("ENZO_BENCH_CLOCKS") or os.path.join(tempfile.gettempdir(), "bench_clocks.csv")
+    return base if r == 0 else f"{base}.rank{r}"
 
 
 class ClockSampler:
