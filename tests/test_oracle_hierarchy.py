@@ -229,3 +229,31 @@ def test_gas_energy_fills_as_a_scalar():
         assert np.array_equal(ge[3:-3, 3:-3, 2 - k], ge[3:-3, 3:-3, 3 + k])
         assert np.array_equal(mx[3:-3, 3:-3, 2 - k], -mx[3:-3, 3:-3, 3 + k])
     assert np.all(ge[3:-3, 3:-3, :3] > 0)
+
+
+@pytest.mark.slow
+def test_dual_hierarchy_conserves_the_five_fields():
+    """With the dual-energy option (cold cells taking their pressure from the
+    gas energy) a subcycled root step still conserves the composite totals of
+    mass, momentum and energy to round-off: the sixth field changes the
+    fluxes, not their conservative use."""
+    layout, _ = _small(seed=3)
+    fields = synth.hierarchy_fields(layout, config=5)
+    six = []
+    for lev in fields:
+        per = []
+        for U in lev:
+            A = [H._active(f) for f in U]
+            ke = 0.5 * ((A[1] ** 2 + A[2] ** 2) + A[3] ** 2) / A[0]
+            V = [f.copy() for f in U]
+            H._active(V[4])[...] = ke + 1e-4 * (A[4] - ke)      # cold: E - KE < 1e-3 E
+            per.append(V + [synth.embed(2e-4 * (A[4] - ke))])   # ge: twice E - KE
+        six.append(per)
+    levels = H.make_levels(layout, six, 1.0 / 16)
+    t0 = H.composite_totals(levels)
+    scale = H.composite_totals([{"patches": [{"n": p["n"], "origin": p["origin"], "parent": p["parent"],
+                                              "U": [np.abs(f) for f in p["U"][:5]]} for p in L["patches"]],
+                                 "dx": L["dx"]} for L in levels])
+    H.root_step(levels, oracle.Params(options=8), log=[])
+    t1 = H.composite_totals(levels)
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0) / scale
