@@ -64,7 +64,7 @@ def test_pack_then_unpack_round_trip(with_ge, flags):
                 assert np.array_equal(active(a), active(want)), (i, f)
 
 
-def test_pack_of_an_empty_batch_and_bad_arguments():
+def test_pack_needs_five_packed_arrays():
     b, _, _ = _batch()
     act_off = torch.zeros(len(SIZES), dtype=torch.int64, device=b.device)
     packed = [torch.zeros(1, dtype=torch.float64, device=b.device) for _ in range(4)]
