@@ -732,7 +732,7 @@ def run_rebuild(args, rank, world):
             root = hier.levels[0]["batch"]
             flags = torch.zeros(R ** 3, dtype=torch.uint8, device=root.device)
             off = torch.zeros(1, dtype=torch.int64, device=root.device)
-            fp = gh._FlagParams(GAMMA, 0.3, 0.33, 0.1, 0.0)
+            fp = gh._FlagParams(GAMMA, 0.3, 0.33, 0.1, 0.0, ez.FP32)
             L = gh._lib()
             with torch.cuda.stream(hier.stream):
                 b = root.c()

@@ -40,7 +40,8 @@ extern "C" {
 #define ENZO_OK 0
 #define ENZO_ERR_ARG (-1)        /* NULL pointer, bad enum, bad size, non-finite dt */
 #define ENZO_ERR_CUDA (-2)       /* a CUDA runtime call or launch failed */
-#define ENZO_ERR_RANGE (-3)      /* a patch descriptor is out of range */
+#define ENZO_ERR_RANGE (-3)      /* a patch descriptor is out of range, or a batch is larger
+                                    than a fixed limit of the call */
 #define ENZO_ERR_WORKSPACE (-4)  /* workspace missing or smaller than required */
 #define ENZO_ERR_UNSUPPORTED (-5)/* option not available in this library */
 
@@ -231,19 +232,20 @@ int enzo_ppm_sweep_logged(const enzo_patch_batch *b, int32_t dir, double dt, int
  * allocate device memory for this library, for instance a host code that owns
  * every device buffer through its own pool, or one whose memory budget is
  * fixed once time stepping starts.  It performs the same sweep with the same
- * arguments, but ignores b->workspace and b->ws_bytes (they may be NULL / 0).
- * Its scratch (the tile table and tile counter) lives in a 128 KiB array of
- * device memory owned by the library.  Every GPU that loads the library keeps
- * that array until the process exits.
+ * arguments and checks as enzo_ppm_sweep (b->patches, b->U, b->status,
+ * b->stream, b->freg, b->ge, p->tile ...), but ignores b->workspace and
+ * b->ws_bytes (they may be NULL / 0).  Its scratch (the tile table and tile
+ * counter) lives in a 128 KiB array of device memory owned by the library.
+ * Every GPU that loads the library keeps that array until the process exits.
  *   - At most 32000 patches per call; larger batches return ENZO_ERR_RANGE.
  *   - The first call on a device looks up the array's device address and
- *     caches it.  Make that first call before any stream capture.
+ *     caches it.  Make that first call before any stream capture, and do not
+ *     keep using the library after cudaDeviceReset.
  *   - All calls share the array.  Each call rewrites the tile table and zeroes
  *     the counter before use, so the previous call's contents do not matter,
  *     but calls whose kernels overlap on the GPU (e.g. on two streams) race on
  *     it.
- *   - Nothing is allocated or freed; ENZO_GUESS_MLP returns ENZO_ERR_UNSUPPORTED.
- * b->patches, b->U, b->status and b->stream are used as in enzo_ppm_sweep. */
+ *   - Nothing is allocated or freed; ENZO_GUESS_MLP returns ENZO_ERR_UNSUPPORTED. */
 int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, double dt, int32_t cover_mask,
                            const enzo_params *p);
 
@@ -446,6 +448,14 @@ typedef struct {
                            (0.33) with u_{i-1} - u_{i+1} > 0 along that axis ... */
     double shock_e;     /* ... and e_i / E_i > shock_e (0.1), e = E - KE */
     double mass;        /* baryon mass: rho dx^3 > mass */
+    int32_t precision;  /* ENZO_FP64: every ratio formed in FP64 as written above (the
+                           default of a zeroed struct); ENZO_FP32: slope and shock from
+                           FP32 primitives (FP64 values rounded toward zero) compared
+                           without division, |q_{i+1} - q_{i-1}| > 2 slope |q_i|,
+                           |dp| > shock_dp min(p), e_i > shock_e E_i; a cell whose FP64
+                           ratio lies within about 1e-6 of its threshold may then flag
+                           differently.  The mass test is FP64 in both.  Other values:
+                           ENZO_ERR_ARG */
 } enzo_flag_params;
 
 enum { ENZO_FLAG_SLOPE = 1, ENZO_FLAG_SHOCK = 2, ENZO_FLAG_MASS = 4 };
@@ -454,9 +464,10 @@ enum { ENZO_FLAG_SLOPE = 1, ENZO_FLAG_SHOCK = 2, ENZO_FLAG_MASS = 4 };
  * + (k n_y + j) n_x + i] receives the ENZO_FLAG_* bits of active cell (i, j, k)
  * of patch i (DEVICE arrays: uint8 flags, int64 flag_off[npatch]).  Neighbours
  * come from the ghost zones, which the caller fills first, or wrap for
- * ENZO_PATCH_PERIODIC patches.  FP64, each operation rounded once in the order
- * written, so the flags are exact functions of the fields.  Uses the batch's
- * workspace and stream.  ENZO_ERR_ARG on NULL arguments. */
+ * ENZO_PATCH_PERIODIC patches.  Each operation is rounded once in the order
+ * written (fp->precision picks FP64 or FP32), so the flags are exact functions
+ * of the fields.  Uses the batch's workspace and stream.  ENZO_ERR_ARG on NULL
+ * arguments or an unknown precision. */
 int enzo_flag_cells(const enzo_patch_batch *b, const enzo_flag_params *fp, uint8_t *flags,
                     const int64_t *flag_off);
 

@@ -24,10 +24,8 @@ Readings where the paper is silent:
   * the slope criterion takes |q_{i+1} - q_{i-1}| / (2 |q_i|) for q = rho and
     E (the conserved densities), the shock criterion the absolute pressure
     jump (shocks moving either way), p = (gamma - 1)(E - KE) and e = E - KE;
-    both are evaluated in FP32 from the conserved values rounded toward zero
-    and compared without division (|q_{i+1} - q_{i-1}| > 2 slope |q_i|,
-    |dp| > shock_dp min(p), e > shock_e E): the flags are heuristics, and FP32
-    keeps them off GB300's slow FP64 pipe;
+    each ratio is formed as the paper writes it, in FP64, and compared with
+    its threshold;
   * flags are grown by `buffer` cells (Chebyshev distance, inside the grid)
     before clustering, and cells within `margin` of the grid's edge are then
     cleared (see the last item);
@@ -62,51 +60,41 @@ def _shifted(a, axis, s):
     return a[tuple(sl)]
 
 
-def f32_rz(x):
-    """FP64 -> FP32 by rounding toward zero (the top 23 mantissa bits kept);
-    values below the FP32 normal range become signed zero, values above it and
-    NaN signed infinity."""
-    b = np.ascontiguousarray(x, dtype=np.float64).view(np.uint64)
-    sign = (((b >> np.uint64(63)) & np.uint64(1)).astype(np.uint32)) << np.uint32(31)
-    e = ((b >> np.uint64(52)) & np.uint64(0x7ff)).astype(np.int64) - 896
-    mant = ((b >> np.uint64(29)) & np.uint64(0x7fffff)).astype(np.uint32)
-    bits = sign | (np.clip(e, 0, 255).astype(np.uint32) << np.uint32(23)) | mant
-    out = np.where(e <= 0, sign, np.where(e >= 255, sign | np.uint32(0x7f800000), bits)).astype(np.uint32)
-    return out.view(np.float32)
-
-
 def flag_patch(U, dx, gamma, slope=0.3, shock_dp=0.33, shock_e=0.1, mass=0.0):
     """Flags (uint8, active cells (z, y, x)) of one patch whose ghost zones are
     filled: bit 0 slope, bit 1 shock, bit 2 baryon mass.  A criterion with a
-    threshold <= 0 is off.  The slope and shock tests run in FP32 on the
-    conserved values rounded toward zero, each operation rounded once (one
-    reciprocal of rho, then products), and compare without division; the mass
-    test runs in FP64."""
-    rho, m1, m2, m3, E = (f32_rz(f) for f in U)
-    shape = tuple(s - 2 * NG for s in U[0].shape)
+    threshold <= 0 is off.  Every quantity is FP64, each ratio formed as
+    Sec. 3.6 writes it:
+      slope:  |q_{i+1} - q_{i-1}| / (2 |q_i|) > slope,  q = rho, E;
+      shock:  |p_{i+1} - p_{i-1}| / min(p_{i+1}, p_{i-1}) > shock_dp,
+              u_{i-1} - u_{i+1} > 0 and e_i / E_i > shock_e;
+      mass:   rho dx^3 > mass;
+    with e = E - |m|^2 / (2 rho), p = (gamma - 1) e and u = m / rho (Sec. 2.1)."""
+    rho, m1, m2, m3, E = U
+    shape = tuple(s - 2 * NG for s in rho.shape)
     out = np.zeros(shape, dtype=np.uint8)
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
-        inv = np.float32(1.0) / rho
-        ke = (np.float32(0.5) * ((m1 * m1 + m2 * m2) + m3 * m3)) * inv
+        ke = 0.5 * ((m1 * m1 + m2 * m2) + m3 * m3) / rho
         e = E - ke
-        p = np.float32(gamma - 1.0) * e
-        vel = (m1 * inv, m2 * inv, m3 * inv)
-        s2, dp, ef = np.float32(2.0 * slope), np.float32(shock_dp), np.float32(shock_e)
+        p = (gamma - 1.0) * e
+        mom = (m1, m2, m3)
         for ax in range(3):
             if slope > 0.0:
                 for q in (rho, E):
                     qm, q0, qp = _shifted(q, ax, -1), _shifted(q, ax, 0), _shifted(q, ax, 1)
-                    out[np.abs(qp - qm) > s2 * np.abs(q0)] |= SLOPE
+                    hit = np.abs(qp - qm) / (2.0 * np.abs(q0)) > slope
+                    out[hit] |= SLOPE
             if shock_dp > 0.0:
                 pm, pp = _shifted(p, ax, -1), _shifted(p, ax, 1)
                 pmin = np.minimum(pm, pp)
-                um, up = _shifted(vel[ax], ax, -1), _shifted(vel[ax], ax, 1)
-                hit = (np.abs(pp - pm) > dp * pmin) & (um - up > np.float32(0.0)) & \
-                      (_shifted(e, ax, 0) > ef * _shifted(E, ax, 0))
+                um = _shifted(mom[ax], ax, -1) / _shifted(rho, ax, -1)
+                up = _shifted(mom[ax], ax, 1) / _shifted(rho, ax, 1)
+                frac = _shifted(e, ax, 0) / _shifted(E, ax, 0)
+                hit = (np.abs(pp - pm) / pmin > shock_dp) & (um - up > 0.0) & (frac > shock_e)
                 out[hit] |= SHOCK
-    if mass > 0.0:
-        hit = _shifted(U[0], 0, 0) * (dx * dx * dx) > mass
-        out[hit] |= MASS
+        if mass > 0.0:
+            hit = _shifted(rho, 0, 0) * (dx * dx * dx) > mass
+            out[hit] |= MASS
     return out
 
 

@@ -189,7 +189,7 @@ __global__ void dt_finalize_kernel(const unsigned long long *rate_bits, double c
     if (dt_out) *dt_out = dt;
 }
 
-static int resolve(const enzo_params *p, MethodParams &m)
+int resolve_params(const enzo_params *p, MethodParams &m)
 {
     if (!p) return ENZO_ERR_ARG;
     if (!(p->gamma > 1.0) || !(p->gamma < 100.0)) return ENZO_ERR_ARG;
@@ -269,9 +269,9 @@ static int device_sms()
     return sms > 0 ? sms : 1;
 }
 
-static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const double *dt_dev,
-                      int cover, const MethodParams &m, int precision, int tile_pencils, float *log = nullptr,
-                      unsigned long long *log_count = nullptr, long long log_cap = 0, int log_stride = 0)
+int sweep_with_scratch(const enzo_patch_batch *b, char *scratch, int dir, double dt, const double *dt_dev,
+                       int cover, const MethodParams &m, int precision, int tile_pencils, float *log,
+                       unsigned long long *log_count, long long log_cap, int log_stride)
 {
     if ((m.options & ENZO_OPT_DUAL) && !b->ge) return ENZO_ERR_ARG;
     // flux registers of a batch with a gas-energy field hold six components
@@ -281,8 +281,11 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
     int tile = tile_pencils > 0 ? tile_pencils : kSweepThreads;
     if (precision == ENZO_FP64 || m.guess == ENZO_GUESS_MLP || b->freg || m.options || m.fallback == 2)
         tile = kSweepThreads;
-    int r = launch_prefix(b, kKindSweep, dir, cover, false, s, tile);
-    if (r) return r;
+    launch_tile_prefix(b->patches, b->npatch, b->field_len, kKindSweep, dir, cover,
+                       reinterpret_cast<int *>(scratch + kWsPrefix), reinterpret_cast<unsigned *>(scratch + kWsCounter),
+                       nullptr, b->status, s, tile);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
     SweepArgs a;
     a.tile = tile;
     a.patches = b->patches;
@@ -294,8 +297,8 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
     a.dt = dt;
     a.dt_ptr = dt_dev;
     a.mp = m;
-    a.prefix = reinterpret_cast<const int *>(ws(b) + kWsPrefix);
-    a.tile_counter = reinterpret_cast<unsigned *>(ws(b) + kWsCounter);
+    a.prefix = reinterpret_cast<const int *>(scratch + kWsPrefix);
+    a.tile_counter = reinterpret_cast<unsigned *>(scratch + kWsCounter);
     a.status = b->status;
     a.freg = b->freg;
     a.ge = (m.options & ENZO_OPT_DUAL) ? b->ge : nullptr;
@@ -312,6 +315,14 @@ static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const doubl
     else e = launch_sweep_fp32(a, sweep_grid_fp32(dev), s);
     note_launch();
     return e == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
+}
+
+static int sweep_impl(const enzo_patch_batch *b, int dir, double dt, const double *dt_dev,
+                      int cover, const MethodParams &m, int precision, int tile_pencils, float *log = nullptr,
+                      unsigned long long *log_count = nullptr, long long log_cap = 0, int log_stride = 0)
+{
+    return sweep_with_scratch(b, ws(b), dir, dt, dt_dev, cover, m, precision, tile_pencils, log, log_count,
+                              log_cap, log_stride);
 }
 
 static int fill_impl(const enzo_patch_batch *b)
@@ -458,7 +469,7 @@ int enzo_ppm_sweep(const enzo_patch_batch *b, int32_t dir, double dt, int32_t co
     int r = check_batch(b);
     if (r) return r;
     MethodParams m;
-    r = resolve(p, m);
+    r = resolve_params(p, m);
     if (r) return r;
     if (dir < 0 || dir > 2 || !(dt >= 0.0) || !std::isfinite(dt) || cover_mask < 0 || cover_mask > 7)
         return ENZO_ERR_ARG;
@@ -473,7 +484,7 @@ int enzo_ppm_sweep_dev(const enzo_patch_batch *b, int32_t dir, const double *dt_
     int r = check_batch(b);
     if (r) return r;
     MethodParams m;
-    r = resolve(p, m);
+    r = resolve_params(p, m);
     if (r) return r;
     if (dir < 0 || dir > 2 || !dt_dev || cover_mask < 0 || cover_mask > 7) return ENZO_ERR_ARG;
     if (m.guess == ENZO_GUESS_MLP && p->precision != ENZO_FP32) return ENZO_ERR_UNSUPPORTED;
@@ -488,7 +499,7 @@ int enzo_ppm_sweep_logged(const enzo_patch_batch *b, int32_t dir, double dt, int
     int r = check_batch(b);
     if (r) return r;
     MethodParams m;
-    r = resolve(p, m);
+    r = resolve_params(p, m);
     if (r) return r;
     if (dir < 0 || dir > 2 || !(dt >= 0.0) || !std::isfinite(dt) || cover_mask < 0 || cover_mask > 7)
         return ENZO_ERR_ARG;
@@ -533,7 +544,7 @@ int enzo_timestep_cfl(const enzo_patch_batch *b, const enzo_params *p, double *d
     int r = check_batch(b);
     if (r) return r;
     MethodParams m;
-    r = resolve(p, m);
+    r = resolve_params(p, m);
     if (r) return r;
     if (!dt_out || !(p->cfl > 0.0) || !(p->cfl <= 1.0)) return ENZO_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
@@ -577,7 +588,7 @@ static int step_impl(const enzo_patch_batch *b, const enzo_params *p, int32_t st
     int r = check_batch(b);
     if (r) return r;
     MethodParams m;
-    r = resolve(p, m);
+    r = resolve_params(p, m);
     if (r) return r;
     if (!dt_dev || step_index < 0) return ENZO_ERR_ARG;
     if (bc && !bc_ok(bc)) return ENZO_ERR_ARG;
@@ -615,7 +626,7 @@ int enzo_riemann_solve(const enzo_riemann_states *st, const enzo_params *p)
 {
     if (!st) return ENZO_ERR_ARG;
     MethodParams m;
-    int r = resolve(p, m);
+    int r = resolve_params(p, m);
     if (r) return r;
     if (st->n < 0) return ENZO_ERR_ARG;
     if (st->n == 0) return ENZO_OK;
@@ -642,7 +653,7 @@ const char *enzo_strerror(int code)
     case ENZO_OK: return "ok";
     case ENZO_ERR_ARG: return "invalid argument";
     case ENZO_ERR_CUDA: return "CUDA error";
-    case ENZO_ERR_RANGE: return "patch descriptor out of range";
+    case ENZO_ERR_RANGE: return "patch descriptor out of range, or batch larger than a fixed limit";
     case ENZO_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case ENZO_ERR_UNSUPPORTED: return "option not supported by this library";
     default: return "unknown error";

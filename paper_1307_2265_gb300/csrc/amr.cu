@@ -1,9 +1,12 @@
 // Hierarchy rebuild (paper Sec. 3.5, 3.6): cell flagging on the GPU and the
 // clustering of flagged cells into new grids on the host.
-//   * flag_kernel: the slope, shock and baryon-mass criteria of Sec. 3.6 per
-//     active cell, from FP32 primitives staged once per 8^3 block (built with
-//     --fmad=false and IEEE division, so each operation rounds once in the
-//     order written and the flags are exact functions of the fields);
+//   * flag_kernel_fp64: the slope, shock and baryon-mass criteria of Sec. 3.6
+//     per active cell, each ratio formed in FP64 as the paper writes it;
+//   * flag_kernel: the same criteria from FP32 primitives staged once per 8^3
+//     block, compared without division (the fast path of FP32 hierarchies);
+//     this unit is built with --fmad=false and IEEE division, so each
+//     operation rounds once in the order written and both kernels' flags are
+//     exact functions of the fields;
 //   * enzo_cluster_flags: Berger & Rigoutsos as Sec. 3.5 describes it, host
 //     C++ over one grid's flags.
 #include <cstdint>
@@ -25,7 +28,83 @@ struct FlagArgs {
     float g1, s2, dp, ef;      // gamma - 1, 2 slope, shock_dp, shock_e (rounded to FP32)
     bool slope, shock;
     double mass;
+    double g1d, sl, dpd, efd;  // the same thresholds in FP64 (flag_kernel_fp64)
 };
+
+// Primitive values of the cell at storage index idx (Sec. 2.1) in FP64, in the
+// order the criteria's reference forms them: KE = 0.5 |m|^2 / rho, e = E - KE,
+// p = (gamma - 1) e, u_ax = m_ax / rho.
+struct Prim64 {
+    double rho, E, e, p;
+};
+
+__device__ __forceinline__ Prim64 prim64(const FlagArgs &a, int64_t idx)
+{
+    Prim64 q;
+    q.rho = a.U[0][idx];
+    q.E = a.U[4][idx];
+    const double m0 = a.U[1][idx], m1 = a.U[2][idx], m2 = a.U[3][idx];
+    const double ke = 0.5 * ((m0 * m0 + m1 * m1) + m2 * m2) / q.rho;
+    q.e = q.E - ke;
+    q.p = a.g1d * q.e;
+    return q;
+}
+
+// FP64 flags, one thread per active cell of an 8^3 block (the tile list of
+// flag_kernel): slope |q_{i+1} - q_{i-1}| / (2 |q_i|) > slope for q = rho, E;
+// shock |p_{i+1} - p_{i-1}| / min(p_{i+1}, p_{i-1}) > shock_dp with
+// u_{i-1} - u_{i+1} > 0 and e_i / E_i > shock_e; mass rho dx^3 > mass.
+// Neighbours come from the ghost zones, or wrap for periodic-flagged patches.
+__global__ void __launch_bounds__(256) flag_kernel_fp64(const __grid_constant__ FlagArgs a)
+{
+    const int total = a.prefix[a.npatch];
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        int lo = 0, hi = a.npatch;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.prefix[mid] <= tile) lo = mid; else hi = mid;
+        }
+        const enzo_patch P = a.patches[lo];
+        const int n[3] = {P.n[0], P.n[1], P.n[2]};
+        const int nt0 = (n[0] + kFlagTile - 1) / kFlagTile, nt1 = (n[1] + kFlagTile - 1) / kFlagTile;
+        const int t = tile - a.prefix[lo];
+        const int b0[3] = {(t % nt0) * kFlagTile, ((t / nt0) % nt1) * kFlagTile, (t / (nt0 * nt1)) * kFlagTile};
+        const int64_t N0 = n[0] + 2 * P.ng, N1 = n[1] + 2 * P.ng;
+        const bool wrap = (P.flags & ENZO_PATCH_PERIODIC) != 0;
+        const double vol = P.dx[0] * P.dx[0] * P.dx[0];
+        for (int c = threadIdx.x; c < kFlagTile * kFlagTile * kFlagTile; c += blockDim.x) {
+            const int g[3] = {b0[0] + c % kFlagTile, b0[1] + (c / kFlagTile) % kFlagTile,
+                              b0[2] + c / (kFlagTile * kFlagTile)};
+            if (g[0] >= n[0] || g[1] >= n[1] || g[2] >= n[2]) continue;
+            auto at = [&](int d, int s) {
+                int h[3] = {g[0], g[1], g[2]};
+                h[d] += s;
+                if (wrap) h[d] = h[d] < 0 ? h[d] + n[d] : (h[d] >= n[d] ? h[d] - n[d] : h[d]);
+                return P.off + (h[0] + P.ng) + N0 * ((h[1] + P.ng) + N1 * (int64_t)(h[2] + P.ng));
+            };
+            const int64_t i0 = at(0, 0);
+            const Prim64 q0 = prim64(a, i0);
+            uint8_t f = 0;
+            for (int ax = 0; ax < 3; ++ax) {
+                const int64_t im = at(ax, -1), ip = at(ax, 1);
+                if (a.slope) {
+                    const double rm = a.U[0][im], rp = a.U[0][ip], Em = a.U[4][im], Ep = a.U[4][ip];
+                    if (fabs(rp - rm) / (2.0 * fabs(q0.rho)) > a.sl) f |= ENZO_FLAG_SLOPE;
+                    if (fabs(Ep - Em) / (2.0 * fabs(q0.E)) > a.sl) f |= ENZO_FLAG_SLOPE;
+                }
+                if (a.shock) {
+                    const Prim64 qm = prim64(a, im), qp = prim64(a, ip);
+                    const double pmin = qm.p < qp.p ? qm.p : qp.p;
+                    const double um = a.U[1 + ax][im] / qm.rho, up = a.U[1 + ax][ip] / qp.rho;
+                    if (fabs(qp.p - qm.p) / pmin > a.dpd && um - up > 0.0 && q0.e / q0.E > a.efd)
+                        f |= ENZO_FLAG_SHOCK;
+                }
+            }
+            if (a.mass > 0.0 && q0.rho * vol > a.mass) f |= ENZO_FLAG_MASS;
+            a.flags[a.flag_off[lo] + g[0] + (int64_t)n[0] * (g[1] + (int64_t)n[1] * g[2])] = f;
+        }
+    }
+}
 
 constexpr int kHalo = kFlagTile + 2;                 // staged block edge
 constexpr int kStage = kHalo * kHalo * kHalo;        // staged cells per CTA
@@ -358,6 +437,7 @@ int enzo_flag_cells(const enzo_patch_batch *b, const enzo_flag_params *fp, uint8
         if (!b->U[f]) return ENZO_ERR_ARG;
     if (b->ws_bytes < enzo_workspace_size(b->npatch)) return ENZO_ERR_WORKSPACE;
     if (!(fp->gamma > 1.0)) return ENZO_ERR_ARG;
+    if (fp->precision != ENZO_FP64 && fp->precision != ENZO_FP32) return ENZO_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(b->stream);
     char *ws = static_cast<char *>(b->workspace);
     launch_tile_prefix(b->patches, b->npatch, b->field_len, kKindTiles8, 0, 0,
@@ -379,7 +459,12 @@ int enzo_flag_cells(const enzo_patch_batch *b, const enzo_flag_params *fp, uint8
     a.slope = fp->slope > 0.0;
     a.shock = fp->shock_dp > 0.0;
     a.mass = fp->mass;
-    flag_kernel<<<sms() * 6, 256, 0, s>>>(a);
+    a.g1d = fp->gamma - 1.0;
+    a.sl = fp->slope;
+    a.dpd = fp->shock_dp;
+    a.efd = fp->shock_e;
+    if (fp->precision == ENZO_FP64) flag_kernel_fp64<<<sms() * 6, 256, 0, s>>>(a);
+    else flag_kernel<<<sms() * 6, 256, 0, s>>>(a);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
 }

@@ -102,6 +102,16 @@ int sweep_grid_fp32(int device);
 // FP32 plain sweep with a chosen tile size (64, 128 or 256 pencils per CTA).
 cudaError_t launch_sweep_fp32_tiled(const SweepArgs &a, cudaStream_t s);
 
+// Checks and defaults of enzo_params shared by every sweep entry point
+// (ENZO_OK or an ENZO_ERR_* code).
+int resolve_params(const enzo_params *p, MethodParams &m);
+// One sweep of batch b whose tile table and tile counter live at `scratch`
+// (the workspace layout: kWsCounter, kWsPrefix).  The batch is checked except
+// for its workspace; dt_dev, when set, replaces dt.
+int sweep_with_scratch(const enzo_patch_batch *b, char *scratch, int dir, double dt, const double *dt_dev,
+                       int cover, const MethodParams &m, int precision, int tile_pencils, float *log = nullptr,
+                       unsigned long long *log_count = nullptr, long long log_cap = 0, int log_stride = 0);
+
 struct CflArgs {
     const enzo_patch *patches;
     int npatch;

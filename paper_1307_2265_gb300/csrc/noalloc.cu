@@ -15,12 +15,15 @@
 //  * Every GPU that loads the library keeps the array until the process exits.
 //  * The first call on each device looks up the array's device address (with
 //    that device current) and caches it.  Make that first call before any
-//    stream capture.
+//    stream capture.  The cached address belongs to the device's primary
+//    context: do not keep using the library after cudaDeviceReset.
 //  * All calls share the one array, and it keeps the contents of the last
 //    call.  The prefix kernel rewrites the tile table and zeroes the counter at
 //    the start of every call.  Calls whose kernels overlap on the GPU (for
 //    example on two streams) race on the array and must not be issued.
 //  * No cudaMalloc, cudaFree or allocating library routine is called.
+//  * Everything else (argument checks, tile sizes, flux registers, the gas
+//    energy) is exactly what enzo_ppm_sweep does with the same arguments.
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -69,64 +72,18 @@ extern "C" int enzo_ppm_sweep_noalloc(const enzo_patch_batch *b, int32_t dir, do
     if (b->npatch > kNoAllocMaxPatches) return ENZO_ERR_RANGE;
     if (dir < 0 || dir > 2 || !(dt >= 0.0) || !(dt < INFINITY) || cover_mask < 0 || cover_mask > 7)
         return ENZO_ERR_ARG;
-    if (!(p->gamma > 1.0) || !(p->gamma < 100.0)) return ENZO_ERR_ARG;
-    if (p->precision != ENZO_FP64 && p->precision != ENZO_FP32) return ENZO_ERR_ARG;
-    if (p->guess != ENZO_GUESS_PLAIN) return p->guess == ENZO_GUESS_MLP ? ENZO_ERR_UNSUPPORTED : ENZO_ERR_ARG;
-    if (!(p->rho_floor > 0.0) || !(p->p_floor > 0.0)) return ENZO_ERR_ARG;
-    if (p->precision == ENZO_FP32 && (p->rho_floor < 1e-37 || p->p_floor < 1e-37)) return ENZO_ERR_ARG;
+    MethodParams m;
+    int r = resolve_params(p, m);      // the checks and defaults of enzo_ppm_sweep
+    if (r) return r;
+    // the learned guess keeps its network state in memory the caller allocates
+    if (m.guess == ENZO_GUESS_MLP) return ENZO_ERR_UNSUPPORTED;
     if (b->npatch == 0) return ENZO_OK;
     if (!b->patches || !b->status || b->field_len <= 0) return ENZO_ERR_ARG;
     for (int f = 0; f < 5; ++f)
         if (!b->U[f]) return ENZO_ERR_ARG;
-    const bool f64 = p->precision == ENZO_FP64;
-    MethodParams m;
-    m.gamma = p->gamma;
-    m.rho_floor = p->rho_floor;
-    m.p_floor = p->p_floor;
-    m.newton_tol = p->newton_tol > 0.0 ? p->newton_tol : (f64 ? 1e-14 : 1e-6);
-    m.newton_max = p->newton_max > 0 ? p->newton_max : (f64 ? 20 : 12);
-    if (m.newton_max > 200) return ENZO_ERR_ARG;
-    if (p->fallback < 0 || p->fallback > 2) return ENZO_ERR_ARG;
-    m.fallback = p->fallback;
-    m.guess = p->guess;
-    m.mlp = nullptr;
-    m.mlp_gate = 0.0;
-    if (p->solver != ENZO_SOLVER_TWOSHOCK && p->solver != ENZO_SOLVER_HLL && p->solver != ENZO_SOLVER_HLLC)
-        return ENZO_ERR_ARG;
-    m.solver = p->solver;
-    if (p->options & ~(ENZO_OPT_STEEPEN | ENZO_OPT_FLATTEN | ENZO_OPT_DIFFUSE | ENZO_OPT_DUAL)) return ENZO_ERR_ARG;
-    if ((p->options & ENZO_OPT_DUAL) && (p->solver != ENZO_SOLVER_TWOSHOCK || !b->ge)) return ENZO_ERR_ARG;
-    m.options = p->options;
-
     void *scratch = nullptr;
-    int r = noalloc_scratch(&scratch);
+    r = noalloc_scratch(&scratch);
     if (r) return r;
-    char *ws = static_cast<char *>(scratch);
-    cudaStream_t s = static_cast<cudaStream_t>(b->stream);
-    launch_tile_prefix(b->patches, b->npatch, b->field_len, 0, dir, cover_mask,
-                       reinterpret_cast<int *>(ws + kWsPrefix), reinterpret_cast<unsigned *>(ws + kWsCounter),
-                       nullptr, b->status, s);
-    if (cudaGetLastError() != cudaSuccess) return ENZO_ERR_CUDA;
-    note_launch();
-
-    SweepArgs a;
-    a.patches = b->patches;
-    a.npatch = b->npatch;
-    a.dir = dir;
-    a.cover_mask = cover_mask;
-    a.field_len = b->field_len;
-    for (int f = 0; f < 5; ++f) a.U[f] = b->U[f];
-    a.dt = dt;
-    a.dt_ptr = nullptr;
-    a.mp = m;
-    a.prefix = reinterpret_cast<const int *>(ws + kWsPrefix);
-    a.tile_counter = reinterpret_cast<unsigned *>(ws + kWsCounter);
-    a.status = b->status;
-    a.ge = (m.options & ENZO_OPT_DUAL) ? b->ge : nullptr;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return ENZO_ERR_CUDA;
-    const cudaError_t e = f64 ? launch_sweep_fp64(a, sweep_grid_fp64(dev), s)
-                              : launch_sweep_fp32(a, sweep_grid_fp32(dev), s);
-    note_launch();
-    return e == cudaSuccess ? ENZO_OK : ENZO_ERR_CUDA;
+    return sweep_with_scratch(b, static_cast<char *>(scratch), dir, dt, nullptr, cover_mask, m, p->precision,
+                              p->tile[dir]);
 }

@@ -40,7 +40,7 @@ FLAG_SLOPE, FLAG_SHOCK, FLAG_MASS = 1, 2, 4
 
 class _FlagParams(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("slope", ctypes.c_double), ("shock_dp", ctypes.c_double),
-                ("shock_e", ctypes.c_double), ("mass", ctypes.c_double)]
+                ("shock_e", ctypes.c_double), ("mass", ctypes.c_double), ("precision", ctypes.c_int32)]
 
 
 class _ClusterParams(ctypes.Structure):
@@ -301,10 +301,11 @@ def cluster_flags(flags, efficiency=0.3, small_cells=64, buffer=1, margin=0):
 _PINNED = {}   # pinned host buffers for the flags, by size (reused across rebuilds)
 
 
-def flag_cells(batch, gamma, slope=0.3, shock_dp=0.33, shock_e=0.1, mass=0.0):
+def flag_cells(batch, gamma, slope=0.3, shock_dp=0.33, shock_e=0.1, mass=0.0, precision=0):
     """Flags (host uint8, one array (z, y, x) per patch) of a batch's active
     cells by the library's flag kernel (Sec. 3.6; ENZO_FLAG_* bits); ghost
-    zones must be filled, periodic-flagged patches wrap."""
+    zones must be filled, periodic-flagged patches wrap.  precision: FP64 (the
+    ratios as the paper writes them) or FP32 (staged primitives, no division)."""
     import torch
     n = np.asarray(batch.table["n"], dtype=np.int64)
     cells = np.prod(n, axis=1)
@@ -313,7 +314,7 @@ def flag_cells(batch, gamma, slope=0.3, shock_dp=0.33, shock_e=0.1, mass=0.0):
     with torch.cuda.stream(stream):
         flags = torch.zeros(max(int(cells.sum()), 1), dtype=torch.uint8, device=batch.device)
         offd = torch.from_numpy(off).to(batch.device)
-        fp = _FlagParams(gamma, slope, shock_dp, shock_e, mass)
+        fp = _FlagParams(gamma, slope, shock_dp, shock_e, mass, precision)
         b = batch.c()
         _check(_lib().enzo_flag_cells(ctypes.byref(b), ctypes.byref(fp), flags.data_ptr(), offd.data_ptr()),
                "enzo_flag_cells")
@@ -522,7 +523,7 @@ class Hierarchy:
                                    f["links"].data_ptr(), 2), "enzo_project")
 
     # -- rebuild (Sec. 3.5, 3.6) ---------------------------------------------
-    def rebuild(self, l, gamma, crit, clus, margin=3, nest=1):
+    def rebuild(self, l, gamma, crit, clus, margin=3, nest=1, precision=0):
         """Replace levels l+1, l+2, ... by grids covering the flagged cells of the
         level above each (Sec. 3.5, 3.6): level l's ghosts are filled, its cells
         flagged on the GPU and each patch's flags clustered on the host; every
@@ -533,20 +534,21 @@ class Hierarchy:
         levels those within `nest` cells of the patch's edge (the coarse cells
         outside every new fine face then lie in the parent).  The fill and
         the interpolation run in FP64 in both precisions (the new grids keep
-        their parents' means to FP64 rounding).  Returns the new boxes of level
-        l+1 as (parent, lo, hi) in level-l cells."""
+        their parents' means to FP64 rounding); `precision` picks the flag
+        kernel (FP64 or FP32).  Returns the new boxes of level l+1 as (parent,
+        lo, hi) in level-l cells."""
         with self.torch.cuda.stream(self.stream):
             self._fill(l, 0)
             first = None
             for m in range(l, len(self.levels) - 1):
-                boxes = self._rebuild_one(m, gamma, crit, clus, margin if m == 0 else nest)
+                boxes = self._rebuild_one(m, gamma, crit, clus, margin if m == 0 else nest, precision)
                 first = boxes if first is None else first
         return first
 
-    def _rebuild_one(self, m, gamma, crit, clus, margin):
+    def _rebuild_one(self, m, gamma, crit, clus, margin, flag_precision=0):
         precision = 0
         lev = self.levels[m]
-        flags = flag_cells(lev["batch"], gamma, **crit)
+        flags = flag_cells(lev["batch"], gamma, precision=flag_precision, **crit)
         boxes = []
         for i, fl in enumerate(flags):
             o = lev["origin"][i]
@@ -640,7 +642,7 @@ class Hierarchy:
                     self._end(m)
                     if rebuild is not None:
                         m = self._mark("rebuild")
-                        self.rebuild(l, **rebuild)
+                        self.rebuild(l, **rebuild, precision=params.precision)
                         self._end(m)
             # the loop stops within 1e-14 of the parent's time; the level has reached it
             lev["t"] = t_parent

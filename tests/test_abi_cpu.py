@@ -60,7 +60,7 @@ def test_null_and_bad_arguments_rejected_without_gpu():
     assert L.enzo_ppm_sweep(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -1      # NULL arrays
     assert L.enzo_riemann_solve(None, ctypes.byref(p)) == -1
     assert L.enzo_workspace_size(4000) >= 4 * 4001
-    assert ez.strerror(-3) == "patch descriptor out of range"
+    assert ez.strerror(-3) == "patch descriptor out of range, or batch larger than a fixed limit"
 
 
 def test_validate_patches_ranges():

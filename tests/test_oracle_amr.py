@@ -81,6 +81,30 @@ def test_slope_and_mass_flags_closed_form():
     assert not amr.flag_patch([np.ones_like(rho), z, z, z, E], 0.5, 1.4).any()   # uniform: nothing
 
 
+def test_shock_flags_closed_form():
+    """p_i = 1 + 0.2 i, u_i = -0.5 i, rho = 1 along x (gamma 1.4): the pressure
+    ratio |p_{i+1} - p_{i-1}| / min(p_{i+1}, p_{i-1}) = 0.4 / (0.8 + 0.2 i)
+    exceeds 0.33 for i <= 2 (with max instead of min only i = 0 would), the
+    flow converges everywhere, and e / E = (1 + 0.2 i) / (1 + 0.2 i + 0.05 i^2)
+    is 1, 0.96, 0.875 for i = 0, 1, 2, so shock_e = 0.9 keeps i <= 1.  The
+    same profile with the velocity reversed (diverging flow) flags nothing."""
+    n, g = 8, 1.4
+    i = np.arange(-NG, n + NG, dtype=np.float64)
+    shape = (1 + 2 * NG, 1 + 2 * NG, n + 2 * NG)
+    rho = np.ones(shape)
+    p = np.broadcast_to(1.0 + 0.2 * i, shape).copy()
+    u = np.broadcast_to(-0.5 * i, shape).copy()
+    z = np.zeros(shape)
+    E = p / (g - 1.0) + 0.5 * rho * u * u
+    U = [rho, rho * u, z, z, E]
+    fl = amr.flag_patch(U, 0.5, g, slope=0.0, shock_dp=0.33, shock_e=0.1)[0, 0]
+    assert list((fl & amr.SHOCK) != 0) == [True] * 3 + [False] * (n - 3)
+    fl = amr.flag_patch(U, 0.5, g, slope=0.0, shock_dp=0.33, shock_e=0.9)[0, 0]
+    assert list((fl & amr.SHOCK) != 0) == [True] * 2 + [False] * (n - 2)
+    U[1] = -U[1]
+    assert not amr.flag_patch(U, 0.5, g, slope=0.0, shock_dp=0.33, shock_e=0.1).any()
+
+
 def test_cluster_exact_rectangles_and_l_shape():
     F = np.zeros((1, 12, 20), np.uint8)
     F[0, 3:7, 4:15] = 1
@@ -203,22 +227,6 @@ def test_dynamic_w_cycle_keeps_the_shock_refined_and_conserves():
         x_prev = xs.max()
     tot = H.composite_totals(levels)
     assert np.all(np.abs(tot - tot0) <= 1e-12 * np.abs(tot0).max()), (tot0, tot)
-
-
-def test_f32_round_toward_zero():
-    """FP32 rounding toward zero: the result is a float no larger in magnitude
-    than x whose successor away from zero is larger than |x|; floats map to
-    themselves; tiny values flush to zero and huge ones become infinite."""
-    rng = np.random.default_rng(5)
-    x = rng.normal(0, 1, 20000) * 10.0 ** rng.uniform(-30, 30, 20000)
-    r = amr.f32_rz(x).astype(np.float64)
-    assert np.all(np.abs(r) <= np.abs(x))
-    nxt = np.nextafter(amr.f32_rz(x), np.copysign(np.float32(np.inf), x).astype(np.float32)).astype(np.float64)
-    assert np.all(np.abs(nxt) > np.abs(x))
-    f = rng.normal(0, 1, 1000).astype(np.float32)
-    assert np.array_equal(amr.f32_rz(f.astype(np.float64)), f)
-    assert np.array_equal(amr.f32_rz(np.array([1e-40, -1e-40, 1e40, -1e40])),
-                          np.array([0.0, -0.0, np.inf, -np.inf], dtype=np.float32))
 
 
 def test_a_level_can_empty_and_refill():

@@ -6,8 +6,10 @@ instead of a caller workspace.
 
 It must give the same result as enzo_ppm_sweep, the entry point that uses a
 caller workspace.  Both run the same kernel, so the FP64 and FP32 outputs must
-be bit-identical.  The check covers two calls in a row, so the second call
-starts from the scratch contents the first call left behind.  This file is
+be bit-identical: the fields, the status words, and where the batch carries
+them the flux registers and the gas energy; an FP32 tile size is honoured.
+The checks cover several calls in a row, so later calls start from the scratch
+contents an earlier call left behind.  This file is
 collected last, so a run that stops at the first failure has run every other
 test first.  It also passes on its own in a fresh process, because the first
 call sets the scratch up.
@@ -16,9 +18,11 @@ import ctypes
 
 import numpy as np
 import pytest
+import torch
 
 import paper_1307_2265_gb300 as ez
 from gpu_helpers import batch_from_patches, gpu_patches, white_patch
+from paper_1307_2265_gb300 import hierarchy as gh
 
 pytestmark = pytest.mark.gpu
 
@@ -51,8 +55,72 @@ def test_noalloc_sweep_matches_workspace_sweep_two_calls(precision, flags):
     assert with_ws.read_status() == no_ws.read_status()
 
 
+def _with_registers(batch, nc=5):
+    """Give every patch all-face and boundary-face flux registers (the layout
+    of a hierarchy level), zeroed."""
+    t = batch.table
+    a_sz, b_sz = gh.register_sizes(t["n"], nc)
+    t["freg_all"] = np.concatenate([[0], np.cumsum(a_sz)[:-1]])
+    t["freg_bnd"] = np.concatenate([[0], np.cumsum(b_sz)[:-1]]) + int(a_sz.sum())
+    batch.patches.copy_(torch.from_numpy(np.frombuffer(t.tobytes(), dtype=np.uint8).copy()).to(batch.device))
+    batch.freg = torch.zeros(int(a_sz.sum() + b_sz.sum()), dtype=torch.float64, device=batch.device)
+    return batch
+
+
+@pytest.mark.parametrize("precision", [ez.FP64, ez.FP32])
+def test_noalloc_writes_the_same_flux_registers(precision):
+    with_ws, no_ws = (_with_registers(b) for b in _pair(0, seed=950 + precision))
+    params = ez.Params(precision=precision)
+    ez.ghost_fill_periodic(with_ws)
+    ez.ghost_fill_periodic(no_ws)
+    dt = 0.4 * ez.timestep_cfl(with_ws, ez.Params(precision=ez.FP64, cfl=1.0))
+    for direction, cover in ((0, 6), (1, 4), (2, 0)):
+        ez.ppm_sweep(with_ws, direction, dt, cover, params)
+        ez.ppm_sweep_noalloc(no_ws, direction, dt, cover, params)
+    assert torch.count_nonzero(with_ws.freg) > 0
+    assert torch.equal(with_ws.freg, no_ws.freg)
+    for a, b in zip(gpu_patches(with_ws), gpu_patches(no_ws)):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_noalloc_dual_energy_and_fp32_tile():
+    """The gas energy of the dual-energy option, and an FP32 tile of 64 pencils."""
+    pairs = []
+    for opt in ("dual", "tile"):
+        w, n = _pair(ez.PATCH_PERIODIC, seed=970 if opt == "dual" else 980)
+        if opt == "dual":
+            for b in (w, n):
+                rho = torch.where(b.U[0] > 0, b.U[0], torch.ones_like(b.U[0]))   # ghost cells may be empty
+                rho_e = b.U[4] - 0.5 * (b.U[1] ** 2 + b.U[2] ** 2 + b.U[3] ** 2) / rho
+                b.ge = (rho_e * 1.01).contiguous()
+            params = ez.Params(precision=ez.FP32, options=ez.OPT_DUAL)
+        else:
+            params = ez.Params(precision=ez.FP32, tile=(64, 64, 64))
+        pairs.append((w, n, params))
+    for w, n, params in pairs:
+        dt = 0.4 * ez.timestep_cfl(w, ez.Params(precision=ez.FP64, cfl=1.0))
+        for direction in (2, 1, 0):
+            ez.ppm_sweep(w, direction, dt, 0, params)
+            ez.ppm_sweep_noalloc(n, direction, dt, 0, params)
+        for a, b in zip(gpu_patches(w), gpu_patches(n)):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
+        if w.ge is not None:
+            assert torch.equal(w.ge, n.ge)
+        assert w.read_status() == n.read_status()
+
+
 def test_noalloc_rejects_batches_above_the_limit():
     b = ez._Batch()
     b.npatch = 32001
     p = ez.Params().c()
     assert ez.lib().enzo_ppm_sweep_noalloc(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -3
+    assert b"fixed limit" in ez.lib().enzo_strerror(-3)
+
+
+def test_noalloc_rejects_a_bad_tile_like_the_workspace_sweep():
+    b = ez._Batch()
+    b.npatch = 0
+    p = ez.Params(precision=ez.FP32, tile=(48, 64, 64)).c()
+    assert ez.lib().enzo_ppm_sweep_noalloc(ctypes.byref(b), 0, 0.1, 0, ctypes.byref(p)) == -1
