@@ -507,6 +507,21 @@ int enzo_cluster_flags(const uint8_t *flags, const int32_t n[3], const enzo_clus
 int enzo_project(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_links,
                  const enzo_patch_batch *fine, const enzo_patch_link *fine_links, int32_t r);
 
+/* ---- measurement helper (not part of the method) ---- */
+
+/* Throughput probe of the FP64 pipe, the denominator of the FP64 sweep's ALU
+ * roofline.  Launches ENZO_PROBE_BLOCKS_PER_SM x (SM count) blocks of 256
+ * threads on `stream` (a cudaStream_t); each thread runs 8 independent chains
+ * of n steps of one operation: ENZO_PROBE_DFMA x = fma(x, a, b), _DADD x + b,
+ * _DMUL x * a, _DSQRT sqrt(x + b), _DDIV a / (x + b) (IEEE division and square
+ * root, as the FP64 path executes them).  *ops (HOST) receives the number of
+ * operations launched; the caller times the launch (CUDA events) and divides.
+ * sink: a DEVICE array of at least (blocks + 1) doubles the kernel may write.
+ * ENZO_ERR_ARG on a bad op, n < 1 or n > 2^30, or NULL pointers. */
+enum { ENZO_PROBE_DFMA = 0, ENZO_PROBE_DADD = 1, ENZO_PROBE_DMUL = 2, ENZO_PROBE_DSQRT = 3, ENZO_PROBE_DDIV = 4 };
+#define ENZO_PROBE_BLOCKS_PER_SM 4
+int enzo_probe_fp64(int32_t op, int64_t n, double *sink, int64_t *ops, void *stream);
+
 /* Text for an ENZO_ERR_* code (static storage). */
 const char *enzo_strerror(int code);
 

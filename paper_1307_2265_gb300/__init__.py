@@ -462,3 +462,23 @@ def mlp_features(rl, ul, pl, rr, ur, pr, gamma):
     _check(_mlp_lib().enzo_mlp_features(*[t.data_ptr() for t in ins], float(gamma), x.data_ptr(), n,
                                         _stream_ptr(ins[0].device)), "enzo_mlp_features")
     return x
+
+
+PROBE_DFMA, PROBE_DADD, PROBE_DMUL, PROBE_DSQRT, PROBE_DDIV = 0, 1, 2, 3, 4
+PROBE_BLOCKS_PER_SM = 4
+
+
+def probe_fp64(op: int, n: int, sink, stream=None) -> int:
+    """Launch the FP64-pipe throughput probe (enzo_probe_fp64) on `stream`;
+    returns the number of operations launched.  sink: a float64 CUDA tensor of
+    at least PROBE_BLOCKS_PER_SM x SMs + 1 elements.  The caller times it."""
+    L = lib()
+    if not getattr(L, "_probe_ready", False):
+        L.enzo_probe_fp64.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+        L.enzo_probe_fp64.restype = ctypes.c_int
+        L._probe_ready = True
+    ops = ctypes.c_int64(0)
+    st = stream.cuda_stream if stream is not None else _stream_ptr(sink.device)
+    _check(L.enzo_probe_fp64(op, n, sink.data_ptr(), ctypes.byref(ops), st), "enzo_probe_fp64")
+    return int(ops.value)

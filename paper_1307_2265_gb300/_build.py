@@ -10,6 +10,7 @@ Translation units and their flags:
   mlp.cu        learned p* guess: tcgen05 inference and training kernels
   amr.cu        hierarchy rebuild: cell flagging (FP64, --fmad=false) and the
                 host clustering of flags into new grids
+  probe.cu      FP64-pipe throughput probe (the FP64 sweep's roofline denominator)
 Objects go to paper_1307_2265_gb300/_build/, the library next to this file.
 """
 from __future__ import annotations
@@ -35,6 +36,7 @@ UNITS = {
     "mlp.cu": ["-use_fast_math"],
     "hierarchy.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     "amr.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
+    "probe.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
 }
 OPTIONAL_UNITS = {}
 

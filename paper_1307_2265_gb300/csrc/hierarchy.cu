@@ -82,33 +82,12 @@ __device__ __forceinline__ T second_order_a(const T Q[3][3][3], int kz, int ky, 
     return ((Q0 + cx * fx) + cy * fy) + cz * fz;
 }
 
-// float <-> double on the integer pipe (as in the FP32 sweep): round toward
-// zero into float, exact widening back.
-__device__ __forceinline__ float h_d2f(double x)
-{
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
-    const unsigned bits = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-    return __uint_as_float(e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : bits));
-}
-__device__ __forceinline__ double h_f2d(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    const unsigned sign = b & 0x80000000u;
-    const unsigned e = (b >> 23) & 0xffu;
-    const unsigned m = b & 0x7fffffu;
-    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
-    unsigned lo = m << 29;
-    hi = e == 0u ? sign : (e == 255u ? (sign | 0x7ff00000u | (m >> 3)) : hi);
-    lo = e == 0u ? 0u : lo;
-    return __hiloint2double((int)hi, (int)lo);
-}
+// float <-> double on the integer pipe (d2f_rz, f2d_exact: internal.cuh)
 __device__ __forceinline__ double to_d(double x) { return x; }
-__device__ __forceinline__ double to_d(float x) { return h_f2d(x); }
+__device__ __forceinline__ double to_d(float x) { return f2d_exact(x); }
 template <class T> __device__ __forceinline__ T from_d(double x);
 template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
-template <> __device__ __forceinline__ float from_d<float>(double x) { return h_d2f(x); }
+template <> __device__ __forceinline__ float from_d<float>(double x) { return d2f_rz(x); }
 
 __device__ __forceinline__ int floordiv2(int g) { return g >= 0 ? g / 2 : -((1 - g) / 2); }
 

@@ -150,18 +150,34 @@ void launch_tile_prefix(const enzo_patch *patches, int npatch, int64_t field_len
                         unsigned long long *status, cudaStream_t s, int tile_pencils = kSweepThreads);
 
 #ifdef __CUDACC__
-// double -> float on the integer pipe.  On GB300 the FP64 pipe retires 2
-// thread-operations per clock per SM (1/64 of FP32), and F2F conversions run
-// on it, so FP32 work converts with bit operations: round toward zero (error
-// below one FP32 ulp); values below the FP32 normal range flush to zero,
-// values above it (and NaN) become infinite.
+// float <-> double conversions on the integer pipe.  On GB300 the FP64 pipe
+// retires 2 thread-operations per clock per SM (1/64 of FP32) and F2F
+// conversions run on it, so FP32 work converts with bit operations.
+//
+// d2f_rz: double -> float rounded toward zero (error below one FP32 ulp): the
+// exponent is rebiased by 1023 - 127 = 896 in place and the top 23 mantissa
+// bits follow through a funnel shift; values below the FP32 normal range
+// flush to signed zero, values above it (and NaN) become signed infinity.
 __device__ __forceinline__ float d2f_rz(double x)
 {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
-    const unsigned bits = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-    return __uint_as_float(e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : bits));
+    const unsigned ah = hi & 0x7fffffffu;
+    const unsigned t = __funnelshift_l(lo, ah - 0x38000000u, 3);
+    const unsigned r = ah < 0x38100000u ? 0u : (ah >= 0x47f00000u ? 0x7f800000u : t);
+    return __uint_as_float(r | (hi & 0x80000000u));
+}
+
+// f2d_exact: float -> double, exact for normal floats, zero and infinity
+// (denormals are flushed to zero by -ftz before they get here; NaN keeps its
+// top payload bits).
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned a = b & 0x7fffffffu;
+    const unsigned mag = (a >> 3) + (a >= 0x7f800000u ? 0x70000000u : 0x38000000u);
+    const unsigned hi = (a < 0x00800000u ? 0u : mag) | (b & 0x80000000u);
+    const unsigned lo = a < 0x00800000u ? 0u : b << 29;
+    return __hiloint2double((int)hi, (int)lo);
 }
 #endif
 

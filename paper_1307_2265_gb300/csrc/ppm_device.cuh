@@ -38,6 +38,17 @@
 #include "mlp_layout.cuh"
 #include "tc05.cuh"
 
+// Cache prefetch of the march: a position's five fields are requested this
+// many steps before their load (0: off).
+#ifndef ENZO_PREFETCH_AHEAD
+#define ENZO_PREFETCH_AHEAD 2
+#endif
+#ifdef ENZO_PREFETCH_TO_L2
+#define ENZO_PREFETCH(p) asm volatile("prefetch.global.L2 [%0];" ::"l"(p))
+#else
+#define ENZO_PREFETCH(p) asm volatile("prefetch.global.L1 [%0];" ::"l"(p))
+#endif
+
 namespace enzo {
 
 template <class R>
@@ -104,22 +115,6 @@ __device__ __forceinline__ Zone<double> prim<double, false>(double rho, double m
 {
     Counters quiet;
     return prim<double, true>(rho, mn, m1, m2, E, k, quiet);
-}
-
-// float <-> double conversions on the integer pipe (d2f_rz: internal.cuh).
-// f2d is exact for normal and zero floats (denormals are already flushed by
-// -ftz).
-__device__ __forceinline__ double f2d_exact(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    const unsigned sign = b & 0x80000000u;
-    const unsigned e = (b >> 23) & 0xffu;
-    const unsigned m = b & 0x7fffffu;
-    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
-    unsigned lo = m << 29;
-    hi = e == 0u ? sign : (e == 255u ? (sign | 0x7ff00000u | (m >> 3)) : hi);
-    lo = e == 0u ? 0u : lo;
-    return __hiloint2double((int)hi, (int)lo);
 }
 
 template <bool COUNT>
@@ -298,8 +293,8 @@ __device__ __forceinline__ R avg_left(R qL, R d, R q6, R sig)
 // value; the others enter through beta corrections of the linearised
 // Lagrangian characteristic relations dp +- C du = 0, dp + C^2 d(1/rho) = 0.
 template <class R, int SIDE>
-__device__ __forceinline__ void trace(const R qL[5], const R qR[5], const R d[5], const R q6[5],
-                                      R u, R c, R dtdx, const Consts<R> &k, R out[5])
+__device__ __forceinline__ void trace_exact(const R qL[5], const R qR[5], const R d[5], const R q6[5],
+                                            R u, R c, R dtdx, const Consts<R> &k, R out[5])
 {
     const R lam0 = u - c, lam1 = u, lam2 = u + c;
     const bool r0 = SIDE > 0 ? lam0 > (R)0 : lam0 < (R)0;
@@ -341,6 +336,74 @@ __device__ __forceinline__ void trace(const R qL[5], const R qR[5], const R d[5]
     out[3] = r1 ? ENZO_I(s1, 3) : edge[3];
     out[4] = r1 ? ENZO_I(s1, 4) : edge[4];
 #undef ENZO_I
+}
+
+// The same characteristic state in FP32, arranged for fewer operations (the
+// FP32 path is bound by instruction issue).  Written for SIDE = +1 with
+// sg = +1, and mirrored through sg = -1:
+//   * a wave's domain fraction is sigma = max(sg lambda dt/dx, 0), so a wave
+//     moving away from the edge averages to the edge value itself;
+//   * the reference is the average over the fastest wave toward the edge
+//     (u + sg c), so that wave's own beta, which measures the difference of
+//     the reference and its own average, vanishes identically and is not
+//     formed; the slow acoustic wave (u - sg c) and the entropy wave (u)
+//     give beta_s = sg (1/2C) [(u_ref - I_s(u)) - sg (p_ref - I_s(p)) / C]
+//     and beta_0 = (p_ref - I_0(p)) / C^2 + 1/rho_ref - 1/I_0(rho), each only
+//     where its wave reaches the edge;
+//   * p = p_ref + C^2 beta_s, u = u_ref - sg C beta_s,
+//     1/rho = 1/rho_ref - (beta_s + beta_0), with 1/C from one reciprocal
+//     square root of C^2 = gamma p_ref rho_ref.
+template <int SIDE>
+__device__ __forceinline__ void trace_f(const float qL[5], const float qR[5], const float d[5],
+                                        const float q6[5], float u, float c, float dtdx,
+                                        const Consts<float> &k, float out[5])
+{
+    constexpr float sg = SIDE > 0 ? 1.0f : -1.0f;
+    const float *edge = SIDE > 0 ? qR : qL;
+    const float sdt = sg * dtdx;
+    const float sf = fmaxf((u + sg * c) * sdt, 0.0f);   // fastest wave toward the edge
+    const float s0 = fmaxf(u * sdt, 0.0f);              // entropy wave
+    const float ss = fmaxf((u - sg * c) * sdt, 0.0f);   // slow acoustic wave
+    // average over a fraction s next to the edge: edge - sg (s/2) (d - sg (1 - 2s/3) q6)
+    const float af = -sg * 0.5f * sf, bf = -sg * fmaf(-2.0f / 3.0f, sf, 1.0f);
+    const float a0 = -sg * 0.5f * s0, b0c = -sg * fmaf(-2.0f / 3.0f, s0, 1.0f);
+    const float as = -sg * 0.5f * ss, bs = -sg * fmaf(-2.0f / 3.0f, ss, 1.0f);
+#define ENZO_AVG(A, B, V) fmaf((A), fmaf((B), q6[V], d[V]), edge[V])
+    float rho_ref = ENZO_AVG(af, bf, 0);
+    const float u_ref = ENZO_AVG(af, bf, 1);
+    float p_ref = ENZO_AVG(af, bf, 2);
+    rho_ref = rho_ref > k.rho_floor ? rho_ref : k.rho_floor;
+    p_ref = p_ref > k.p_floor ? p_ref : k.p_floor;
+    const float C2 = k.gamma * p_ref * rho_ref;
+    const float iC = rsqrtf(C2);
+    const float C = C2 * iC;
+    const float irho = 1.0f / rho_ref;
+    float bsl = 0.0f, b0 = 0.0f;
+    if (ss > 0.0f) {
+        const float du = u_ref - ENZO_AVG(as, bs, 1), dp = p_ref - ENZO_AVG(as, bs, 2);
+        bsl = (sg * 0.5f * iC) * fmaf(-sg * dp, iC, du);
+    }
+    if (s0 > 0.0f) {
+        const float dp = p_ref - ENZO_AVG(a0, b0c, 2);
+        b0 = fmaf(dp, iC * iC, irho) - 1.0f / ENZO_AVG(a0, b0c, 0);
+    }
+    float p = fmaf(C2, bsl, p_ref);
+    const float un = fmaf(-sg * C, bsl, u_ref);
+    float rho = 1.0f / (irho - (bsl + b0));
+    out[0] = rho > k.rho_floor ? rho : k.rho_floor;
+    out[1] = un;
+    out[2] = p > k.p_floor ? p : k.p_floor;
+    out[3] = ENZO_AVG(a0, b0c, 3);
+    out[4] = ENZO_AVG(a0, b0c, 4);
+#undef ENZO_AVG
+}
+
+template <class R, int SIDE>
+__device__ __forceinline__ void trace(const R qL[5], const R qR[5], const R d[5], const R q6[5],
+                                      R u, R c, R dtdx, const Consts<R> &k, R out[5])
+{
+    if constexpr (std::is_same<R, float>::value) trace_f<SIDE>(qL, qR, d, q6, u, c, dtdx, k, out);
+    else trace_exact<R, SIDE>(qL, qR, d, q6, u, c, dtdx, k, out);
 }
 
 // A passive variable (eps of the dual-energy option) traced to one edge of its
@@ -412,10 +475,99 @@ struct RiemannOut {
     bool conv;
 };
 
+// FP32 two-shock solve (Sec. 4.1.2): the method of riemann_exact below,
+// arranged for the FP32 pipe.  With rad_s = 1 + (gamma+1)/(2 gamma)(p*/p_s - 1)
+// and r_s = rad_s^{-1/2}: W_s = C_s sqrt(rad_s), so 1/W_s = r_s / C_s, and
+// Z_s = 2 W_s^3 / (W_s^2 + C_s^2) = 2 C_s rad_s^{3/2} / (1 + rad_s), so
+// 1/Z_s = (r_s / (2 C_s)) (1 + r_s^2).  One reciprocal square root per side
+// and iteration therefore gives the star velocities u*_L = u_L - (p* - p_L)/W_L,
+// u*_R = u_R + (p* - p_R)/W_R and the Newton step f / (1/Z_L + 1/Z_R), and
+// u* = (Z_L u*_L + Z_R u*_R)/(Z_L + Z_R) = (u*_L/Z_R + u*_R/Z_L)/(1/Z_L + 1/Z_R).
+// The loop keeps the side quantities of the iterate it accepts, so the star
+// state needs no second evaluation: it stops when |f| meets the tolerance, or
+// when the next step is below step_tol p* (the iterate is then within that
+// step of the root).  A learned start that reaches the iteration cap restarts
+// once from the plain guess inside the same loop.  The upwind side alone is
+// sampled.
+__device__ __forceinline__ RiemannOut<float> riemann_f(float rl, float ul, float pl, float rr, float ur, float pr,
+                                                      float pguess, const Consts<float> &k, Counters &cnt)
+{
+    const float C2L = k.gamma * pl * rl, C2R = k.gamma * pr * rr;
+    const float iCL = rsqrtf(C2L), iCR = rsqrtf(C2R);
+    const float ipl = 1.0f / pl, ipr = 1.0f / pr;
+    float plain, ftol;
+    {
+        const float CL = C2L * iCL, CR = C2R * iCR;
+        // |u*_R - u*_L| <= tol (|u_L| + |u_R| + c_L + c_R), c = C / rho
+        ftol = k.tol * ((fabsf(ul) + fabsf(ur)) + (CL / rl + CR / rr));
+        plain = (CR * pl + CL * pr + CL * CR * (ul - ur)) / (CL + CR);
+        plain = plain > k.p_floor ? plain : k.p_floor;
+    }
+    float ps = pguess > 0.0f ? (pguess > k.p_floor ? pguess : k.p_floor) : plain;
+    float rsL, rsR, usL, usR, izL, izR;
+    int it = 0, lim = k.nmax;
+    bool conv = false, restarted = pguess <= 0.0f;
+    for (;;) {
+        if (it >= lim) {
+            // a learned start that does not converge restarts once from the plain guess
+            if (restarted) break;
+            restarted = true;
+            cnt.restarts++;
+            ps = plain;
+            lim += k.nmax;
+        }
+        const float radL = fmaxf(fmaf(k.gp1o2g, fmaf(ps, ipl, -1.0f), 1.0f), 1e-6f);
+        const float radR = fmaxf(fmaf(k.gp1o2g, fmaf(ps, ipr, -1.0f), 1.0f), 1e-6f);
+        rsL = rsqrtf(radL);
+        rsR = rsqrtf(radR);
+        const float iWL = rsL * iCL, iWR = rsR * iCR;
+        usL = fmaf(pl - ps, iWL, ul);
+        usR = fmaf(ps - pr, iWR, ur);
+        izL = iWL * fmaf(0.5f * rsL, rsL, 0.5f);
+        izR = iWR * fmaf(0.5f * rsR, rsR, 0.5f);
+        const float f = usR - usL;
+        if (fabsf(f) <= ftol) { conv = true; break; }
+        float pn = ps - f / (izL + izR);
+        pn = pn > k.p_floor ? pn : k.p_floor;
+        ++it;
+        if (fabsf(pn - ps) <= k.step_tol * pn) { conv = true; break; }
+        ps = pn;
+    }
+    RiemannOut<float> o;
+    o.iters = it;
+    o.conv = conv;
+    const float us = (usL * izR + usR * izL) / (izL + izR);
+    o.ustar = us;
+    o.pstar = ps;
+    // sample x/t = 0 on the side upwind of the contact: sg = +1 left, -1 right;
+    // w is the weight of the star state (0 outside the wave, 1 inside, linear in
+    // the head/tail speed fraction across a transonic rarefaction)
+    const bool left = us >= 0.0f;
+    const float sg = left ? 1.0f : -1.0f;
+    const float r_s = left ? rl : rr, u_s = left ? ul : ur, p_s = left ? pl : pr;
+    const float iW = left ? rsL * iCL : rsR * iCR;              // 1 / W
+    const float ir_s = 1.0f / r_s;
+    float rs_st = 1.0f / fmaf(p_s - ps, iW * iW, ir_s);          // 1/rho* = 1/rho - (p* - p)/W^2
+    rs_st = rs_st > k.rho_floor ? rs_st : k.rho_floor;
+    const float Sshock = u_s - sg * ir_s / iW;                   // shock speed u -+ W / rho
+    const float c_s = sqrtf(k.gamma * p_s * ir_s);
+    const float c_st = sqrtf(k.gamma * ps / rs_st);
+    const float Sh = u_s - sg * c_s;
+    const float St = us - sg * c_st;
+    const float fr = -Sh / (St - Sh);
+    const float w_rare = sg * Sh >= 0.0f ? 0.0f : (sg * St <= 0.0f ? 1.0f : fr);
+    const float w_shock = sg * Sshock >= 0.0f ? 0.0f : 1.0f;
+    const float w = ps > p_s ? w_shock : w_rare;
+    o.rho = fmaf(w, rs_st - r_s, r_s);
+    o.u = fmaf(w, us - u_s, u_s);
+    o.p = fmaf(w, ps - p_s, p_s);
+    return o;
+}
+
 // Two-shock solve and sampling of the self-similar solution at x/t = 0.
 template <class R>
-__device__ __forceinline__ RiemannOut<R> riemann(R rl, R ul, R pl, R rr, R ur, R pr, R pguess,
-                                                 const Consts<R> &k, Counters &cnt)
+__device__ __forceinline__ RiemannOut<R> riemann_exact(R rl, R ul, R pl, R rr, R ur, R pr, R pguess,
+                                                       const Consts<R> &k, Counters &cnt)
 {
     RiemannOut<R> o;
     R ps;
@@ -447,32 +599,6 @@ __device__ __forceinline__ RiemannOut<R> riemann(R rl, R ul, R pl, R rr, R ur, R
     o.ustar = us;
     o.pstar = ps;
     R rho, u, p;
-    if (sizeof(R) == 4) {
-        // FP32: the same sampling rule without divergent branches.  sg = +1
-        // samples the left side (contact moving right), -1 the right side; w is
-        // the weight of the star state (0 outside the wave, 1 inside, linear in
-        // the head/tail speed fraction across a transonic rarefaction).
-        const bool left = us >= (R)0;
-        const R sg = left ? (R)1 : (R)-1;
-        const R r_s = left ? rl : rr, u_s = left ? ul : ur, p_s = left ? pl : pr;
-        const R W_s = left ? WL : WR, rs_s = left ? rsL : rsR;
-        const R Sshock = u_s - sg * W_s / r_s;
-        const R c_s = sqrt(k.gamma * p_s / r_s);
-        const R c_st = sqrt(k.gamma * ps / rs_s);
-        const R Sh = u_s - sg * c_s;
-        const R St = us - sg * c_st;
-        const R fr = -Sh / (St - Sh);
-        const R w_rare = sg * Sh >= (R)0 ? (R)0 : (sg * St <= (R)0 ? (R)1 : fr);
-        const R w_shock = sg * Sshock >= (R)0 ? (R)0 : (R)1;
-        const R w = ps > p_s ? w_shock : w_rare;
-        rho = r_s + w * (rs_s - r_s);
-        u = u_s + w * (us - u_s);
-        p = p_s + w * (ps - p_s);
-        o.rho = rho;
-        o.u = u;
-        o.p = p;
-        return o;
-    }
     if (us >= (R)0) {
         if (ps > pl) {
             const R S = ul - WL / rl;
@@ -516,6 +642,14 @@ __device__ __forceinline__ RiemannOut<R> riemann(R rl, R ul, R pl, R rr, R ur, R
     o.u = u;
     o.p = p;
     return o;
+}
+
+template <class R>
+__device__ __forceinline__ RiemannOut<R> riemann(R rl, R ul, R pl, R rr, R ur, R pr, R pguess,
+                                                 const Consts<R> &k, Counters &cnt)
+{
+    if constexpr (std::is_same<R, float>::value) return riemann_f(rl, ul, pl, rr, ur, pr, pguess, k, cnt);
+    else return riemann_exact<R>(rl, ul, pl, rr, ur, pr, pguess, k, cnt);
 }
 
 // Physical flux of the split 1-D equations (Sec. 4.1): mass, normal momentum,
@@ -645,12 +779,23 @@ struct alignas(1024) GuessSmem {
     unsigned char a1[128 * 16 * 2];  // A of layer 1: features
     unsigned char a2[128 * 80 * 2];  // A of layer 2: layer-1 activations
     float4 ring[2][128][3];          // per thread: traced states (sL, sR) of two march steps
-    float w3[64];
+    __half2 w3h[32];                 // output unit weights as FP16 pairs (w3_2i, w3_2i+1)
     float b3;
     int err;
     uint64_t mbar;
     uint32_t tmem;
 };
+
+// SiLU of two accumulator values in FP16 (h = z/2; z sigmoid(z) = h + h tanh(h)),
+// then their terms of the output unit's dot product added into acc.
+__device__ __forceinline__ __half2 silu_dot_f16x2(float h0, float h1, __half2 w, __half2 acc)
+{
+    const __half2 h = __floats2half2_rn(h0, h1);
+    uint32_t tb;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(tb) : "r"(*reinterpret_cast<const uint32_t *>(&h)));
+    const __half2 sl = __hfma2(h, *reinterpret_cast<const __half2 *>(&tb), h);
+    return __hfma2(w, sl, acc);
+}
 
 // SiLU of two accumulator values holding h = z/2: z sigmoid(z) = h + h tanh(h).
 __device__ __forceinline__ uint32_t silu_half_bf16x2(float h0, float h1)
@@ -687,8 +832,8 @@ struct LearnedGuess {
     bool committed;      // products issued by the previous call (CTA-uniform)
     bool any1, any2;     // layer 1 / layer 2 in flight for the interfaces 1 / 2 calls back
     bool need1, need2;   // this thread's interface 1 / 2 calls back passed the gate
-    float s1, s2;        // sqrt(pL pR) of those interfaces
-    float gamma;
+    float s1, s2;        // log2 sqrt(pL pR) of those interfaces
+    float gamma, rsqg;   // gamma and 1/sqrt(gamma)
     float gate, gate2g;  // jump-strength gate (< 0: always) and gate^2 gamma
 
     __device__ void setup(unsigned char *raw, const void *blob, float g, double gate_)
@@ -718,7 +863,7 @@ struct LearnedGuess {
             const int r = i >> 4, k = 64 + (i & 15);
             *reinterpret_cast<unsigned short *>(S->a2 + tc::tile_off(r, k, 80)) = k == 64 ? 0x3F80u : 0u;
         }
-        for (int i = threadIdx.x; i < 64; i += blockDim.x) S->w3[i] = bvec[128 + i];
+        for (int i = threadIdx.x; i < 32; i += blockDim.x) S->w3h[i] = __floats2half2_rn(bvec[128 + 2 * i], bvec[129 + 2 * i]);
         if (threadIdx.x == 0) {
             S->b3 = bvec[192];
             S->err = 0;
@@ -734,6 +879,7 @@ struct LearnedGuess {
         committed = any1 = any2 = need1 = need2 = false;
         s1 = s2 = 0.0f;
         gamma = g;
+        rsqg = rsqrtf(g);
         gate = (float)gate_;
         gate2g = gate * gate * g;
     }
@@ -764,20 +910,20 @@ struct LearnedGuess {
         }
         float p0 = -1.0f;
         if (any2) {
-            // output unit of the interface two calls back
-            float y0 = S->b3, y1 = 0.0f;
+            // output unit of the interface two calls back: SiLU and the dot
+            // product in packed FP16, one partial sum per 16 units, summed in FP32
+            float y = S->b3;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 float v[16];
                 tc::tmem_ld16(S->tmem + lane + 64 + c * 16, v);
+                __half2 acc = __float2half2_rn(0.0f);
 #pragma unroll
-                for (int i = 0; i < 16; i += 2) {
-                    const uint32_t o = silu_half_bf16x2(v[i], v[i + 1]);
-                    y0 = fmaf(S->w3[c * 16 + i], __uint_as_float(o << 16), y0);
-                    y1 = fmaf(S->w3[c * 16 + i + 1], __uint_as_float(o & 0xFFFF0000u), y1);
-                }
+                for (int i = 0; i < 8; ++i) acc = silu_dot_f16x2(v[2 * i], v[2 * i + 1], S->w3h[c * 8 + i], acc);
+                const float2 a = __half22float2(acc);
+                y += a.x + a.y;
             }
-            if (need2) p0 = s2 * __expf(y0 + y1);
+            if (need2) p0 = exp2f(fmaf(y, 1.44269504f, s2));   // sqrt(p_L p_R) e^y
         }
         if (any1) {
             // layer-1 activations of the interface one call back
@@ -801,8 +947,25 @@ struct LearnedGuess {
         // features of the new interface (column 6 carries the bias)
         const float psum = pl + pr, du = ul - ur;
         const bool need = valid && (gate < 0.0f || fabsf(pl - pr) > gate * psum || du * du * (rl + rr) > gate2g * psum);
+        // the features of mlp_features from four base-2 logarithms: with
+        // l = log2 of rho_L, rho_R, p_L, p_R, ln(rho_L/rho_ref) = (ln 2 / 2)(l_rL - l_rR),
+        // ln(p_L/p_ref) likewise, and 1/c_ref = 2^(-(l_pL + l_pR - l_rL - l_rR)/4) / sqrt(gamma)
         float x[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (need) mlp_features(rl, ul, pl, rr, ur, pr, gamma, x);
+        float lgp = 0.0f;                       // log2 sqrt(p_L p_R)
+        if (need) {
+            const float lrl = __log2f(rl), lrr = __log2f(rr), lpl = __log2f(pl), lpr = __log2f(pr);
+            constexpr float hln2 = 0.34657359f;   // ln 2 / 2
+            const float a = hln2 * (lrl - lrr), b = hln2 * (lpl - lpr);
+            lgp = 0.5f * (lpl + lpr);
+            const float icref = exp2f(0.25f * ((lrl + lrr) - (lpl + lpr))) * rsqg;
+            const float du2 = 0.5f * du * icref;
+            x[0] = a;
+            x[1] = du2;
+            x[2] = b;
+            x[3] = -a;
+            x[4] = -du2;
+            x[5] = -b;
+        }
         {
             uint4 lo;
             const __nv_bfloat162 x01 = __floats2bfloat162_rn(x[0], x[1]);
@@ -843,7 +1006,7 @@ struct LearnedGuess {
         need2 = need1;
         need1 = need;
         s2 = s1;
-        s1 = need ? sqrtf(pl * pr) : 0.0f;
+        s1 = lgp;
         return p0;
     }
 };
@@ -862,8 +1025,49 @@ struct Marcher {
     double *reg_all;      // this pencil's all-face flux register row, or nullptr
     double *reg_bnd;      // this pencil's boundary-face register pair, or nullptr
     double dt64;
-    Zone<R> c0, c1, c2;   // WRAP: initial state of the first three active cells
-    R ce0, ce1, ce2;      // WRAP with dual energy: their initial eps
+    // WRAP: the initial state of the first three active cells (and their eps
+    // with dual energy), which the trailing ghost positions reuse after the
+    // pencil has updated those cells.  FP32 keeps them in shared memory (the
+    // kernel's per-thread slots, stride kSave), FP64 in registers.
+    float *wsave;
+    static constexpr int kSave = 7;   // r, u, p, t1, t2, c, eps
+    // Plain FP32 march: the raw FP64 values (rho, m_n, m_t1, m_t2, E) of the
+    // last kRingSlots positions, in shared memory ([slot][field] x blockDim.x,
+    // this thread's column), so the update of a cell four steps after its load
+    // and the fallback test read them there instead of going back to L2.
+    double *uring;
+    static constexpr int kRingSlots = 5;
+    __device__ __forceinline__ double &ring(int s, int f) const
+    {
+        return uring[((s % kRingSlots) * 5 + f) * (int)blockDim.x];
+    }
+    Zone<R> c0, c1, c2;
+    R ce0, ce1, ce2;
+
+    __device__ __forceinline__ void save(int t, const Zone<R> &z, R e)
+    {
+        if constexpr (sizeof(R) == 4) {
+            float *o = wsave + t * kSave * blockDim.x;
+            const float v[kSave] = {z.r, z.u, z.p, z.t1, z.t2, z.c, e};
+            _Pragma("unroll") for (int i = 0; i < kSave; ++i) o[i * blockDim.x] = v[i];
+        } else {
+            if (t == 0) { c0 = z; ce0 = e; }
+            else if (t == 1) { c1 = z; ce1 = e; }
+            else { c2 = z; ce2 = e; }
+        }
+    }
+    __device__ __forceinline__ Zone<R> saved(int t, R &e) const
+    {
+        if constexpr (sizeof(R) == 4) {
+            const float *o = wsave + t * kSave * blockDim.x;
+            e = o[6 * blockDim.x];
+            return Zone<R>{o[0], o[blockDim.x], o[2 * blockDim.x], o[3 * blockDim.x], o[4 * blockDim.x],
+                           o[5 * blockDim.x]};
+        } else {
+            e = t == 0 ? ce0 : (t == 1 ? ce1 : ce2);
+            return t == 0 ? c0 : (t == 1 ? c1 : c2);
+        }
+    }
 
     // Dual energy: gas-energy flux and interface velocity of one face.
     struct GeFace {
@@ -892,6 +1096,53 @@ struct Marcher {
 
     __device__ __forceinline__ const double *F(int f) const { return a.U[f]; }
 
+    // Storage index of pencil position s (the stored cell or its periodic
+    // image); -1 for a trailing wrapped ghost, whose zone is a saved one.
+    __device__ __forceinline__ int64_t index_of(int s) const
+    {
+        if (WRAP) {
+            const int j = s - pc.ng;
+            if (j >= pc.n) return -1;
+            return pc.at(pc.ng + (j < 0 ? (pc.n - ((-j) % pc.n)) % pc.n : j));
+        }
+        return pc.at(s);
+    }
+
+    // Ask the memory system for the five fields of pencil position s ahead of
+    // their load (a cache prefetch: no registers are held), so that the load
+    // a few march steps later hits the cache instead of waiting for HBM.
+    __device__ __forceinline__ void warm(int s) const
+    {
+        // x pencils walk their own rows, which the cache lines they already
+        // loaded cover 16 positions at a time
+        if (ENZO_PREFETCH_AHEAD == 0 || DIR == 0 || s >= pc.L) return;
+        const int64_t idx = index_of(s);
+        if (idx < 0) return;
+        ENZO_PREFETCH(a.U[0] + idx);
+        ENZO_PREFETCH(a.U[1] + idx);
+        ENZO_PREFETCH(a.U[2] + idx);
+        ENZO_PREFETCH(a.U[3] + idx);
+        ENZO_PREFETCH(a.U[4] + idx);
+    }
+
+    // Zone at pencil position s, its raw values also kept in the ring.
+    __device__ __forceinline__ Zone<R> zone_keep(int s, Counters &cnt)
+    {
+        const int64_t idx = index_of(s);
+        if (idx < 0) {
+            R e;
+            return saved((s - pc.ng - pc.n) % pc.n, e);
+        }
+        const double v0 = __ldg(a.U[0] + idx), v1 = __ldg(a.U[1 + DIR] + idx), v2 = __ldg(a.U[1 + A1] + idx),
+                     v3 = __ldg(a.U[1 + A2] + idx), v4 = __ldg(a.U[4] + idx);
+        ring(s, 0) = v0;
+        ring(s, 1) = v1;
+        ring(s, 2) = v2;
+        ring(s, 3) = v3;
+        ring(s, 4) = v4;
+        return prim<R, true>(v0, v1, v2, v3, v4, k, cnt);
+    }
+
     // Zone at pencil position s, before any update of this sweep.
     template <bool COUNT>
     __device__ __forceinline__ Zone<R> zone(int s, Counters &cnt)
@@ -902,8 +1153,8 @@ struct Marcher {
             if (j >= pc.n) {
                 // trailing ghost: image of active cell (j - n) mod n, which this
                 // pencil may already have updated, so its initial state is kept
-                const int t = (j - pc.n) % pc.n;
-                return t == 0 ? c0 : (t == 1 ? c1 : c2);
+                R e;
+                return saved((j - pc.n) % pc.n, e);
             }
             const int jj = j < 0 ? (pc.n - ((-j) % pc.n)) % pc.n : j;
             idx = pc.at(pc.ng + jj);
@@ -925,9 +1176,7 @@ struct Marcher {
         if (WRAP) {
             const int j = s - pc.ng;
             if (j >= pc.n) {
-                const int t = (j - pc.n) % pc.n;
-                eps = t == 0 ? ce0 : (t == 1 ? ce1 : ce2);
-                return t == 0 ? c0 : (t == 1 ? c1 : c2);
+                return saved((j - pc.n) % pc.n, eps);
             }
             const int jj = j < 0 ? (pc.n - ((-j) % pc.n)) % pc.n : j;
             idx = pc.at(pc.ng + jj);
@@ -983,13 +1232,19 @@ struct Marcher {
     }
 
     // Density of cell s at the start of the sweep (raw, no floor).
-    __device__ __forceinline__ double rho_old(int s) const { return a.U[0][pc.at(s)]; }
+    template <bool RING = false>
+    __device__ __forceinline__ double rho_old(int s) const
+    {
+        if constexpr (RING) return ring(s, 0);
+        else return a.U[0][pc.at(s)];
+    }
 
     // Write the final state of active cell s given its two face terms.  With
     // dual energy (gm, gp non-null) also the gas energy: its flux difference
     // and the source -p (u_{s+1/2} - u_{s-1/2}) dt/dx with the zone pressure pz;
     // the cell then becomes the pending one, and the previous pending cell,
     // whose right neighbour this is, is resynchronised and written.
+    template <bool RING = false>
     __device__ __forceinline__ void update(int s, const R Fm[5], const R Fp[5], double dtdx64,
                                            const double Gm[5], const double Gp[5], bool fb,
                                            Counters &cnt, const GeFace *gm = nullptr,
@@ -1000,7 +1255,7 @@ struct Marcher {
         const int map[5] = {0, 1 + DIR, 1 + A1, 1 + A2, 4};
         _Pragma("unroll") for (int v = 0; v < 5; ++v)
         {
-            const double U = a.U[map[v]][idx];
+            const double U = RING ? ring(s, v) : a.U[map[v]][idx];
             if (sizeof(R) == 8) u[v] = cell_update(U, dtdx64, (double)Fm[v], (double)Fp[v]);
             else u[v] = (U + Gm[v]) - Gp[v];
         }
@@ -1176,6 +1431,7 @@ struct Marcher {
     template <class GS>
     __device__ void run(R dtdx, double dtdx64, const MethodParams &mp, Counters &cnt, GS &guess)
     {
+        constexpr bool RING = sizeof(R) == 4 && EXT == 0;   // the shared-memory ring of raw values
         const int L = pc.L;
         const bool fb = mp.fallback != 0;
         Zone<R> zm2, zm1, z0;                 // zones k-2, k-1, k
@@ -1221,13 +1477,16 @@ struct Marcher {
             }
             zm2 = zm1;
             zm1 = z0;
-            if (dual) z0 = zone_dual<true>(kk, cnt, e0);
-            else z0 = zone<true>(kk, cnt);
+            if (dual) {
+                z0 = zone_dual<true>(kk, cnt, e0);
+            } else {
+                warm(kk + ENZO_PREFETCH_AHEAD);
+                if constexpr (RING) z0 = zone_keep(kk, cnt);
+                else z0 = zone<true>(kk, cnt);
+            }
             if (WRAP) {
                 const int j = kk - pc.ng;
-                if (j == 0) { c0 = z0; ce0 = e0; }
-                else if (j == 1) { c1 = z0; ce1 = e0; }
-                else if (j == 2) { c2 = z0; ce2 = e0; }
+                if (j >= 0 && j < 3) save(j, z0, e0);
             }
             if (sizeof(R) == 4) {
                 rho3 = rho2;
@@ -1313,14 +1572,14 @@ struct Marcher {
                                     bad = (sizeof(R) == 8 || dual || !clearly_ok(zm3, Fgprev, Fg, dtdx))
                                               ? fails_full(c, Fgprev, Fg, dtdx, dtdx64) : false;
                                 } else if (sizeof(R) == 8) {
-                                    bad = !(cell_update(rho_old(c), dtdx64, (double)Fgprev[0], (double)Fg[0]) > 0.0);
+                                    bad = !(cell_update(rho_old<RING>(c), dtdx64, (double)Fgprev[0], (double)Fg[0]) > 0.0);
                                 } else {
                                     // FP32 screen; cells near zero are decided in FP64
                                     const R rt = rho3 + dtdx * (Fgprev[0] - Fg[0]);
                                     if (!(rt > (R)1e-3 * rho3)) {
                                         const double g0 = f2d_exact((float)(dtdx * Fgprev[0]));
                                         const double g1 = f2d_exact((float)(dtdx * Fg[0]));
-                                        bad = !((rho_old(c) + g0) - g1 > 0.0);
+                                        bad = !((rho_old<RING>(c) + g0) - g1 > 0.0);
                                     }
                                 }
                                 if (bad && active) cnt.rare(ENZO_ST_HLL_CELLS);
@@ -1338,8 +1597,8 @@ struct Marcher {
                                 record(kk - 6, Fu1, G1, gfin.F, sizeof(R) == 4 ? f2d_exact((float)(dtdx * gfin.F)) : 0.0);
                             else record(kk - 6, Fu1, G1);
                             if (kk >= 7)
-                                update(kk - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt, dual ? &gfin2 : nullptr,
-                                       &gfin, p4, dtdx);
+                                update<RING>(kk - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt,
+                                             dual ? &gfin2 : nullptr, &gfin, p4, dtdx);
                             gfin2 = gfin;
                             _Pragma("unroll") for (int v = 0; v < 5; ++v)
                             {
@@ -1374,7 +1633,7 @@ struct Marcher {
             record(pc.n, Fu1, G1, gfin.F, sizeof(R) == 4 ? f2d_exact((float)(dtdx * gfin.F)) : 0.0);
         else record(pc.n, Fu1, G1);
         // the pressure of zone L-4 is the last window's zone k-3
-        update(L - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt, dual ? &gfin2 : nullptr, &gfin, zm3.p, dtdx);
+        update<RING>(L - 4, Fuprev2, Fu1, dtdx64, Gprev2, G1, fb, cnt, dual ? &gfin2 : nullptr, &gfin, zm3.p, dtdx);
         if (dual) ge_commit(Eghost_right);
     }
 
@@ -1432,12 +1691,11 @@ struct Marcher {
             if (kk < L) {
                 zm2 = zm1;
                 zm1 = z0;
+                warm(kk + ENZO_PREFETCH_AHEAD);
                 z0 = zone<true>(kk, cnt);
                 if (WRAP) {
                     const int j = kk - pc.ng;
-                    if (j == 0) c0 = z0;
-                    else if (j == 1) c1 = z0;
-                    else if (j == 2) c2 = z0;
+                    if (j >= 0 && j < 3) save(j, z0, (R)0);
                 }
             }
             if (sizeof(R) == 4) {
@@ -1573,6 +1831,14 @@ __device__ __forceinline__ void warp_flush(unsigned long long *status, unsigned 
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(status + word, v);
 }
 
+// Dynamic shared memory of a plain (not learned) sweep kernel: the FP32
+// default kernels keep the raw values of their last five positions there.
+template <class R, int THREADS, int EXT>
+__host__ __device__ constexpr int ring_bytes()
+{
+    return (sizeof(R) == 4 && EXT == 0) ? 5 * 5 * THREADS * (int)sizeof(double) : 0;
+}
+
 // Persistent sweep kernel: CTAs take (patch, 128-pencil tile) work items from a
 // device counter until the batch is exhausted.  DIR is the sweep axis.
 #ifndef ENZO_SWEEP_MIN_BLOCKS_FP32
@@ -1592,7 +1858,12 @@ __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? (EXT 
 {
     constexpr int A1 = DIR == 0 ? 1 : 0, A2 = DIR == 2 ? 1 : 2;
     __shared__ int s_tile;
-    extern __shared__ unsigned char dsmem[];
+    // FP32: per-thread slots for the wrapped pencils' first three cells
+    __shared__ float s_wrap[sizeof(R) == 4 ? 3 * 7 * THREADS : 1];
+    extern __shared__ __align__(16) unsigned char dsmem[];
+    // plain FP32 default kernels: the ring of raw values in dynamic shared memory
+    double *uring = nullptr;
+    if constexpr (ring_bytes<R, THREADS, EXT>() > 0 && !LEARNED) uring = reinterpret_cast<double *>(dsmem) + threadIdx.x;
     Counters cnt;
     cnt.st = a.status;
     const Consts<R> k = make_consts<R>(a.mp);
@@ -1654,11 +1925,11 @@ __global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? (EXT 
             }
         }
         if (P.flags & ENZO_PATCH_PERIODIC) {
-            Marcher<R, true, DIR, REG, EXT> m{a, pc, k, valid, key, reg_all, reg_bnd, dt};
+            Marcher<R, true, DIR, REG, EXT> m{a, pc, k, valid, key, reg_all, reg_bnd, dt, s_wrap + threadIdx.x, uring};
             if constexpr (LEARNED) m.run_piped(dtdx, dtdx64, a.mp, cnt, guess);
             else m.run(dtdx, dtdx64, a.mp, cnt, guess);
         } else {
-            Marcher<R, false, DIR, REG, EXT> m{a, pc, k, valid, key, reg_all, reg_bnd, dt};
+            Marcher<R, false, DIR, REG, EXT> m{a, pc, k, valid, key, reg_all, reg_bnd, dt, s_wrap + threadIdx.x, uring};
             if constexpr (LEARNED) m.run_piped(dtdx, dtdx64, a.mp, cnt, guess);
             else m.run(dtdx, dtdx64, a.mp, cnt, guess);
         }
@@ -1772,6 +2043,22 @@ __global__ void __launch_bounds__(256) riemann_kernel(const __grid_constant__ Ri
     if (a.iters) a.iters[i] = o.conv ? o.iters : -o.iters;
 }
 
+// Allow a plain kernel's ring above the 48 KB default (256-pencil tiles), once
+// per device.
+template <class R, int DIR, int THREADS, bool REG>
+cudaError_t ring_prepare(int dev)
+{
+    constexpr int bytes = ring_bytes<R, THREADS, 0>();
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static bool done[64] = {false};
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (done[dev]) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(ppm_sweep_kernel<R, DIR, false, THREADS, REG>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
 template <class R>
 int sweep_grid_for(int device)
 {
@@ -1780,7 +2067,8 @@ int sweep_grid_for(int device)
     if (cached[device]) return cached[device];
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<R, 0, false>, kSweepThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<R, 0, false>, kSweepThreads,
+                                                  ring_bytes<R, kSweepThreads, 0>());
     if (sms < 1) sms = 1;
     if (per < 1) per = 1;
     cached[device] = sms * per;
@@ -1795,7 +2083,9 @@ int tiled_grid(int device)
     if (cached[device]) return cached[device];
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<R, 0, false, THREADS>, THREADS, 0);
+    ring_prepare<R, 0, THREADS, false>(device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ppm_sweep_kernel<R, 0, false, THREADS>, THREADS,
+                                                  ring_bytes<R, THREADS, 0>());
     cached[device] = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
     return cached[device];
 }
@@ -1806,11 +2096,23 @@ cudaError_t launch_tiled(const SweepArgs &a, cudaStream_t s)
     int dev = 0;
     cudaGetDevice(&dev);
     const int grid = tiled_grid<R, THREADS>(dev);
+    constexpr int smem = ring_bytes<R, THREADS, 0>();
+    cudaError_t e = cudaSuccess;
     switch (a.dir) {
-    case 0: ppm_sweep_kernel<R, 0, false, THREADS><<<grid, THREADS, 0, s>>>(a); break;
-    case 1: ppm_sweep_kernel<R, 1, false, THREADS><<<grid, THREADS, 0, s>>>(a); break;
-    default: ppm_sweep_kernel<R, 2, false, THREADS><<<grid, THREADS, 0, s>>>(a); break;
+    case 0:
+        e = ring_prepare<R, 0, THREADS, false>(dev);
+        if (e == cudaSuccess) ppm_sweep_kernel<R, 0, false, THREADS><<<grid, THREADS, smem, s>>>(a);
+        break;
+    case 1:
+        e = ring_prepare<R, 1, THREADS, false>(dev);
+        if (e == cudaSuccess) ppm_sweep_kernel<R, 1, false, THREADS><<<grid, THREADS, smem, s>>>(a);
+        break;
+    default:
+        e = ring_prepare<R, 2, THREADS, false>(dev);
+        if (e == cudaSuccess) ppm_sweep_kernel<R, 2, false, THREADS><<<grid, THREADS, smem, s>>>(a);
+        break;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1871,18 +2173,19 @@ cudaError_t launch_sweep_dir(const SweepArgs &a, int grid, cudaStream_t s)
         }
         return cudaGetLastError();
     }
+    constexpr int smem = ring_bytes<R, kSweepThreads, 0>();
     if (a.freg) {
         switch (a.dir) {
-        case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, true><<<grid, kSweepThreads, 0, s>>>(a); break;
-        case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, true><<<grid, kSweepThreads, 0, s>>>(a); break;
-        default: ppm_sweep_kernel<R, 2, false, kSweepThreads, true><<<grid, kSweepThreads, 0, s>>>(a); break;
+        case 0: ppm_sweep_kernel<R, 0, false, kSweepThreads, true><<<grid, kSweepThreads, smem, s>>>(a); break;
+        case 1: ppm_sweep_kernel<R, 1, false, kSweepThreads, true><<<grid, kSweepThreads, smem, s>>>(a); break;
+        default: ppm_sweep_kernel<R, 2, false, kSweepThreads, true><<<grid, kSweepThreads, smem, s>>>(a); break;
         }
         return cudaGetLastError();
     }
     switch (a.dir) {
-    case 0: ppm_sweep_kernel<R, 0, false><<<grid, kSweepThreads, 0, s>>>(a); break;
-    case 1: ppm_sweep_kernel<R, 1, false><<<grid, kSweepThreads, 0, s>>>(a); break;
-    default: ppm_sweep_kernel<R, 2, false><<<grid, kSweepThreads, 0, s>>>(a); break;
+    case 0: ppm_sweep_kernel<R, 0, false><<<grid, kSweepThreads, smem, s>>>(a); break;
+    case 1: ppm_sweep_kernel<R, 1, false><<<grid, kSweepThreads, smem, s>>>(a); break;
+    default: ppm_sweep_kernel<R, 2, false><<<grid, kSweepThreads, smem, s>>>(a); break;
     }
     return cudaGetLastError();
 }

@@ -129,13 +129,19 @@ def test_blast_grid_512_learned_and_plain(trained):
 def test_config3_full_level_sampled_patches_match_the_oracle():
     """The batched level at full size (4000 self-periodic patches of 8..64
     cells per axis, 1.89e8 cells), in the bench's launch configuration: one
-    persistent launch per sweep over the whole level, the FP32 + learned step
-    replayed from a CUDA graph.  The level dt is the oracle's CFL rule over
-    every patch (the GPU's FP64 reduction gives the same value).  On sampled
-    patches (the first, the last, the largest, the smallest and four seeded
-    ones), which the oracle steps one by one with that dt: the FP64 step is
-    bit-identical, the FP32 + learned step within L1 1e-4 per field."""
+    persistent launch per sweep over the whole level, the FP32 + learned steps
+    replayed from CUDA graphs.  Sampled patches (the first, the last, the
+    largest, the smallest and four seeded ones) are stepped by the oracle one
+    by one with the same level dt:
+      * one FP64 step (dt from the oracle's CFL rule over every patch, which
+        the GPU's FP64 reduction reproduces) is bit-identical;
+      * K = 5 FP32 + learned steps, each with the dt the GPU's CFL rule gives
+        on its own state, are within the FP32 rule of the other configurations
+        over the sampled cells: per-field L1 relative error <= max(4 x floor,
+        2e-6) and <= 1e-4, the floor being the L1 spread of two oracle runs
+        whose inputs differ by 2^-24 relative noise."""
     import torch
+    K = 5
     sizes = synth.patch_sizes(4000, config=3)
     sizes, offsets, flat = synth.batched_level(4000, config=3, sizes=sizes)
     dx = [1.0 / 64] * 3
@@ -148,9 +154,10 @@ def test_config3_full_level_sampled_patches_match_the_oracle():
     rng = np.random.default_rng(77)
     sample = sorted({0, len(sizes) - 1, int(np.argmax(cells)), int(np.argmin(cells)),
                      *rng.choice(len(sizes), 4, replace=False).tolist()})
+    init = {i: [synth.patch_view(f, offsets[i], sizes[i]).copy() for f in flat] for i in sample}
     ref = {}
     for i in sample:
-        U = [synth.patch_view(f, offsets[i], sizes[i]).copy() for f in flat]
+        U = [f.copy() for f in init[i]]
         oracle.step_periodic(U, dx, dt, 0, P)
         ref[i] = U
     stream = torch.cuda.Stream()
@@ -183,20 +190,50 @@ def test_config3_full_level_sampled_patches_match_the_oracle():
         for d in (0, 1, 2):
             ez.ppm_sweep_dev(batch, d, batch.dt_dev, 0, pml)
     stream.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=stream):
-        for d in (0, 1, 2):
-            ez.ppm_sweep_dev(batch, d, batch.dt_dev, 0, pml)
+    graphs = []
+    for order in ((0, 1, 2), (2, 1, 0)):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for d in order:
+                ez.ppm_sweep_dev(batch, d, batch.dt_dev, 0, pml)
+        graphs.append(g)
     reset()
     batch.reset_status()
-    with torch.cuda.stream(stream):
-        batch.dt_dev.fill_(dt)
-        g.replay()
+    dts = []
+    for s in range(K):
+        with torch.cuda.stream(stream):
+            dts.append(ez.timestep_cfl(batch, ez.Params(gamma=G, cfl=0.4, precision=ez.FP64)))
+            batch.dt_dev.fill_(dts[-1])
+            graphs[s % 2].replay()
     stream.synchronize()
     assert batch.read_status()["nan"] == 0
-    for i in sample:
-        for f, (a, b) in enumerate(zip(batch.patch_fields(i), ref[i])):
-            A = a.cpu().numpy()[3:-3, 3:-3, 3:-3]
-            B = b[3:-3, 3:-3, 3:-3]
-            l1 = float(np.sum(np.abs(A - B)) / np.sum(np.abs(B)))
-            assert l1 <= 1e-4, (i, f, l1)
+
+    def evolve(start):
+        out = {}
+        for i in sample:
+            U = [f.copy() for f in start[i]]
+            for s, dts_ in enumerate(dts):
+                oracle.step_periodic(U, dx, dts_, s, P)
+            out[i] = U
+        return out
+
+    base = evolve(init)
+    noise = np.random.default_rng(78)
+    pert = evolve({i: [f * (1.0 + 2.0 ** -24 * noise.standard_normal(f.shape)) for f in init[i]] for i in sample})
+
+    def l1(a_of, b_of):
+        num, den = np.zeros(5), np.zeros(5)
+        for i in sample:
+            for f in range(5):
+                A = a_of(i, f)[3:-3, 3:-3, 3:-3]
+                B = base[i][f][3:-3, 3:-3, 3:-3]
+                num[f] += np.sum(np.abs(A - B))
+                den[f] += np.sum(np.abs(B))
+        return num / den
+
+    got = {i: [a.cpu().numpy() for a in batch.patch_fields(i)] for i in sample}
+    err = l1(lambda i, f: got[i][f], None)
+    floor = l1(lambda i, f: pert[i][f], None)
+    print(f"config 3, {K} FP32 + learned steps, sampled cells: L1 {err.tolist()}, floor {floor.tolist()}")
+    for e, fl in zip(err, floor):
+        assert e <= max(4.0 * fl, 2e-6) and e <= 1e-4, (err, floor)
