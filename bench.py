@@ -204,21 +204,26 @@ def fp64_probe(stream):
     sms = props.multi_processor_count
     sink = torch.zeros(sms * ez.PROBE_BLOCKS_PER_SM + 1, dtype=torch.float64, device="cuda")
     out = {}
-    for name, op, n in (("dfma", ez.PROBE_DFMA, 2048), ("dadd", ez.PROBE_DADD, 2048), ("dmul", ez.PROBE_DMUL, 2048),
-                        ("dsqrt", ez.PROBE_DSQRT, 128), ("ddiv", ez.PROBE_DDIV, 128)):
-        with torch.cuda.stream(stream):
-            ez.probe_fp64(op, 16, sink, stream)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ops = ez.probe_fp64(op, n, sink, stream)
-            e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        out[name] = {"ops_per_s": ops / (ms * 1e-3), "ms": ms, "ops": ops}
-    mx = _max_sm_mhz()
+    clk = ClockSampler(_clocks_path() + ".probe")
+    with clk:
+        # DFMA for about a second (clock samples every 200 ms), the others briefly
+        for name, op, n, reps in (("dfma", ez.PROBE_DFMA, 4096, 100), ("dadd", ez.PROBE_DADD, 2048, 1),
+                                  ("dmul", ez.PROBE_DMUL, 2048, 1), ("dsqrt", ez.PROBE_DSQRT, 128, 1),
+                                  ("ddiv", ez.PROBE_DDIV, 128, 1)):
+            with torch.cuda.stream(stream):
+                ez.probe_fp64(op, 16, sink, stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ops = sum(ez.probe_fp64(op, n, sink, stream) for _ in range(reps))
+                e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[name] = {"ops_per_s": ops / (ms * 1e-3), "ms": ms, "ops": ops}
+    c = clk.summary(_env_int("LOCAL_RANK", 0)) or {}
+    mhz = c.get("sm_mhz") or _max_sm_mhz()
     for v in out.values():
-        v["per_sm_per_clock_at_max"] = v["ops_per_s"] / (sms * mx * 1e6)
-    out["sms"], out["sm_max_mhz"] = sms, mx
+        v["per_sm_per_clock"] = v["ops_per_s"] / (sms * mhz * 1e6)
+    out["sms"], out["sm_mhz"], out["clocks"] = sms, mhz, c
     return out
 
 

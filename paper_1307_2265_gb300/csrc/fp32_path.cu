@@ -21,18 +21,18 @@ static cudaError_t launch_learned_dir(const SweepArgs &a, cudaStream_t s)
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    const size_t smem = sizeof(GuessSmem) + 1024;
+    const size_t smem = sizeof(GuessSmem) + 128;
     if (!grid[dev]) {
         cudaError_t e = cudaFuncSetAttribute(ppm_sweep_kernel<float, DIR, true, kSweepThreads, REG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        // 3 CTAs per SM: the launch bounds cap registers for 3, TMEM holds
-        // 4 x 128 columns and shared memory 6 x GuessSmem.  (The occupancy
-        // query reported 1 here; a CTA that cannot be resident yet only starts
-        // later and finds fewer tiles, since tiles come from a counter.)
+        // ENZO_LEARNED_CTAS CTAs per SM: the launch bounds cap registers for
+        // that many and TMEM holds 4 x 128 columns.  (A CTA that cannot be
+        // resident yet only starts later and finds fewer tiles, since tiles
+        // come from a counter.)
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid[dev] = (sms > 0 ? sms : 1) * 3;
+        grid[dev] = (sms > 0 ? sms : 1) * ENZO_LEARNED_CTAS;
     }
     ppm_sweep_kernel<float, DIR, true, kSweepThreads, REG><<<grid[dev], kSweepThreads, smem, s>>>(a);
     return cudaGetLastError();

@@ -43,6 +43,9 @@
 #ifndef ENZO_PREFETCH_AHEAD
 #define ENZO_PREFETCH_AHEAD 2
 #endif
+#ifndef ENZO_NEWTON_HEAD
+#define ENZO_NEWTON_HEAD 3   // FP32 Newton: evaluations done as straight-line code before the loop
+#endif
 #ifdef ENZO_PREFETCH_TO_L2
 #define ENZO_PREFETCH(p) asm volatile("prefetch.global.L2 [%0];" ::"l"(p))
 #else
@@ -507,6 +510,37 @@ __device__ __forceinline__ RiemannOut<float> riemann_f(float rl, float ul, float
     float rsL, rsR, usL, usR, izL, izR;
     int it = 0, lim = k.nmax;
     bool conv = false, restarted = pguess <= 0.0f;
+#if ENZO_NEWTON_HEAD > 0
+    // the first ENZO_NEWTON_HEAD evaluations as straight-line code: each lane
+    // keeps its accepted iterate once it has converged, so the steps after
+    // that re-evaluate the same p* and change nothing
+#pragma unroll
+    for (int h = 0; h < ENZO_NEWTON_HEAD; ++h) {
+        const float radL = fmaxf(fmaf(k.gp1o2g, fmaf(ps, ipl, -1.0f), 1.0f), 1e-6f);
+        const float radR = fmaxf(fmaf(k.gp1o2g, fmaf(ps, ipr, -1.0f), 1.0f), 1e-6f);
+        rsL = rsqrtf(radL);
+        rsR = rsqrtf(radR);
+        const float iWL = rsL * iCL, iWR = rsR * iCR;
+        usL = fmaf(pl - ps, iWL, ul);
+        usR = fmaf(ps - pr, iWR, ur);
+        izL = iWL * fmaf(0.5f * rsL, rsL, 0.5f);
+        izR = iWR * fmaf(0.5f * rsR, rsR, 0.5f);
+        const float f = usR - usL;
+        float pn = ps - f / (izL + izR);
+        pn = pn > k.p_floor ? pn : k.p_floor;
+        const bool fconv = fabsf(f) <= ftol;
+        const bool sconv = fabsf(pn - ps) <= k.step_tol * pn;
+        if (!conv) {
+            if (fconv) conv = true;
+            else {
+                ++it;
+                if (sconv) conv = true;
+                else ps = pn;
+            }
+        }
+    }
+    if (!conv)
+#endif
     for (;;) {
         if (it >= lim) {
             // a learned start that does not converge restarts once from the plain guess
@@ -772,8 +806,10 @@ struct PlainGuess {
 // Operands, as the sweep keeps them: both layers' weights pre-scaled by 1/2 (so
 // the accumulators hold h = z/2, the argument SiLU needs) and both biases folded
 // into the products through an input column held at 1 (column 6 of the 16
-// feature columns; column 64 of the 80 activation columns).
-struct alignas(1024) GuessSmem {
+// feature columns; column 64 of the 80 activation columns).  (Adding layer 2's
+// bias in FP16 before the SiLU instead, with K = 64, measured slower.)
+// No-swizzle K-major tiles need 16-byte alignment; 128 is kept.
+struct alignas(128) GuessSmem {
     unsigned char w1[64 * 16 * 2];   // B of layer 1: 64 units x 16 inputs
     unsigned char w2[64 * 80 * 2];   // B of layer 2: 64 units x (64 + 16) inputs
     unsigned char a1[128 * 16 * 2];  // A of layer 1: features
@@ -838,7 +874,7 @@ struct LearnedGuess {
 
     __device__ void setup(unsigned char *raw, const void *blob, float g, double gate_)
     {
-        S = reinterpret_cast<GuessSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+        S = reinterpret_cast<GuessSmem *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
         const unsigned char *b = static_cast<const unsigned char *>(blob);
         const float *bvec = reinterpret_cast<const float *>(b + kBlobF32);   // b1, b2, w3, b3
         // layer 1: inputs 0..5 from the blob (already 16-column tiles), column 6 = b1
@@ -923,6 +959,7 @@ struct LearnedGuess {
                 const float2 a = __half22float2(acc);
                 y += a.x + a.y;
             }
+
             if (need2) p0 = exp2f(fmaf(y, 1.44269504f, s2));   // sqrt(p_L p_R) e^y
         }
         if (any1) {
@@ -1030,7 +1067,7 @@ struct Marcher {
     // pencil has updated those cells.  FP32 keeps them in shared memory (the
     // kernel's per-thread slots, stride kSave), FP64 in registers.
     float *wsave;
-    static constexpr int kSave = 7;   // r, u, p, t1, t2, c, eps
+    static constexpr int kSave = EXT == 2 ? 7 : 6;   // r, u, p, t1, t2, c (and eps with dual energy)
     // Plain FP32 march: the raw FP64 values (rho, m_n, m_t1, m_t2, E) of the
     // last kRingSlots positions, in shared memory ([slot][field] x blockDim.x,
     // this thread's column), so the update of a cell four steps after its load
@@ -1048,7 +1085,7 @@ struct Marcher {
     {
         if constexpr (sizeof(R) == 4) {
             float *o = wsave + t * kSave * blockDim.x;
-            const float v[kSave] = {z.r, z.u, z.p, z.t1, z.t2, z.c, e};
+            const float v[7] = {z.r, z.u, z.p, z.t1, z.t2, z.c, e};
             _Pragma("unroll") for (int i = 0; i < kSave; ++i) o[i * blockDim.x] = v[i];
         } else {
             if (t == 0) { c0 = z; ce0 = e; }
@@ -1060,7 +1097,7 @@ struct Marcher {
     {
         if constexpr (sizeof(R) == 4) {
             const float *o = wsave + t * kSave * blockDim.x;
-            e = o[6 * blockDim.x];
+            e = EXT == 2 ? o[6 * blockDim.x] : 0.0f;
             return Zone<R>{o[0], o[blockDim.x], o[2 * blockDim.x], o[3 * blockDim.x], o[4 * blockDim.x],
                            o[5 * blockDim.x]};
         } else {
@@ -1670,6 +1707,12 @@ struct Marcher {
         float4 *ring = guess.S->ring[0][threadIdx.x];
         const int ring_stride = kSweepThreads * 3;     // float4 between the two slots
         const int L = pc.L;
+        if (!__any_sync(0xffffffffu, active)) {
+            // a warp of stand-in rows only takes part in the network's hand-off
+            // (one call per march step, as the marching warps make)
+            for (int kk = 5; kk < L + D; ++kk) guess.pipe(false, 1.0f, 0.0f, 1.0f, 1.0f, 0.0f, 1.0f);
+            return;
+        }
         const bool fb = mp.fallback != 0;
         Zone<R> zm2, zm1, z0;                 // zones k-2, k-1, k
         R dprev[5], qfprev[5], sLprev[5];
@@ -1844,6 +1887,9 @@ __host__ __device__ constexpr int ring_bytes()
 #ifndef ENZO_SWEEP_MIN_BLOCKS_FP32
 #define ENZO_SWEEP_MIN_BLOCKS_FP32 4   // 128 registers per thread: 16 warps per SM
 #endif
+#ifndef ENZO_LEARNED_CTAS
+#define ENZO_LEARNED_CTAS 3            // learned guess: CTAs per SM (TMEM holds 4 x 128 columns)
+#endif
 #ifndef ENZO_SWEEP_MIN_BLOCKS_DUAL
 #define ENZO_SWEEP_MIN_BLOCKS_DUAL 3   // dual energy (FP32): 168 registers per thread
 #endif
@@ -1853,13 +1899,13 @@ __host__ __device__ constexpr int ring_bytes()
 // REG: the batch has flux registers (hierarchy levels); the per-pencil register
 // rows are then tracked, otherwise the recording compiles away.
 template <class R, int DIR, bool LEARNED, int THREADS = kSweepThreads, bool REG = false, int EXT = 0>
-__global__ void __launch_bounds__(THREADS, LEARNED ? 3 : (sizeof(R) == 4 ? (EXT == 2 ? ENZO_SWEEP_MIN_BLOCKS_DUAL : ENZO_SWEEP_MIN_BLOCKS_FP32 * 128 / THREADS) : 2))
+__global__ void __launch_bounds__(THREADS, LEARNED ? ENZO_LEARNED_CTAS : (sizeof(R) == 4 ? (EXT == 2 ? ENZO_SWEEP_MIN_BLOCKS_DUAL : ENZO_SWEEP_MIN_BLOCKS_FP32 * 128 / THREADS) : 2))
     ppm_sweep_kernel(const __grid_constant__ SweepArgs a)
 {
     constexpr int A1 = DIR == 0 ? 1 : 0, A2 = DIR == 2 ? 1 : 2;
     __shared__ int s_tile;
     // FP32: per-thread slots for the wrapped pencils' first three cells
-    __shared__ float s_wrap[sizeof(R) == 4 ? 3 * 7 * THREADS : 1];
+    __shared__ float s_wrap[sizeof(R) == 4 ? 3 * (EXT == 2 ? 7 : 6) * THREADS : 1];
     extern __shared__ __align__(16) unsigned char dsmem[];
     // plain FP32 default kernels: the ring of raw values in dynamic shared memory
     double *uring = nullptr;
