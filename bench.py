@@ -145,6 +145,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class _Range:
+    """An NVTX range around a leg of the bench, so a profiler can pick its
+    kernels (ncu --nvtx --nvtx-include "name/")."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        import torch
+        torch.cuda.nvtx.range_push(self.name)
+
+    def __exit__(self, *a):
+        import torch
+        torch.cuda.nvtx.range_pop()
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -339,7 +355,7 @@ def run_gpu(args, rank, world):
 
     # --- headline: batched FP32 + learned guess, graph replay
     clk = ClockSampler(_clocks_path())
-    with clk:
+    with clk, _Range("headline"):
         ms, graphs = timed_graph(pml, args.steps, args.warmup)
     ms = max_over_ranks(ms, world)
     status_ml = batch.read_status()
@@ -350,7 +366,7 @@ def run_gpu(args, rank, world):
     reset()
     ksw = max(2, min(args.steps, 4))
     evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)] for _ in range(ksw)]
-    with torch.cuda.stream(stream):
+    with torch.cuda.stream(stream), _Range("headline_sweeps"):
         for s in range(ksw):
             one_step(pml, s, evs[s])
     stream.synchronize()
@@ -358,13 +374,14 @@ def run_gpu(args, rank, world):
 
     # --- plain FP32 (autotuned tiles), graph replay
     reset()
-    ms32, graphs = timed_graph(p32, args.steps, 1)
+    with _Range("fp32_plain"):
+        ms32, graphs = timed_graph(p32, args.steps, 1)
     status_32 = batch.read_status()
     del graphs
 
     # --- plain FP64 batched sweep on the same level (ALU bound: one step)
     reset()
-    with torch.cuda.stream(stream):
+    with torch.cuda.stream(stream), _Range("fp64_plain"):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         one_step(p64, 1)

@@ -178,6 +178,13 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const unsigned char *_
 // ---------------------------------------------------------------------------
 // training
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 struct alignas(1024) TrainSmem {
     FwdSmem f;
     unsigned char w2t[64 * 64 * 2];          // B of dH1 = dZ2 W2: rows in, cols out
@@ -186,7 +193,7 @@ struct alignas(1024) TrainSmem {
     unsigned char bh1[64 * 128 * 2];         // B of dW2: rows in, cols sample (H1^T)
     unsigned char adw1[128 * 128 * 2];       // A of dW1: rows hidden (64 used), cols sample (dZ1^T)
     unsigned char bx[16 * 128 * 2];          // B of dW1: rows input (6 used), cols sample (X^T)
-    float gsmall[4 * 64 + 4];                // db1, db2, dw3, db3 partial sums
+    float gsmall[4 * 64 + 4];                // (unused), db2, dw3, db3 partial sums
     float loss;
 };
 
@@ -235,8 +242,11 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(const unsigned char *__r
 #pragma unroll
         for (int k = 0; k < kMlpIn; ++k) xi[k] = valid ? x[r * kMlpIn + k] : 0.0f;
         write_a1_row(S, xi);
+        // X^T for dW1, with input column 6 held at 1 for valid rows: its column
+        // of dW1 = dZ1^T X is then sum_r dz1[r][j], the gradient of b1
 #pragma unroll
-        for (int k = 0; k < 16; ++k) st_bf16(T.bx, tile_off(k, row, 128), k < kMlpIn ? xi[k] : 0.0f);
+        for (int k = 0; k < 16; ++k)
+            st_bf16(T.bx, tile_off(k, row, 128), k < kMlpIn ? xi[k] : (k == kMlpIn && valid ? 1.0f : 0.0f));
         // forward; keep H1^T for dW2
         float z2[64];
         {
@@ -256,13 +266,18 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(const unsigned char *__r
             for (int c = 0; c < 4; ++c) {
                 float v[16];
                 tmem_ld16(S.tmem + lane_off + kTZ1 + c * 16, v);
+                uint32_t pk[8];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
+                for (int i = 0; i < 16; i += 2) {
                     const int j = c * 16 + i;
-                    const float h = silu(v[i] + S.bias[j]);
-                    st_bf16(S.a2, tile_off(row, j, 64), h);
-                    st_bf16(T.bh1, tile_off(j, row, 128), valid ? h : 0.0f);
+                    const float h0 = silu(v[i] + S.bias[j]), h1 = silu(v[i + 1] + S.bias[j + 1]);
+                    const __nv_bfloat162 hp = __floats2bfloat162_rn(h0, h1);
+                    pk[i / 2] = *reinterpret_cast<const uint32_t *>(&hp);
+                    st_bf16(T.bh1, tile_off(j, row, 128), valid ? h0 : 0.0f);
+                    st_bf16(T.bh1, tile_off(j + 1, row, 128), valid ? h1 : 0.0f);
                 }
+                *reinterpret_cast<uint4 *>(S.a2 + tile_off(row, c * 16, 64)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4 *>(S.a2 + tile_off(row, c * 16 + 8, 64)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
             fence_async_smem();
             fence_before();
@@ -293,15 +308,34 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(const unsigned char *__r
         const float e = valid ? yv - target[r] : 0.0f;
         lsum += e * e;
         const float dy = 2.0f * e * inv_n;
-        atomicAdd(&T.gsmall[192], dy);
+        // sums over the tile's rows (db3, dw3, db2): reduced across the warp with
+        // shuffles, then one shared-memory add per warp (the 128 rows of a tile
+        // adding into the same 64 words would serialise)
+        const bool lead = (row & 31) == 0;
+        const float sdy = warp_sum(dy);
+        if (lead) atomicAdd(&T.gsmall[192], sdy);
 #pragma unroll
-        for (int j = 0; j < 64; ++j) {
-            const float h2 = silu(z2[j]);
-            const float dz2 = dy * S.bias[128 + j] * silu_grad(z2[j]);
-            atomicAdd(&T.gsmall[128 + j], dy * h2);      // dw3
-            atomicAdd(&T.gsmall[64 + j], dz2);           // db2
-            st_bf16(T.ad2, tile_off(row, j, 64), dz2);
-            st_bf16(T.adw2, tile_off(j, row, 128), dz2);
+        for (int j8 = 0; j8 < 64; j8 += 8) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+                float d[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = j8 + i + h;
+                    const float h2 = silu(z2[j]);
+                    d[h] = dy * S.bias[128 + j] * silu_grad(z2[j]);
+                    const float s3 = warp_sum(dy * h2), s2 = warp_sum(d[h]);
+                    if (lead) {
+                        atomicAdd(&T.gsmall[128 + j], s3);      // dw3
+                        atomicAdd(&T.gsmall[64 + j], s2);       // db2
+                    }
+                    st_bf16(T.adw2, tile_off(j, row, 128), d[h]);
+                }
+                const __nv_bfloat162 dp = __floats2bfloat162_rn(d[0], d[1]);
+                pk[i / 2] = *reinterpret_cast<const uint32_t *>(&dp);
+            }
+            *reinterpret_cast<uint4 *>(T.ad2 + tile_off(row, j8, 64)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
         // dH1 = dZ2 W2 and dW2 += dZ2^T H1
         fence_async_smem();
@@ -333,8 +367,7 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(const unsigned char *__r
             for (int i = 0; i < 16; ++i) {
                 const int j = c * 16 + i;
                 const float dz1 = valid ? dh[i] * silu_grad(z1[i] + S.bias[j]) : 0.0f;
-                atomicAdd(&T.gsmall[j], dz1);            // db1
-                st_bf16(T.adw1, tile_off(j, row, 128), dz1);
+                st_bf16(T.adw1, tile_off(j, row, 128), dz1);   // db1 comes with dW1
             }
         }
         fence_async_smem();
@@ -373,6 +406,7 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(const unsigned char *__r
         if (row < 64) {
 #pragma unroll
             for (int k = 0; k < kMlpIn; ++k) atomicAdd(&grad[kMW1 + row * kMlpIn + k], v[k]);
+            atomicAdd(&grad[kMB1 + row], v[kMlpIn]);    // the column of ones
         }
     }
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
@@ -381,7 +415,6 @@ __global__ void __launch_bounds__(128) mlp_train_kernel(const unsigned char *__r
     __syncthreads();
     if (!S.error) {
         if (row < 64) {
-            atomicAdd(&grad[kMB1 + row], T.gsmall[row]);
             atomicAdd(&grad[kMB2 + row], T.gsmall[64 + row]);
             atomicAdd(&grad[kMW3 + row], T.gsmall[128 + row]);
         }
