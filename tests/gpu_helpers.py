@@ -81,3 +81,17 @@ def white_patch(n, seed, mach=1.0, sigma=0.5, gamma=5.0 / 3.0):
     nx, ny, nz = n
     prims = synth.white_noise_prims(rng, (nz, ny, nx), sigma=sigma, mach=mach, gamma=gamma)
     return [synth.embed(f) for f in synth.prims_to_conserved(*prims, gamma)]
+
+
+def with_registers(batch, nc=5):
+    """Give every patch all-face and boundary-face flux registers (the layout
+    of a hierarchy level), zeroed."""
+    import torch
+    from paper_1307_2265_gb300 import hierarchy as gh
+    tab = batch.table
+    a_sz, b_sz = gh.register_sizes(tab["n"], nc)
+    tab["freg_all"] = np.concatenate([[0], np.cumsum(a_sz)[:-1]])
+    tab["freg_bnd"] = np.concatenate([[0], np.cumsum(b_sz)[:-1]]) + int(a_sz.sum())
+    batch.patches.copy_(torch.from_numpy(np.frombuffer(tab.tobytes(), dtype=np.uint8).copy()).to(batch.device))
+    batch.freg = torch.zeros(int(a_sz.sum() + b_sz.sum()), dtype=torch.float64, device=batch.device)
+    return batch

@@ -21,8 +21,7 @@ import pytest
 import torch
 
 import paper_1307_2265_gb300 as ez
-from gpu_helpers import batch_from_patches, gpu_patches, white_patch
-from paper_1307_2265_gb300 import hierarchy as gh
+from gpu_helpers import batch_from_patches, gpu_patches, white_patch, with_registers
 
 pytestmark = pytest.mark.gpu
 
@@ -55,21 +54,9 @@ def test_noalloc_sweep_matches_workspace_sweep_two_calls(precision, flags):
     assert with_ws.read_status() == no_ws.read_status()
 
 
-def _with_registers(batch, nc=5):
-    """Give every patch all-face and boundary-face flux registers (the layout
-    of a hierarchy level), zeroed."""
-    t = batch.table
-    a_sz, b_sz = gh.register_sizes(t["n"], nc)
-    t["freg_all"] = np.concatenate([[0], np.cumsum(a_sz)[:-1]])
-    t["freg_bnd"] = np.concatenate([[0], np.cumsum(b_sz)[:-1]]) + int(a_sz.sum())
-    batch.patches.copy_(torch.from_numpy(np.frombuffer(t.tobytes(), dtype=np.uint8).copy()).to(batch.device))
-    batch.freg = torch.zeros(int(a_sz.sum() + b_sz.sum()), dtype=torch.float64, device=batch.device)
-    return batch
-
-
 @pytest.mark.parametrize("precision", [ez.FP64, ez.FP32])
 def test_noalloc_writes_the_same_flux_registers(precision):
-    with_ws, no_ws = (_with_registers(b) for b in _pair(0, seed=950 + precision))
+    with_ws, no_ws = (with_registers(b) for b in _pair(0, seed=950 + precision))
     params = ez.Params(precision=precision)
     ez.ghost_fill_periodic(with_ws)
     ez.ghost_fill_periodic(no_ws)
