@@ -21,7 +21,7 @@ static cudaError_t launch_learned_dir(const SweepArgs &a, cudaStream_t s)
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    const size_t smem = sizeof(GuessSmem) + 128;
+    const size_t smem = learned_smem_bytes<DIR>();
     if (!grid[dev]) {
         cudaError_t e = cudaFuncSetAttribute(ppm_sweep_kernel<float, DIR, true, kSweepThreads, REG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

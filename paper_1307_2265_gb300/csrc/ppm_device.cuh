@@ -1094,9 +1094,14 @@ struct Marcher {
     double *uring;
     static constexpr int kRingSlots = DIR == 0 ? 5 : 8;
     static constexpr int kStage = 3;
+    // Learned march (y and z): no room for the update's ring beside the
+    // network's shared memory, only for the loads: positions k..k+2, staged
+    // two steps ahead, after the network's shared memory.
+    static constexpr int kLearnedSlots = 3;
+    template <int SLOTS = kRingSlots>
     __device__ __forceinline__ double &ring(int s, int f) const
     {
-        return uring[((s % kRingSlots) * 5 + f) * (int)blockDim.x];
+        return uring[((s % SLOTS) * 5 + f) * (int)blockDim.x];
     }
     Zone<R> c0, c1, c2;
     R ce0, ce1, ce2;
@@ -1183,9 +1188,10 @@ struct Marcher {
     }
 
     // Start the asynchronous copy of pencil position s's five raw values into
-    // its ring slot (nothing for a trailing wrapped ghost or past the pencil's
-    // end), as one commit group of this thread.  A warp's 32 copies of one
-    // field are 32 consecutive doubles in y and z sweeps.
+    // its slot of a SLOTS-slot ring (nothing for a trailing wrapped ghost or
+    // past the pencil's end), as one commit group of this thread.  A warp's 32
+    // copies of one field are 32 consecutive doubles in y and z sweeps.
+    template <int SLOTS = kRingSlots>
     __device__ __forceinline__ void stage(int s) const
     {
         if (s < pc.L) {
@@ -1195,7 +1201,7 @@ struct Marcher {
                                         a.U[4] + idx};
                 _Pragma("unroll") for (int f = 0; f < 5; ++f)
                 {
-                    const unsigned dst = (unsigned)__cvta_generic_to_shared(&ring(s, f));
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(&ring<SLOTS>(s, f));
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src[f]) : "memory");
                 }
             }
@@ -1204,15 +1210,17 @@ struct Marcher {
     }
 
     // Zone at pencil position s from its ring slot, once its copy has landed
-    // (the kStage groups committed after it may still be in flight).
+    // (the AHEAD groups committed after it may still be in flight).
+    template <int SLOTS = kRingSlots, int AHEAD = kStage>
     __device__ __forceinline__ Zone<R> zone_staged(int s, Counters &cnt)
     {
         if (index_of(s) < 0) {
             R e;
             return saved((s - pc.ng - pc.n) % pc.n, e);
         }
-        asm volatile("cp.async.wait_group %0;" ::"n"(kStage) : "memory");
-        return prim<R, true>(ring(s, 0), ring(s, 1), ring(s, 2), ring(s, 3), ring(s, 4), k, cnt);
+        asm volatile("cp.async.wait_group %0;" ::"n"(AHEAD) : "memory");
+        return prim<R, true>(ring<SLOTS>(s, 0), ring<SLOTS>(s, 1), ring<SLOTS>(s, 2), ring<SLOTS>(s, 3),
+                             ring<SLOTS>(s, 4), k, cnt);
     }
 
     // Zone at pencil position s, its raw values also kept in the ring.
@@ -1790,14 +1798,21 @@ struct Marcher {
         }
         _Pragma("unroll") for (int i = 0; i < 6; ++i) rh[i] = (R)0;
         z0 = zm1 = zm2 = Zone<R>{};
+        if constexpr (DIR != 0)
+            for (int q = 0; q < kLearnedSlots - 1; ++q) stage<kLearnedSlots>(q);
         for (int kk = 0; kk < L + D; ++kk) {
             bool have = false;                // states of interface (kk-3)+1/2 traced this step
             R sLi[5], sRi[5];
             if (kk < L) {
                 zm2 = zm1;
                 zm1 = z0;
-                warm(kk + ENZO_PREFETCH_AHEAD);
-                z0 = zone<true>(kk, cnt);
+                if constexpr (DIR != 0) {
+                    stage<kLearnedSlots>(kk + kLearnedSlots - 1);
+                    z0 = zone_staged<kLearnedSlots, kLearnedSlots - 1>(kk, cnt);
+                } else {
+                    warm(kk + ENZO_PREFETCH_AHEAD);
+                    z0 = zone<true>(kk, cnt);
+                }
                 if (WRAP) {
                     const int j = kk - pc.ng;
                     if (j >= 0 && j < 3) save(j, z0, (R)0);
@@ -1948,6 +1963,15 @@ __host__ __device__ constexpr int ring_bytes()
     return (sizeof(R) == 4 && EXT == 0) ? (DIR == 0 ? 5 : 8) * 5 * THREADS * (int)sizeof(double) : 0;
 }
 
+// Learned kernels: the network's shared memory (aligned to 128 bytes inside
+// the dynamic block), then in y and z sweeps the staged loads' ring.
+__host__ __device__ constexpr size_t learned_ring_offset() { return (sizeof(GuessSmem) + 127 + 127) & ~size_t(127); }
+template <int DIR>
+__host__ __device__ constexpr size_t learned_smem_bytes()
+{
+    return learned_ring_offset() + (DIR != 0 ? 3 * 5 * kSweepThreads * sizeof(double) : 0);
+}
+
 // Persistent sweep kernel: CTAs take (patch, 128-pencil tile) work items from a
 // device counter until the batch is exhausted.  DIR is the sweep axis.
 #ifndef ENZO_SWEEP_MIN_BLOCKS_FP32
@@ -1976,6 +2000,7 @@ __global__ void __launch_bounds__(THREADS, LEARNED ? ENZO_LEARNED_CTAS : (sizeof
     // plain FP32 default kernels: the ring of raw values in dynamic shared memory
     double *uring = nullptr;
     if constexpr (ring_bytes<R, THREADS, EXT, DIR>() > 0 && !LEARNED) uring = reinterpret_cast<double *>(dsmem) + threadIdx.x;
+    if constexpr (LEARNED && DIR != 0) uring = reinterpret_cast<double *>(dsmem + learned_ring_offset()) + threadIdx.x;
     Counters cnt;
     cnt.st = a.status;
     const Consts<R> k = make_consts<R>(a.mp);
