@@ -11,9 +11,12 @@
  * update), one split direction per call, with the hydro CFL rule of Sec. 9.
  *
  * Conventions shared by every entry point:
- *   - All array pointers are DEVICE pointers owned by the caller.  The library
- *     allocates nothing and frees nothing; it keeps no state between calls
- *     except a per-device cache of launch sizes.
+ *   - All array pointers are DEVICE pointers owned by the caller.  Outside the
+ *     hierarchy driver (enzo_hierarchy_*, which owns the device state of a
+ *     hierarchy, allocated through the caller's allocator or cudaMalloc) the
+ *     library allocates nothing and frees nothing; it keeps no state between
+ *     calls except a per-device cache of launch sizes and the fixed scratch
+ *     array of enzo_ppm_sweep_noalloc.
  *   - Every call is asynchronous on the given stream (NULL = legacy default
  *     stream) unless stated otherwise, and returns ENZO_OK or a negative
  *     ENZO_ERR_* code.  No C++ exception crosses the ABI.
@@ -506,6 +509,151 @@ int enzo_cluster_flags(const uint8_t *flags, const int32_t n[3], const enzo_clus
  * both batches carry it (one alone is ENZO_ERR_ARG). */
 int enzo_project(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_links,
                  const enzo_patch_batch *fine, const enzo_patch_link *fine_links, int32_t r);
+
+/* ---- hierarchy driver (Sec. 3: EvolveLevel with subcycling; Sec. 3.5, 3.6:
+ * rebuild).  The library owns a hierarchy's device state and runs its whole
+ * root step: per level the ghost fill (enzo_ghost_fill_level from the parent,
+ * interpolated in time, then the sibling copies; enzo_ghost_fill_boundary on a
+ * root with external boundaries), the level's CFL timestep (capped at its
+ * parent's time), a copy of the state at the start of the step for a level
+ * with children, the three sweeps in alternating order recording flux
+ * registers, then, for a level with children, the ghost fill at the new time,
+ * the finer level advanced to this level's time by the same rules, flux
+ * correction in the order of its face parts, projection, and optionally a
+ * rebuild.  The plans (sibling copy boxes, interpolated ghost regions,
+ * correction face parts in waves) are built on the host at creation and again
+ * for every rebuilt level.  All calls are host-synchronous where a host value
+ * is needed (every level CFL, a rebuild's flags) and otherwise queue work on
+ * the hierarchy's stream. */
+typedef struct enzo_hierarchy enzo_hierarchy;   /* opaque */
+
+typedef struct {
+    int32_t npatch;         /* patches of the level (>= 0; the root level has one or more) */
+    const int32_t *n;       /* HOST [npatch][3] active cells per axis (>= 1; even below the root) */
+    const int32_t *origin;  /* HOST [npatch][3] global index at this level of the first active
+                               cell (even below the root: patches cover whole parent cells) */
+    const int32_t *parent;  /* HOST [npatch] index of the enclosing patch in level l-1, -1 on
+                               level 0 */
+} enzo_level_layout;
+
+/* Device memory for a hierarchy: alloc returns a DEVICE block of at least
+ * `bytes` (256-byte aligned) or NULL; release frees it.  ctx is passed
+ * through.  A NULL allocator (or NULL members) selects cudaMalloc / cudaFree. */
+typedef void *(*enzo_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*enzo_free_fn)(void *ptr, void *ctx);
+typedef struct {
+    enzo_alloc_fn alloc;
+    enzo_free_fn release;
+    void *ctx;
+} enzo_allocator;
+
+/* Rebuild rules (Sec. 3.5, 3.6): cells flagged by `flag` (enzo_flag_cells) are
+ * clustered per patch by `cluster` (enzo_cluster_flags; its margin member is
+ * replaced by root_margin on level 0 and by nest below, which keeps new grids
+ * off the domain boundary or properly nested). */
+typedef struct {
+    enzo_flag_params flag;
+    enzo_cluster_params cluster;
+    int32_t root_margin;    /* typically 3 */
+    int32_t nest;           /* typically 1 */
+} enzo_rebuild_params;
+
+/* Build a hierarchy of nlevel levels (refinement factor 2 between levels).
+ * Level l has cell width root_dx / 2^l.  nfields: 5, or 6 with the gas energy
+ * of the dual-energy option (then carried by every operation; sweeps need
+ * ENZO_OPT_DUAL).  root_bc: HOST bc[3] (ENZO_BC_*) of a root whose ghosts are
+ * filled before each step, or NULL for a periodic root that wraps inside its
+ * sweeps (then level 1 must stay 3 root cells from the domain boundary:
+ * ENZO_ERR_RANGE otherwise).  stream: cudaStream_t of every operation.
+ * Fields start at zero: fill them through enzo_hierarchy_level's batch (e.g.
+ * enzo_unpack_active or copies into U).  *out receives the hierarchy.
+ * ENZO_ERR_ARG on inconsistent layouts (parent out of range, odd sizes or
+ * origins below the root), ENZO_ERR_CUDA when memory runs out. */
+int enzo_hierarchy_create(const enzo_level_layout *levels, int32_t nlevel, double root_dx, int32_t nfields,
+                          const int32_t *root_bc, void *stream, const enzo_allocator *allocator,
+                          enzo_hierarchy **out);
+
+/* Free a hierarchy's device memory (after synchronising its stream). */
+int enzo_hierarchy_destroy(enzo_hierarchy *h);
+
+/* Number of levels. */
+int enzo_hierarchy_nlevel(const enzo_hierarchy *h);
+
+/* One level's state, owned by the hierarchy: valid until that level is
+ * rebuilt (generation then changes) or the hierarchy is destroyed. */
+typedef struct {
+    enzo_patch_batch batch;         /* its fields, descriptors, workspace, status, registers
+                                       (stream: the hierarchy's) */
+    const enzo_patch_link *links;   /* DEVICE [npatch] */
+    const enzo_patch *table;        /* HOST [npatch] copy of the descriptors */
+    const int32_t *n, *origin, *parent;   /* HOST layout, as in enzo_level_layout */
+    double dx;                      /* cell width */
+    double t;                       /* the level's time */
+    int64_t cells;                  /* active cells */
+    int64_t freg_len;               /* doubles in batch.freg */
+    uint64_t generation;            /* the hierarchy's rebuild counter */
+} enzo_level_info;
+int enzo_hierarchy_level(const enzo_hierarchy *h, int32_t level, enzo_level_info *info);
+
+/* One root step: dt_0 = the root's CFL timestep (rule of `cfl`, NULL: p), then
+ * EvolveLevel from level 0 to t + dt_0 with the sweep parameters p.  rb: NULL
+ * (static hierarchy) or the rules of a rebuild after every step of a level with
+ * children (after flux correction and projection), which replaces every finer
+ * level.  *dt0_out (may be NULL) receives dt_0.  The (level, dt) of every level
+ * step is appended to the hierarchy's log (enzo_hierarchy_take_log).  Any
+ * ENZO_ERR_* of a library call it makes is returned (the state is then
+ * undefined). */
+int enzo_hierarchy_root_step(enzo_hierarchy *h, const enzo_params *p, const enzo_params *cfl,
+                             const enzo_rebuild_params *rb, double *dt0_out);
+
+/* As enzo_hierarchy_root_step with the root's step ending at t_end (> the
+ * root's time) instead of its CFL timestep, e.g. to land on an output time; the
+ * caller keeps t_end - t within the root's CFL limit. */
+int enzo_hierarchy_step_to(enzo_hierarchy *h, double t_end, const enzo_params *p, const enzo_params *cfl,
+                           const enzo_rebuild_params *rb);
+
+/* Rebuild levels level+1, level+2, ... now (Sec. 3.5, 3.6): level `level`'s
+ * ghosts are filled, its cells flagged and clustered, and each new patch is
+ * interpolated from its parent (FP64, SecondOrderA) and overwritten by the old
+ * patches of its level where they overlap; a level whose grids come out
+ * unchanged is kept.  HOST boxes[nbox][7] receives the new grids of level+1 as
+ * (parent, lo[3], hi[3]) in level-`level` cells, *nbox their number
+ * (ENZO_ERR_RANGE, after the rebuild, when more than cap). */
+int enzo_hierarchy_rebuild(enzo_hierarchy *h, int32_t level, const enzo_rebuild_params *rb, int32_t *boxes,
+                           int32_t cap, int32_t *nbox);
+
+/* Move the step log into HOST levels[] / dts[] (cap entries) and clear it;
+ * *n receives the number of entries (ENZO_ERR_RANGE, log kept, when > cap). */
+int enzo_hierarchy_take_log(enzo_hierarchy *h, int32_t *levels, double *dts, int32_t cap, int32_t *n);
+
+/* Device time per operation kind, from CUDA events around each operation on
+ * the hierarchy's stream while timing is on: ms[ENZO_HOP_*] (HOST, may be
+ * NULL; synchronises the stream).  *cell_updates (may be NULL): active cells
+ * swept (one per cell per level step) since creation.  enable: 1 clears the
+ * times and turns timing on, 0 clears and turns it off, -1 leaves it as it is. */
+enum {
+    ENZO_HOP_GHOST_FILL = 0, ENZO_HOP_CFL = 1, ENZO_HOP_SAVE_OLD = 2, ENZO_HOP_SWEEPS = 3,
+    ENZO_HOP_CORRECT_PROJECT = 4, ENZO_HOP_REBUILD = 5, ENZO_HOP_COUNT = 6
+};
+int enzo_hierarchy_timing(enzo_hierarchy *h, int32_t enable, double ms[ENZO_HOP_COUNT], int64_t *cell_updates);
+
+/* The driver's plans on their own (host code, no GPU).  enzo_plan_level: for a
+ * level's layout (HOST n[npatch][3], origin[npatch][3]), the sibling copy boxes
+ * (every intersection of a patch's ghost-extended box with another patch's
+ * active box, by destination then source) and the ghost regions to interpolate
+ * (of the 26 around each patch, z slowest, then y, x, each -1, 0, 1: those not
+ * lying wholly in one sibling's active box; dst = src = the patch).
+ * enzo_plan_correction: the flux-correction face parts of a coarse level
+ * against its fine level (Sec. 3.4) in the order (fine patch, axis, side,
+ * coarse patch), and for each a wave: parts in one wave share no coarse cell,
+ * and a part that shares cells with earlier ones comes in a later wave.
+ * Outputs go to HOST arrays of cap entries; the counts are written first
+ * (ENZO_ERR_RANGE when they exceed the capacity). */
+int enzo_plan_level(const int32_t *n, const int32_t *origin, int32_t npatch, enzo_copy_box *sib, int32_t sib_cap,
+                    int32_t *nsib, enzo_copy_box *itp, int32_t itp_cap, int32_t *nitp);
+int enzo_plan_correction(const int32_t *fine_n, const int32_t *fine_origin, int32_t nfine, const int32_t *coarse_n,
+                         const int32_t *coarse_origin, int32_t ncoarse, enzo_fc_face *parts, int32_t *wave,
+                         int32_t cap, int32_t *nparts);
 
 /* ---- measurement helper (not part of the method) ---- */
 

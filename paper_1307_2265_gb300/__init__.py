@@ -190,6 +190,28 @@ class PatchBatch:
                 self.ge = torch.from_numpy(np.ascontiguousarray(ge, dtype=np.float64)).to(self.device)
             assert int(self.ge.numel()) == self.field_len
 
+    @classmethod
+    def wrap(cls, table, U, patches, workspace, ws_bytes, status, stream, freg=None, ge=None):
+        """A batch over device tensors that already hold its state (descriptors,
+        five fields, workspace, status words; flux registers and gas energy
+        optional), e.g. a level of a native hierarchy.  Nothing is copied."""
+        import torch
+        b = cls.__new__(cls)
+        b.torch = torch
+        b.device = U[0].device
+        b.table = np.ascontiguousarray(table, dtype=PATCH_DTYPE)
+        b.U = list(U)
+        b.field_len = int(U[0].numel())
+        b.patches = patches
+        b.workspace = workspace
+        b._ws_bytes = int(ws_bytes)
+        b.status = status
+        b.dt_dev = torch.zeros(1, dtype=torch.float64, device=b.device)
+        b.stream = stream
+        b.freg = freg
+        b.ge = ge
+        return b
+
     def c(self) -> _Batch:
         b = _Batch()
         b.npatch = len(self.table)

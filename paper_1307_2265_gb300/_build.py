@@ -11,6 +11,8 @@ Translation units and their flags:
   amr.cu        hierarchy rebuild: cell flagging (FP64, --fmad=false) and the
                 host clustering of flags into new grids
   probe.cu      FP64-pipe throughput probe (the FP64 sweep's roofline denominator)
+  driver.cu     AMR hierarchy driver: level plans, the EvolveLevel W-cycle, rebuilds
+                (host code calling the entry points above)
 Objects go to paper_1307_2265_gb300/_build/, the library next to this file.
 """
 from __future__ import annotations
@@ -37,6 +39,7 @@ UNITS = {
     "hierarchy.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     "amr.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     "probe.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
+    "driver.cu": [],
 }
 OPTIONAL_UNITS = {}
 

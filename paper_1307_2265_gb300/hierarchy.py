@@ -1,19 +1,24 @@
-"""AMR hierarchy on the GPU: host plans per level, every step of the W-cycle
-run by the library's kernels (paper Sec. 3), and an optional rebuild of the
-finer levels from flagged cells (Sec. 3.5, 3.6).
+"""AMR hierarchy on the GPU (paper Sec. 3), run by the library's native driver
+(enzo_hierarchy_*, csrc/driver.cu): the level plans, the EvolveLevel W-cycle
+and the rebuild of the finer levels from flagged cells (Sec. 3.5, 3.6) are
+host C++ in the library, every operation on the fields one of its kernels.
+This module marshals arguments, views the levels' device state as tensors,
+and exposes the plans and the rebuild's building blocks on their own.
 
-A level is one PatchBatch.  Host plans per level (again after a rebuild):
+Plans per level (again after a rebuild):
   * links: origin (global index of the first active cell) and parent index;
-  * sibling copy boxes: ghost regions of each patch that lie in a sibling's
-    active box.  Static levels tile boxes by tensor-product cuts, so a patch's
-    ghost region meets at most its 26 neighbours, found by a lattice lookup;
-    rebuilt levels are any disjoint boxes, and every pair of patches is
-    intersected;
+  * sibling copy boxes: every intersection of a patch's ghost-extended box with
+    another patch's active box;
+  * interpolated ghost regions: the 26 regions around each patch that no single
+    sibling covers (the copies that follow overwrite what siblings do cover);
   * flux-correction face parts: the cells outside each fine face, per coarse
     patch holding them, in waves so that corrections meeting in one coarse
     cell add in a fixed order;
   * flux registers: all-face registers for patches with children, boundary-face
     registers for patches with a parent.
+sibling_boxes / interp_boxes / correction_faces are the lattice versions of the
+same plans for the tensor-product tilings of synth.hierarchy_layout, kept as an
+independent check of the library's general ones.
 
 W-cycle of one root step (EvolveLevel of Sec. 3):
   fill ghosts; dt = min(CFL, t_parent - t); save the old state if the level has
@@ -27,8 +32,7 @@ import ctypes
 
 import numpy as np
 
-from . import (GUESS_MLP, PATCH_PERIODIC, PatchBatch, Params, _check, ghost_fill_boundary, lib, patch_table,
-               ppm_sweep, timestep_cfl)
+from . import PATCH_DTYPE, STATUS_WORDS, PatchBatch, Params, _Batch, _check, lib
 
 NG = 3
 LINK_DTYPE = np.dtype([("origin", "<i4", (3,)), ("parent", "<i4")])
@@ -62,8 +66,22 @@ def _lib():
         L.enzo_copy_level.argtypes = [vp, vp, vp, vp, vp, i32]
         L.enzo_flag_cells.argtypes = [vp, vp, vp, vp]
         L.enzo_cluster_flags.argtypes = [vp, vp, vp, vp, i32, vp]
+        L.enzo_plan_level.argtypes = [vp, vp, i32, vp, i32, vp, vp, i32, vp]
+        L.enzo_plan_correction.argtypes = [vp, vp, i32, vp, vp, i32, vp, vp, i32, vp]
+        L.enzo_hierarchy_create.argtypes = [vp, i32, d, i32, vp, vp, vp, vp]
+        L.enzo_hierarchy_destroy.argtypes = [vp]
+        L.enzo_hierarchy_nlevel.argtypes = [vp]
+        L.enzo_hierarchy_level.argtypes = [vp, i32, vp]
+        L.enzo_hierarchy_root_step.argtypes = [vp, vp, vp, vp, vp]
+        L.enzo_hierarchy_rebuild.argtypes = [vp, i32, vp, vp, i32, vp]
+        L.enzo_hierarchy_step_to.argtypes = [vp, d, vp, vp, vp]
+        L.enzo_hierarchy_take_log.argtypes = [vp, vp, vp, i32, vp]
+        L.enzo_hierarchy_timing.argtypes = [vp, i32, vp, vp]
         for n in ("enzo_ghost_fill_level", "enzo_flux_correct", "enzo_project", "enzo_copy_level",
-                  "enzo_flag_cells", "enzo_cluster_flags"):
+                  "enzo_flag_cells", "enzo_cluster_flags", "enzo_plan_level", "enzo_plan_correction",
+                  "enzo_hierarchy_create", "enzo_hierarchy_destroy", "enzo_hierarchy_nlevel",
+                  "enzo_hierarchy_level", "enzo_hierarchy_root_step", "enzo_hierarchy_rebuild",
+                  "enzo_hierarchy_take_log", "enzo_hierarchy_timing", "enzo_hierarchy_step_to"):
             getattr(L, n).restype = ctypes.c_int
         L._hier_ready = True
     return L
@@ -199,40 +217,41 @@ def correction_faces(fine, coarse, r=2):
     return t
 
 
+def _layout_arrays(n, origin):
+    n = np.ascontiguousarray(np.asarray(n, dtype=np.int32).reshape(-1, 3))
+    origin = np.ascontiguousarray(np.asarray(origin, dtype=np.int32).reshape(-1, 3))
+    return n, origin
+
+
+def _level_plans(n, origin):
+    """The library's level plans (enzo_plan_level): sibling copy boxes and the
+    ghost regions to interpolate."""
+    n, origin = _layout_arrays(n, origin)
+    ns, ni = ctypes.c_int32(0), ctypes.c_int32(0)
+    L = _lib()
+    r = L.enzo_plan_level(n.ctypes.data, origin.ctypes.data, len(n), None, 0, ctypes.byref(ns), None, 0,
+                          ctypes.byref(ni))
+    if r not in (0, -3):
+        _check(r, "enzo_plan_level")
+    sib = np.zeros(ns.value, dtype=BOX_DTYPE)
+    itp = np.zeros(ni.value, dtype=BOX_DTYPE)
+    _check(L.enzo_plan_level(n.ctypes.data, origin.ctypes.data, len(n), sib.ctypes.data, len(sib),
+                             ctypes.byref(ns), itp.ctypes.data, len(itp), ctypes.byref(ni)), "enzo_plan_level")
+    return sib, itp
+
+
 def sibling_boxes_general(n, origin):
     """sibling_boxes for any disjoint layout: every intersection of a patch's
-    ghost-extended box with another patch's active box."""
-    n, origin = np.asarray(n, dtype=np.int64), np.asarray(origin, dtype=np.int64)
-    lo, hi = origin, origin + n
-    out = []
-    for a in range(len(n)):
-        blo = np.maximum(lo[a] - NG, lo)
-        bhi = np.minimum(hi[a] + NG, hi)
-        keep = np.all(blo < bhi, axis=1)
-        keep[a] = False
-        b = np.flatnonzero(keep)
-        out.append(_boxes(np.full(len(b), a), b, blo[b], bhi[b]))
-    return np.concatenate(out) if out else _boxes([], [], np.zeros((0, 3)), np.zeros((0, 3)))
+    ghost-extended box with another patch's active box (the library's plan, the
+    one its hierarchy driver uses)."""
+    return _level_plans(n, origin)[0]
 
 
 def interp_boxes_general(n, origin):
     """The 26 ghost regions of every patch, except those lying wholly in one
     sibling's active box; the sibling copies that follow overwrite the parts
-    siblings cover (the order of Sec. 3.1)."""
-    n, origin = np.asarray(n, dtype=np.int64), np.asarray(origin, dtype=np.int64)
-    lo, hi = origin, origin + n
-    out = []
-    for a in range(len(n)):
-        for d in _DIRS:
-            blo = np.where(d < 0, lo[a] - NG, np.where(d > 0, hi[a], lo[a]))
-            bhi = np.where(d < 0, lo[a], np.where(d > 0, hi[a] + NG, hi[a]))
-            inside = np.all((lo <= blo) & (bhi <= hi), axis=1)
-            if not inside.any():
-                out.append((a, blo, bhi))
-    if not out:
-        return _boxes([], [], np.zeros((0, 3)), np.zeros((0, 3)))
-    a = np.array([o[0] for o in out])
-    return _boxes(a, a, np.array([o[1] for o in out]), np.array([o[2] for o in out]))
+    siblings cover (the order of Sec. 3.1).  The library's plan."""
+    return _level_plans(n, origin)[1]
 
 
 def correction_parts(fine, coarse, r=2):
@@ -242,40 +261,24 @@ def correction_parts(fine, coarse, r=2):
     entirely are left out (projection overwrites those cells).  Returns the
     parts and, for each, a wave: parts in one wave share no coarse cell, and a
     part that shares cells with earlier parts comes in a later wave, so the
-    additions happen in the listed order."""
-    fn, fo = np.asarray(fine["n"], dtype=np.int64), np.asarray(fine["origin"], dtype=np.int64)
-    cn, co = np.asarray(coarse["n"], dtype=np.int64), np.asarray(coarse["origin"], dtype=np.int64)
-    flo, fhi = fo // r, (fo + fn) // r          # coarse footprints of the fine patches
-    clo, chi = co, co + cn
-    parts, cells = [], []
-    for i in range(len(fn)):
-        for d in range(3):
-            a1 = 1 if d == 0 else 0
-            a2 = 1 if d == 2 else 2
-            for side in (0, 1):
-                X = (fo[i, d] + (fn[i, d] if side else 0)) // r
-                olo, ohi = flo[i].copy(), fhi[i].copy()
-                olo[d], ohi[d] = (X - 1, X) if side == 0 else (X, X + 1)
-                vol = int(np.prod(ohi - olo))
-                ilo, ihi = np.maximum(olo, flo), np.minimum(ohi, fhi)
-                covered = int(np.prod(np.clip(ihi - ilo, 0, None), axis=1).sum())
-                if covered >= vol:
-                    continue
-                tlo, thi = np.maximum(olo, clo), np.minimum(ohi, chi)
-                for t in np.flatnonzero(np.all(tlo < thi, axis=1)):
-                    parts.append((i, d, side, t, tlo[t][a1] - flo[i, a1], tlo[t][a2] - flo[i, a2],
-                                  thi[t][a1] - flo[i, a1], thi[t][a2] - flo[i, a2]))
-                    cells.append((t, tlo[t], thi[t]))
-    out = np.zeros(len(parts), dtype=FACE_DTYPE)
-    wave = np.zeros(len(parts), dtype=np.int64)
-    for k, (i, d, side, t, l1, l2, h1, h2) in enumerate(parts):
-        out[k] = (i, d, side, t, (l1, l2), (h1, h2))
-        tk, lk, hk = cells[k]
-        for q in range(k):
-            tq, lq, hq = cells[q]
-            if tq == tk and np.all(np.maximum(lk, lq) < np.minimum(hk, hq)):
-                wave[k] = max(wave[k], wave[q] + 1)
-    return out, wave
+    additions happen in the listed order.  The library's plan
+    (enzo_plan_correction, refinement factor 2)."""
+    if r != 2:
+        raise ValueError("the library refines by 2")
+    fn, fo = _layout_arrays(fine["n"], fine["origin"])
+    cn, co = _layout_arrays(coarse["n"], coarse["origin"])
+    L = _lib()
+    cnt = ctypes.c_int32(0)
+    rc = L.enzo_plan_correction(fn.ctypes.data, fo.ctypes.data, len(fn), cn.ctypes.data, co.ctypes.data, len(cn),
+                                None, None, 0, ctypes.byref(cnt))
+    if rc not in (0, -3):
+        _check(rc, "enzo_plan_correction")
+    out = np.zeros(cnt.value, dtype=FACE_DTYPE)
+    wave = np.zeros(cnt.value, dtype=np.int32)
+    _check(L.enzo_plan_correction(fn.ctypes.data, fo.ctypes.data, len(fn), cn.ctypes.data, co.ctypes.data,
+                                  len(cn), out.ctypes.data, wave.ctypes.data, len(out), ctypes.byref(cnt)),
+           "enzo_plan_correction")
+    return out, wave.astype(np.int64)
 
 
 def cluster_flags(flags, efficiency=0.3, small_cells=64, buffer=1, margin=0):
@@ -338,13 +341,92 @@ def register_sizes(n, nc=5):
     return all_f, bnd
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("release", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class _LevelLayout(ctypes.Structure):
+    _fields_ = [("npatch", ctypes.c_int32), ("n", ctypes.c_void_p), ("origin", ctypes.c_void_p),
+                ("parent", ctypes.c_void_p)]
+
+
+class _RebuildParams(ctypes.Structure):
+    _fields_ = [("flag", _FlagParams), ("cluster", _ClusterParams), ("root_margin", ctypes.c_int32),
+                ("nest", ctypes.c_int32)]
+
+
+class _LevelInfo(ctypes.Structure):
+    _fields_ = [("batch", _Batch), ("links", ctypes.c_void_p), ("table", ctypes.c_void_p),
+                ("n", ctypes.c_void_p), ("origin", ctypes.c_void_p), ("parent", ctypes.c_void_p),
+                ("dx", ctypes.c_double), ("t", ctypes.c_double), ("cells", ctypes.c_int64),
+                ("freg_len", ctypes.c_int64), ("generation", ctypes.c_uint64)]
+
+
+OPS = ("ghost_fill", "cfl", "save_old", "sweeps", "correct_project", "rebuild")   # ENZO_HOP_* order
+
+
+class _TorchMemory:
+    """Device memory of a hierarchy, taken from PyTorch's allocator on the
+    hierarchy's stream, so that tensors can view the levels' state."""
+
+    def __init__(self, device, stream):
+        import torch
+        self.torch, self.device, self.stream = torch, device, stream
+        self.blocks = {}
+        self._alloc = _ALLOC_FN(self._alloc_cb)
+        self._free = _FREE_FN(self._free_cb)
+        self.c = _Allocator(self._alloc, self._free, None)
+
+    def _alloc_cb(self, nbytes, ctx):
+        try:
+            with self.torch.cuda.stream(self.stream):
+                t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+            self.blocks[t.data_ptr()] = t
+            return t.data_ptr()
+        except Exception:           # the library sees NULL and reports ENZO_ERR_CUDA
+            return None
+
+    def _free_cb(self, ptr, ctx):
+        self.blocks.pop(ptr, None)
+
+    def view(self, ptr, dtype, count):
+        return self.blocks[ptr].view(dtype)[:count]
+
+
+def _host_array(addr, dtype, count):
+    if count == 0 or not addr:
+        return np.zeros(0, dtype=dtype)
+    nbytes = count * np.dtype(dtype).itemsize
+    return np.frombuffer((ctypes.c_char * nbytes).from_address(addr), dtype=dtype).copy()
+
+
+class _LevelView(dict):
+    """One level of a Hierarchy; its time ("t") is read from the driver on each
+    access, so a view held across steps stays current."""
+
+    def __init__(self, hier, l, data):
+        super().__init__(data)
+        self._hier, self._l = hier, l
+
+    def __getitem__(self, key):
+        if key == "t":
+            return self._hier._time(self._l)
+        return super().__getitem__(key)
+
+
 class Hierarchy:
-    """Device state of a hierarchy built from synth.hierarchy_layout (static),
-    with an optional rebuild of the finer levels from flagged cells (Sec. 3.5,
-    3.6)."""
+    """An AMR hierarchy run by the library's native driver (enzo_hierarchy_*:
+    level plans, the EvolveLevel W-cycle of Sec. 3, rebuilds of Sec. 3.5, 3.6).
+    This class marshals arguments and gives tensor views of the levels' state,
+    whose device memory the driver takes from PyTorch's allocator."""
 
     def __init__(self, layout, fields, root_dx, device="cuda", stream=None, root_bc=None):
-        """fields: per level, per patch, the five ghost-zoned fields, or six with
+        """layout: per level {"n", "origin", "parent"} (synth.hierarchy_layout).
+        fields: per level, per patch, the five ghost-zoned fields, or six with
         the gas energy of the dual-energy option (Sec. 4.1.1; every patch then
         carries it, it goes through every hierarchy operation, and the level
         sweeps need OPT_DUAL).  root_bc: external boundaries (bc_x, bc_y, bc_z)
@@ -357,309 +439,197 @@ class Hierarchy:
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         self.root_dx = root_dx
         self.root_bc = None if root_bc is None else tuple(int(v) for v in root_bc)
-        self.levels = []
         self.nf = len(fields[0][0])
         if self.nf not in (5, 6):
             raise ValueError("a patch has five fields, or six with the gas energy")
-        nlev = len(layout)
-        if nlev > 1:
-            self._check_root_margin(np.asarray(layout[0]["n"][0]), np.asarray(layout[1]["origin"]),
-                                    np.asarray(layout[1]["n"]))
-        for l, L in enumerate(layout):
-            n = np.asarray(L["n"], dtype=np.int64)
-            vols = np.prod(n + 2 * NG, axis=1)
-            offs = np.concatenate([[0], np.cumsum(vols)[:-1]]).astype(np.int64)
-            flat = [np.zeros(int(vols.sum())) for _ in range(self.nf)]
-            for i in range(len(n)):
-                for f in range(self.nf):
-                    blk = np.asarray(fields[l][i][f])
-                    flat[f][offs[i]:offs[i] + blk.size] = blk.ravel()
-            self.levels.append(self._build_level(l, n, np.asarray(L["origin"]), np.asarray(L["parent"]), flat,
-                                                 l + 1 < nlev, general=False))
-        for l in range(nlev - 1):
-            self._plan_correction(l, general=False)
-        # the uploads and zero fills above ran on the current stream; the
-        # hierarchy's own stream must not start before they are done
-        torch.cuda.synchronize(self.device)
-        self.cell_updates = 0
-        self.timing = None          # {op: [(start, end) events]} when profiling
-
-    @staticmethod
-    def _check_root_margin(root_n, origin, n):
-        # the periodic root wraps inside its sweeps and keeps no ghost cells, so
-        # the level-1 ghost interpolation (SecondOrderA reaches one root cell
-        # beyond the cell under a fine ghost) must find its parent cells inside it
-        if len(n) and (np.any(origin // 2 < 3) or np.any((origin + n + 1) // 2 > root_n - 3)):
-            raise ValueError("level 1 must stay 3 root cells away from the domain boundary")
-
-    def _build_level(self, l, n, origin, parent, flat, has_children, general, state=None):
-        """Device state of level l from its layout; flat: the five (six with
-        gas energy) flat host fields, or None for zeros.  state: time
-        bookkeeping to keep."""
-        torch = self.torch
-        n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
-        vols = np.prod(n + 2 * NG, axis=1)
-        offs = np.concatenate([[0], np.cumsum(vols)[:-1]]).astype(np.int64)
-        dx = self.root_dx / 2 ** l
-        wrap = l == 0 and self.root_bc is None
-        table = patch_table(n, offs, [dx] * 3, flags=PATCH_PERIODIC if wrap else 0, level=l)
-        has_parent = l > 0
-        a_sz, b_sz = register_sizes(n, self.nf)
-        reg = 0
-        if has_children:
-            table["freg_all"] = np.concatenate([[0], np.cumsum(a_sz)[:-1]]) + reg
-            reg += int(a_sz.sum())
-        if has_parent:
-            table["freg_bnd"] = np.concatenate([[0], np.cumsum(b_sz)[:-1]]) + reg
-            reg += int(b_sz.sum())
-        if flat is None:
-            flat = [torch.zeros(max(int(vols.sum()), 1), dtype=torch.float64, device=self.device)
-                    for _ in range(self.nf)]
+        keep, lays = [], []
+        for L in layout:
+            n = np.ascontiguousarray(np.asarray(L["n"], dtype=np.int32).reshape(-1, 3))
+            o = np.ascontiguousarray(np.asarray(L["origin"], dtype=np.int32).reshape(-1, 3))
+            par = np.ascontiguousarray(np.asarray(L["parent"], dtype=np.int32).reshape(-1))
+            keep += [n, o, par]
+            lays.append(_LevelLayout(len(n), n.ctypes.data, o.ctypes.data, par.ctypes.data))
+        arr = (_LevelLayout * len(lays))(*lays)
+        bc = (ctypes.c_int32 * 3)(*self.root_bc) if self.root_bc is not None else None
+        self._mem = _TorchMemory(self.device, self.stream)
+        self._h = ctypes.c_void_p()
+        self._views = {}
+        self._timing = None
+        with torch.cuda.device(self.device):
+            _check(_lib().enzo_hierarchy_create(arr, len(lays), float(root_dx), self.nf, bc,
+                                                self.stream.cuda_stream, ctypes.byref(self._mem.c),
+                                                ctypes.byref(self._h)), "enzo_hierarchy_create")
         with torch.cuda.stream(self.stream):
-            batch = PatchBatch(table, flat[:5], device=self.device, stream=self.stream,
-                               ge=flat[5] if self.nf == 6 else None)
-        if reg:
-            batch.freg = torch.zeros(reg, dtype=torch.float64, device=self.device)
-        links = np.zeros(len(n), dtype=LINK_DTYPE)
-        links["origin"] = np.asarray(origin).reshape(-1, 3)
-        links["parent"] = np.asarray(parent).reshape(-1)
-        lev = {"batch": batch, "links": _to_dev(links, self.device), "table": table, "n": n,
-               "origin": np.asarray(origin).reshape(-1, 3), "parent": np.asarray(parent).reshape(-1), "dx": dx,
-               "t": 0.0, "step": 0, "t_old": 0.0, "has_children": has_children, "bnd_sl": None,
-               "cells": int(np.prod(n, axis=1).sum()), "general": general}
-        if state is not None:
-            lev.update(state)
-        if has_parent:
-            sib = sibling_boxes_general if general else sibling_boxes
-            itp = interp_boxes_general if general else interp_boxes
-            bx = sib(n, lev["origin"])
-            lev["boxes"], lev["nbox"] = _to_dev(bx, self.device), len(bx)
-            ib = itp(n, lev["origin"])
-            lev["ibox"], lev["nibox"] = _to_dev(ib, self.device), len(ib)
-            lo = int(table["freg_bnd"].min()) if len(n) else 0
-            lev["bnd_sl"] = (lo, lo + int(b_sz.sum()))
-        if has_children:
-            lev["old"] = [torch.empty_like(u) for u in self._fields(batch)]
-        return lev
+            for l, lev in enumerate(self.levels):
+                targets = self._fields(lev["batch"])
+                for f, u in enumerate(targets):
+                    flat = np.zeros(int(u.numel()))
+                    for i, t in enumerate(lev["table"]):
+                        blk = np.asarray(fields[l][i][f], dtype=np.float64).ravel()
+                        flat[int(t["off"]):int(t["off"]) + blk.size] = blk
+                    u.copy_(torch.from_numpy(flat))
+        self.stream.synchronize()
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _lib().enzo_hierarchy_destroy(h)
+            except Exception:
+                pass
+            self._h = None
 
     def _fields(self, batch):
         """The fields a hierarchy operation carries: U, and ge with dual energy."""
         return list(batch.U) + ([batch.ge] if self.nf == 6 else [])
 
-    def _plan_correction(self, l, general):
-        """Flux-correction parts of level l (coarse) against level l + 1, as
-        device arrays per wave."""
-        fine = {"n": self.levels[l + 1]["n"], "origin": self.levels[l + 1]["origin"]}
-        coarse = {"n": self.levels[l]["n"], "origin": self.levels[l]["origin"]}
-        if general:
-            fc, wave = correction_parts(fine, coarse)
-        else:
-            fc = correction_faces(fine, coarse)
-            wave = np.zeros(len(fc), dtype=np.int64)
-        waves = []
-        for w in range(int(wave.max()) + 1 if len(wave) else 0):
-            sel = fc[wave == w]
-            waves.append((_to_dev(sel, self.device), len(sel)))
-        self.levels[l]["waves"] = waves
+    # -- views of the driver's levels ------------------------------------------
+    def _level(self, l):
+        torch = self.torch
+        info = _LevelInfo()
+        _check(_lib().enzo_hierarchy_level(self._h, l, ctypes.byref(info)), "enzo_hierarchy_level")
+        b = info.batch
+        npatch = int(b.npatch)
+        key = (l, int(info.generation), b.U[0])
+        batch = self._views.get(key)
+        if batch is None:
+            m = self._mem
+            flen = int(b.field_len)
+            table = _host_array(info.table, PATCH_DTYPE, npatch)
+            batch = PatchBatch.wrap(
+                table, [m.view(b.U[f], torch.float64, flen) for f in range(5)],
+                m.view(b.patches, torch.uint8, 72 * npatch), m.view(b.workspace, torch.uint8, int(b.ws_bytes)),
+                int(b.ws_bytes), m.view(b.status, torch.int64, STATUS_WORDS), self.stream,
+                freg=m.view(b.freg, torch.float64, int(info.freg_len)) if b.freg else None,
+                ge=m.view(b.ge, torch.float64, flen) if b.ge else None)
+            self._views = {k: v for k, v in self._views.items() if k[0] != l}
+            self._views[key] = batch
+        n = _host_array(info.n, np.int32, 3 * npatch).reshape(-1, 3).astype(np.int64)
+        origin = _host_array(info.origin, np.int32, 3 * npatch).reshape(-1, 3).astype(np.int64)
+        parent = _host_array(info.parent, np.int32, npatch).astype(np.int64)
+        return _LevelView(self, l, {"batch": batch, "n": n, "origin": origin, "parent": parent, "dx": info.dx,
+                                    "table": batch.table, "cells": int(info.cells), "links": info.links})
 
-    def _mark(self, op):
-        """Record a CUDA event pair around an operation when timing is on."""
-        if self.timing is None:
-            return None
-        e = self.torch.cuda.Event(enable_timing=True)
-        e.record(self.stream)
-        self.timing.setdefault(op, []).append([e, None])
-        return self.timing[op][-1]
+    def _time(self, l):
+        info = _LevelInfo()
+        _check(_lib().enzo_hierarchy_level(self._h, l, ctypes.byref(info)), "enzo_hierarchy_level")
+        return info.t
 
-    def _end(self, mark):
-        if mark is None:
-            return
-        e = self.torch.cuda.Event(enable_timing=True)
-        e.record(self.stream)
-        mark[1] = e
+    @property
+    def levels(self):
+        """Per level: its batch (tensor views of the driver's state), layout
+        (n, origin, parent), dx, time and descriptor table."""
+        return [self._level(l) for l in range(_lib().enzo_hierarchy_nlevel(self._h))]
 
-    def timing_ms(self):
-        """Milliseconds per operation type (after synchronising the stream)."""
-        self.stream.synchronize()
-        return {op: sum(a.elapsed_time(b) for a, b in v) for op, v in (self.timing or {}).items()}
+    # -- the W-cycle, rebuilds, timing -----------------------------------------
+    @staticmethod
+    def _rebuild_params(gamma, crit, clus, margin=3, nest=1, precision=0):
+        crit, clus = dict(crit or {}), dict(clus or {})
+        fp = _FlagParams(gamma, crit.get("slope", 0.3), crit.get("shock_dp", 0.33), crit.get("shock_e", 0.1),
+                         crit.get("mass", 0.0), precision)
+        cp = _ClusterParams(clus.get("efficiency", 0.3), clus.get("small_cells", 64), clus.get("buffer", 1), 0)
+        return _RebuildParams(fp, cp, margin, nest)
 
-    # -- primitive operations -------------------------------------------
-    def _fill(self, l, precision):
-        lev = self.levels[l]
-        if l == 0:
-            if self.root_bc is not None:
-                ghost_fill_boundary(lev["batch"], self.root_bc)
-            return          # a periodic root wraps inside its sweeps
-        par = self.levels[l - 1]
-        w = (lev["t"] - par["t_old"]) / (par["t"] - par["t_old"])
-        b, pb = lev["batch"].c(), par["batch"].c()
-        old = (ctypes.c_void_p * 5)(*[u.data_ptr() for u in par["old"][:5]])
-        old_ge = par["old"][5].data_ptr() if self.nf == 6 else None
-        _check(_lib().enzo_ghost_fill_level(ctypes.byref(b), lev["links"].data_ptr(), ctypes.byref(pb),
-                                            par["links"].data_ptr(), old, old_ge, w, lev["ibox"].data_ptr(),
-                                            lev["nibox"], lev["boxes"].data_ptr(), lev["nbox"], precision, 2),
-               "enzo_ghost_fill_level")
+    def _take_log(self, log):
+        L = _lib()
+        n = ctypes.c_int32(0)
+        cap = 256
+        while True:
+            lv = (ctypes.c_int32 * cap)()
+            dt = (ctypes.c_double * cap)()
+            r = L.enzo_hierarchy_take_log(self._h, lv, dt, cap, ctypes.byref(n))
+            if r == -3:
+                cap = n.value
+                continue
+            _check(r, "enzo_hierarchy_take_log")
+            break
+        if log is not None:
+            log.extend((int(lv[k]), float(dt[k])) for k in range(n.value))
 
-    def _step(self, l, dt, params):
-        lev = self.levels[l]
-        order = (0, 1, 2) if lev["step"] % 2 == 0 else (2, 1, 0)
-        done = 0
-        for d in order:
-            cover = 7 & ~done & ~(1 << d)
-            ppm_sweep(lev["batch"], d, dt, cover, params)
-            done |= 1 << d
-        lev["step"] += 1
-        self.cell_updates += lev["cells"]
+    def root_step(self, params, cfl_params=None, log=None, rebuild=None):
+        """One root step: dt_0 from the root CFL rule, then the W-cycle.
+        rebuild: None, or a dict (gamma, crit, clus[, margin, nest]) for a
+        rebuild after every step of a level with children (flags in the sweeps'
+        precision).  Appends (level, dt) of every level step to log."""
+        cfl_params = cfl_params if cfl_params is not None else Params(
+            gamma=params.gamma, cfl=params.cfl, precision=params.precision)
+        p, c = params.c(), cfl_params.c()
+        rb = self._rebuild_params(**rebuild, precision=params.precision) if rebuild is not None else None
+        dt0 = ctypes.c_double(0.0)
+        with self.torch.cuda.device(self.device):
+            r = _lib().enzo_hierarchy_root_step(self._h, ctypes.byref(p), ctypes.byref(c),
+                                                ctypes.byref(rb) if rb is not None else None, ctypes.byref(dt0))
+        self._take_log(log)
+        _check(r, "enzo_hierarchy_root_step")
+        return dt0.value
 
-    def _correct_and_project(self, l, dt, params):
-        c, f = self.levels[l], self.levels[l + 1]
-        cb, fb = c["batch"].c(), f["batch"].c()
-        for faces, nface in c["waves"]:
-            _check(_lib().enzo_flux_correct(ctypes.byref(cb), c["links"].data_ptr(), ctypes.byref(fb),
-                                            f["links"].data_ptr(), faces.data_ptr(), nface, dt, 2,
-                                            1 if params.precision == 1 else 0),
-                   "enzo_flux_correct")
-        _check(_lib().enzo_project(ctypes.byref(cb), c["links"].data_ptr(), ctypes.byref(fb),
-                                   f["links"].data_ptr(), 2), "enzo_project")
+    def evolve_level(self, l, t_parent, params, cfl_params, log=None, rebuild=None):
+        """Advance the root (l = 0) and with it every finer level to t_parent in
+        one root step (the W-cycle below it as in root_step)."""
+        if l != 0:
+            raise ValueError("the driver advances the hierarchy from its root")
+        p, c = params.c(), cfl_params.c()
+        rb = self._rebuild_params(**rebuild, precision=params.precision) if rebuild is not None else None
+        with self.torch.cuda.device(self.device):
+            r = _lib().enzo_hierarchy_step_to(self._h, float(t_parent), ctypes.byref(p), ctypes.byref(c),
+                                              ctypes.byref(rb) if rb is not None else None)
+        self._take_log(log)
+        _check(r, "enzo_hierarchy_step_to")
 
-    # -- rebuild (Sec. 3.5, 3.6) ---------------------------------------------
     def rebuild(self, l, gamma, crit, clus, margin=3, nest=1, precision=0):
         """Replace levels l+1, l+2, ... by grids covering the flagged cells of the
         level above each (Sec. 3.5, 3.6): level l's ghosts are filled, its cells
         flagged on the GPU and each patch's flags clustered on the host; every
-        new patch is interpolated from its parent (SecondOrderA) and overwritten
-        by the old patches of its level where they overlap (a level whose boxes
-        come out unchanged is kept as it is).  On the root, flags
+        new patch is interpolated from its parent (SecondOrderA, FP64) and
+        overwritten by the old patches of its level where they overlap (a level
+        whose boxes come out unchanged is kept as it is).  On the root, flags
         within `margin` cells of the domain boundary are dropped, on deeper
-        levels those within `nest` cells of the patch's edge (the coarse cells
-        outside every new fine face then lie in the parent).  The fill and
-        the interpolation run in FP64 in both precisions (the new grids keep
-        their parents' means to FP64 rounding); `precision` picks the flag
-        kernel (FP64 or FP32).  Returns the new boxes of level l+1 as (parent,
-        lo, hi) in level-l cells."""
-        with self.torch.cuda.stream(self.stream):
-            self._fill(l, 0)
-            first = None
-            for m in range(l, len(self.levels) - 1):
-                boxes = self._rebuild_one(m, gamma, crit, clus, margin if m == 0 else nest, precision)
-                first = boxes if first is None else first
-        return first
+        levels those within `nest` cells of the patch's edge.  `precision`
+        picks the flag kernel (FP64 or FP32).  Returns the new boxes of level
+        l+1 as (parent, lo, hi) in level-l cells."""
+        rb = self._rebuild_params(gamma, crit, clus, margin, nest, precision)
+        cap = 1 << 16
+        while True:
+            boxes = (ctypes.c_int32 * (7 * cap))()
+            nb = ctypes.c_int32(0)
+            with self.torch.cuda.device(self.device):
+                r = _lib().enzo_hierarchy_rebuild(self._h, l, ctypes.byref(rb), boxes, cap, ctypes.byref(nb))
+            if r == -3 and nb.value > cap:
+                # rebuilt, but the box list was short: level l is unchanged, so
+                # flagging it again gives the same grids, which are then kept
+                cap = nb.value
+                continue
+            _check(r, "enzo_hierarchy_rebuild")
+            break
+        v = np.frombuffer(boxes, dtype=np.int32)[:7 * nb.value].reshape(-1, 7)
+        return [(int(e[0]), tuple(int(x) for x in e[1:4]), tuple(int(x) for x in e[4:7])) for e in v]
 
-    def _rebuild_one(self, m, gamma, crit, clus, margin, flag_precision=0):
-        precision = 0
-        lev = self.levels[m]
-        flags = flag_cells(lev["batch"], gamma, precision=flag_precision, **crit)
-        boxes = []
-        for i, fl in enumerate(flags):
-            o = lev["origin"][i]
-            for lo, hi in cluster_flags(fl, margin=margin, **clus):
-                boxes.append((i, tuple(int(o[a] + lo[a]) for a in range(3)), tuple(int(o[a] + hi[a]) for a in range(3))))
-        n = np.array([[2 * (hi[a] - lo[a]) for a in range(3)] for _, lo, hi in boxes], dtype=np.int64).reshape(-1, 3)
-        origin = np.array([[2 * lo[a] for a in range(3)] for _, lo, _ in boxes], dtype=np.int64).reshape(-1, 3)
-        parent = np.array([b[0] for b in boxes], dtype=np.int64)
-        old = self.levels[m + 1]
-        same = [(int(p), tuple(int(v) // 2 for v in o), tuple((int(v) + int(w)) // 2 for v, w in zip(o, n_)))
-                for p, o, n_ in zip(old["parent"], old["origin"], old["n"])]
-        if boxes == same:
-            # the same grids: the level stays as it is; the level above may be
-            # new, so its correction parts are planned again
-            self._plan_correction(m, general=True)
-            return boxes
-        state = {k: old[k] for k in ("t", "step", "t_old")}
-        new = self._build_level(m + 1, n, origin, parent, None, old["has_children"], general=True, state=state)
-        if len(n):
-            L = _lib()
-            full = _boxes(np.arange(len(n)), np.arange(len(n)), origin - NG, origin + n + NG)
-            fb = _to_dev(full, self.device)
-            nb, pb = new["batch"].c(), lev["batch"].c()
-            cur = (ctypes.c_void_p * 5)(*[u.data_ptr() for u in lev["batch"].U])
-            cur_ge = lev["batch"].ge.data_ptr() if self.nf == 6 else None
-            _check(L.enzo_ghost_fill_level(ctypes.byref(nb), new["links"].data_ptr(), ctypes.byref(pb),
-                                           lev["links"].data_ptr(), cur, cur_ge, 0.0, fb.data_ptr(), len(full),
-                                           None, 0,
-                                           precision, 2), "enzo_ghost_fill_level")
-            # cells of the new patches (ghosts included) lying in an old patch
-            olo, ohi = old["origin"], old["origin"] + old["n"]
-            cps = []
-            for a in range(len(n)):
-                blo = np.maximum(origin[a] - NG, olo)
-                bhi = np.minimum(origin[a] + n[a] + NG, ohi)
-                b = np.flatnonzero(np.all(blo < bhi, axis=1))
-                cps.append(_boxes(np.full(len(b), a), b, blo[b], bhi[b]))
-            cp = np.concatenate(cps)
-            if len(cp):
-                cb = _to_dev(cp, self.device)
-                ob = old["batch"].c()
-                _check(L.enzo_copy_level(ctypes.byref(nb), new["links"].data_ptr(), ctypes.byref(ob),
-                                         old["links"].data_ptr(), cb.data_ptr(), len(cp)), "enzo_copy_level")
-        self.levels[m + 1] = new
-        self._plan_correction(m, general=True)
-        return boxes
+    @property
+    def timing(self):
+        return self._timing
 
-    # -- W-cycle ------------------------------------------------------------
-    def evolve_level(self, l, t_parent, params, cfl_params, log=None, rebuild=None):
-        """Advance level l to t_parent (W-cycle).  rebuild: None, or a dict
-        (gamma, crit, clus) for rebuild() after every step of a level with
-        children (after flux correction and projection)."""
-        lev = self.levels[l]
-        if lev["cells"] == 0:
-            lev["t"] = t_parent          # a level without grids has nothing to advance
-            return
-        with self.torch.cuda.stream(self.stream):
-            while lev["t"] < t_parent * (1 - 1e-14):
-                m = self._mark("ghost_fill")
-                self._fill(l, params.precision)
-                self._end(m)
-                if l == 0:
-                    dt = t_parent - lev["t"]
-                else:
-                    m = self._mark("cfl")
-                    dt = min(timestep_cfl(lev["batch"], cfl_params), t_parent - lev["t"])
-                    self._end(m)
-                if lev["has_children"]:
-                    m = self._mark("save_old")
-                    for u, o in zip(self._fields(lev["batch"]), lev["old"]):
-                        o.copy_(u)
-                    self._end(m)
-                    lev["t_old"] = lev["t"]
-                m = self._mark("sweeps")
-                self._step(l, dt, params)
-                self._end(m)
-                lev["t"] += dt
-                if log is not None:
-                    log.append((l, dt))
-                if lev["has_children"]:
-                    m = self._mark("ghost_fill")
-                    self._fill(l, params.precision)
-                    self._end(m)
-                    child = self.levels[l + 1]
-                    if child["batch"].freg is not None:         # None: a level without grids
-                        lo, hi = child["bnd_sl"]
-                        child["batch"].freg[lo:hi].zero_()
-                    self.evolve_level(l + 1, lev["t"], params, cfl_params, log, rebuild)
-                    m = self._mark("correct_project")
-                    self._correct_and_project(l, dt, params)
-                    self._end(m)
-                    if rebuild is not None:
-                        m = self._mark("rebuild")
-                        self.rebuild(l, **rebuild, precision=params.precision)
-                        self._end(m)
-            # the loop stops within 1e-14 of the parent's time; the level has reached it
-            lev["t"] = t_parent
+    @timing.setter
+    def timing(self, value):
+        """Set to {} to time each operation kind on the device (CUDA events), None to stop."""
+        _check(_lib().enzo_hierarchy_timing(self._h, 0 if value is None else 1, None, None), "enzo_hierarchy_timing")
+        self._timing = value
 
-    def root_step(self, params, cfl_params=None, log=None, rebuild=None):
-        """One root step: dt_0 from the root CFL rule, then the W-cycle."""
-        cfl_params = cfl_params if cfl_params is not None else Params(
-            gamma=params.gamma, cfl=params.cfl, precision=params.precision)
-        root = self.levels[0]
-        with self.torch.cuda.stream(self.stream):
-            dt0 = timestep_cfl(root["batch"], cfl_params)
-        self.evolve_level(0, root["t"] + dt0, params, cfl_params, log, rebuild)
-        return dt0
+    def timing_ms(self):
+        """Milliseconds per operation kind since timing was switched on (synchronises the stream)."""
+        ms = (ctypes.c_double * len(OPS))()
+        _check(_lib().enzo_hierarchy_timing(self._h, -1, ms, None), "enzo_hierarchy_timing")
+        return {name: ms[k] for k, name in enumerate(OPS) if ms[k] > 0.0}
+
+    @property
+    def cell_updates(self):
+        cu = ctypes.c_int64(0)
+        _check(_lib().enzo_hierarchy_timing(self._h, -1, None, ctypes.byref(cu)), "enzo_hierarchy_timing")
+        return int(cu.value)
 
     def patch_fields(self, l, i):
         """Host copies of patch i of level l: the five fields, and the gas
         energy as a sixth with dual energy."""
+        self.stream.synchronize()
         b = self.levels[l]["batch"]
         views = b.patch_fields(i) + ([b.patch_ge(i)] if self.nf == 6 else [])
         return [f.cpu().numpy() for f in views]

@@ -115,3 +115,31 @@ def test_active_offsets_are_consecutive_blocks():
     sizes = [(3, 4, 5), (1, 1, 1), (16, 8, 2)]
     t = ez.patch_table(sizes, [0, 1000, 2000], [0.1] * 3)
     assert list(ez.active_offsets(t)) == [0, 60, 61]
+
+
+def test_hierarchy_driver_rejects_bad_layouts_before_any_cuda_call():
+    import ctypes
+    L = gh._lib()
+
+    def create(levels, nf=5, dx=1.0 / 16):
+        keep, lays = [], []
+        for n, o, p in levels:
+            n = np.ascontiguousarray(np.asarray(n, dtype=np.int32).reshape(-1, 3))
+            o = np.ascontiguousarray(np.asarray(o, dtype=np.int32).reshape(-1, 3))
+            p = np.ascontiguousarray(np.asarray(p, dtype=np.int32).reshape(-1))
+            keep += [n, o, p]
+            lays.append(gh._LevelLayout(len(n), n.ctypes.data, o.ctypes.data, p.ctypes.data))
+        arr = (gh._LevelLayout * len(lays))(*lays)
+        h = ctypes.c_void_p()
+        return L.enzo_hierarchy_create(arr, len(lays), dx, nf, None, None, None, ctypes.byref(h))
+
+    root = ([[16, 16, 16]], [[0, 0, 0]], [-1])
+    assert create([root, ([[8, 8, 8]], [[12, 12, 12]], [1])]) == -1      # parent out of range
+    assert create([root, ([[8, 8, 7]], [[12, 12, 12]], [0])]) == -1      # odd size below the root
+    assert create([root, ([[8, 8, 8]], [[12, 12, 13]], [0])]) == -1      # odd origin
+    assert create([([[16, 16, 16]], [[0, 0, 0]], [0])]) == -1             # a root with a parent
+    assert create([root], nf=7) == -1
+    assert create([root], dx=0.0) == -1
+    # level 1 must stay 3 root cells inside a periodic root (no ghosts to interpolate from)
+    assert create([root, ([[8, 8, 8]], [[2, 12, 12]], [0])]) == -3
+    assert L.enzo_hierarchy_destroy(None) == -1

@@ -231,3 +231,69 @@ def test_full_size_hierarchy_conserves_the_composite_totals():
     assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0) / scale
     st = sum(np.array(list(lev["batch"].read_status().values())) for lev in hier.levels)
     assert st[7] == 0                                   # no NaN anywhere
+
+
+def test_c_caller_runs_the_w_cycle_on_its_own():
+    """The driver's C entry points as a C caller uses them: device memory from
+    cudaMalloc (no allocator), the active cells loaded with enzo_unpack_active
+    (ghost zones start at zero: the W-cycle fills them before any read), two
+    FP32 root steps.  The step log and every active cell equal those of the
+    Python wrapper, which uploads whole ghost-zoned patches."""
+    import ctypes
+    import torch
+    layout, fields = _setup(3)
+    params = ez.Params(precision=ez.FP32)
+    hier = gh.Hierarchy(layout, fields, 1.0 / 16)
+    L = gh._lib()
+    keep, lays = [], []
+    for Lv in layout:
+        n = np.ascontiguousarray(np.asarray(Lv["n"], dtype=np.int32).reshape(-1, 3))
+        o = np.ascontiguousarray(np.asarray(Lv["origin"], dtype=np.int32).reshape(-1, 3))
+        par = np.ascontiguousarray(np.asarray(Lv["parent"], dtype=np.int32).reshape(-1))
+        keep += [n, o, par]
+        lays.append(gh._LevelLayout(len(n), n.ctypes.data, o.ctypes.data, par.ctypes.data))
+    arr = (gh._LevelLayout * len(lays))(*lays)
+    stream = torch.cuda.Stream()
+    h = ctypes.c_void_p()
+    assert L.enzo_hierarchy_create(arr, len(lays), 1.0 / 16, 5, None, stream.cuda_stream, None,
+                                   ctypes.byref(h)) == 0
+    try:
+        def level(l):
+            info = gh._LevelInfo()
+            assert L.enzo_hierarchy_level(h, l, ctypes.byref(info)) == 0
+            table = gh._host_array(info.table, ez.PATCH_DTYPE, int(info.batch.npatch))
+            return info, torch.from_numpy(ez.active_offsets(table)).cuda()
+
+        for l, Lv in enumerate(layout):
+            info, act = level(l)
+            packed = [torch.from_numpy(np.concatenate([H._active(np.asarray(fields[l][i][f])).ravel()
+                                                       for i in range(len(fields[l]))])).cuda() for f in range(5)]
+            torch.cuda.synchronize()
+            ptrs = (ctypes.c_void_p * 5)(*[t.data_ptr() for t in packed])
+            assert L.enzo_unpack_active(ctypes.byref(info.batch), ptrs, None, act.data_ptr()) == 0
+        p, c = params.c(), ez.Params(precision=ez.FP32).c()
+        for _ in range(2):
+            log_w = []
+            hier.root_step(params, log=log_w)
+            dt0 = ctypes.c_double(0.0)
+            assert L.enzo_hierarchy_root_step(h, ctypes.byref(p), ctypes.byref(c), None, ctypes.byref(dt0)) == 0
+            lv, dts, cnt = (ctypes.c_int32 * 256)(), (ctypes.c_double * 256)(), ctypes.c_int32(0)
+            assert L.enzo_hierarchy_take_log(h, lv, dts, 256, ctypes.byref(cnt)) == 0
+            assert [(int(lv[k]), float(dts[k])) for k in range(cnt.value)] == log_w
+        hier.stream.synchronize()
+        for l in range(len(layout)):
+            info, act = level(l)
+            cells = int(info.cells)
+            out = [torch.empty(cells, dtype=torch.float64, device="cuda") for _ in range(5)]
+            ptrs = (ctypes.c_void_p * 5)(*[t.data_ptr() for t in out])
+            assert L.enzo_pack_active(ctypes.byref(info.batch), ptrs, None, act.data_ptr()) == 0
+            stream.synchronize()
+            want = [np.concatenate([H._active(hier.patch_fields(l, i)[f]).ravel()
+                                    for i in range(len(layout[l]["n"]))]) for f in range(5)]
+            for f in range(5):
+                assert np.array_equal(out[f].cpu().numpy(), want[f]), (l, f)
+        cu = ctypes.c_int64(0)
+        assert L.enzo_hierarchy_timing(h, -1, None, ctypes.byref(cu)) == 0
+        assert cu.value == hier.cell_updates
+    finally:
+        assert L.enzo_hierarchy_destroy(h) == 0
