@@ -566,7 +566,7 @@ def run_gpu(args, rank, world):
                                      "wall_seconds": time.perf_counter() - t0}
         t0 = time.perf_counter()
         hp, layout, setup = hierarchy_paths(net, args.root, args.mlp_gate, rank,
-                                            ("fp32_learned", "fp32_plain", "fp64_plain"))
+                                            ("fp32_learned", "fp32_plain", "fp64_plain"), probe=res["fp64_probe"])
         res["config5_hierarchy"] = {"config": {"workload": _hierarchy_workload(args.root, layout),
                                                "patches_per_level": [len(L["n"]) for L in layout]},
                                     "paths": hp, "setup_seconds": setup, "wall_seconds": time.perf_counter() - t0}
@@ -592,8 +592,9 @@ def run_hierarchy(args, rank, world):
     dev = _env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(dev)
     net, train_info = _train_net(args)
+    probe = fp64_probe(torch.cuda.Stream())
     out, layout, setup = hierarchy_paths(net, args.root, args.mlp_gate, rank,
-                                         ("fp32_learned", "fp32_plain", "fp32_dual", "fp64_plain"))
+                                         ("fp32_learned", "fp32_plain", "fp32_dual", "fp64_plain"), probe=probe)
     res = {"metric": METRIC, "value": out["fp32_learned"]["value"], "unit": "Mcell-updates/s", "n_gpus": world,
            "steps": 1, "warmup": 0, "ms_per_step": out["fp32_learned"]["ms_per_root_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc",
@@ -601,7 +602,7 @@ def run_hierarchy(args, rank, world):
            "config": {"workload": _hierarchy_workload(args.root, layout),
                       "patches_per_level": [len(L["n"]) for L in layout],
                       "cells_per_level": [int(np.prod(L["n"], axis=1).sum()) for L in layout]},
-           "paths": out, "training": train_info, "setup_seconds": setup}
+           "paths": out, "training": train_info, "setup_seconds": setup, "fp64_probe": probe}
     return res
 
 
@@ -611,7 +612,7 @@ def _hierarchy_workload(root, layout):
             f"root step")
 
 
-def hierarchy_paths(net, root, mlp_gate, seed, names):
+def hierarchy_paths(net, root, mlp_gate, seed, names, probe=None):
     """One subcycled root step of the config-5 hierarchy per path in `names`
     (fp32_learned, fp32_plain, fp32_dual, fp64_plain), timed with CUDA events
     on the hierarchy's stream.  The sweeps' HBM rate counts 240 algorithmic
@@ -665,7 +666,14 @@ def hierarchy_paths(net, root, mlp_gate, seed, names):
                      "nan": st["nan"], "hll_cells": st["hll_cells"],
                      "ms_by_operation": hier.timing_ms()}
         sweep_ms = out[name]["ms_by_operation"].get("sweeps")
-        if sweep_ms:
+        if sweep_ms and params.precision == ez.FP64 and probe is not None:
+            # the FP64 path is bound by the FP64 pipe: its arithmetic per cell-sweep
+            # (the batched level's capture) over the sweeps' time, against the
+            # probe's DFMA rate; ghost-cover pencils are not counted as work
+            roof = fp64_alu_roofline(hier.cell_updates / (sweep_ms * 1e-3) / 1e6, probe)
+            if roof is not None:
+                out[name]["sweep_roofline"] = dict(roof, cell_sweeps="3 per cell update, over the sweeps' time")
+        elif sweep_ms:
             ach = 240.0 * hier.cell_updates / (sweep_ms * 1e-3) / 1e9
             out[name]["sweep_roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                            "frac": ach / peak, "peak_source": peak_kind,

@@ -85,10 +85,12 @@ struct Zone {
 __device__ __forceinline__ double div6(double x) { return x / 6.0; }
 __device__ __forceinline__ float div6(float x) { return x * (1.0f / 6.0f); }
 
-// Load of a field value by the march.  An x pencil's thread reads its own row,
-// one cache line per 16 positions, and the lines of a warp's 32 rows and five
-// fields outgrow L1 before they are used up: x loads ask L1 to keep their lines
-// (evict_last).  y and z sweeps read each line once per warp.
+// Load of a field value by the march (and the update's read of a cell's old
+// value where no ring holds it).  An x pencil's thread reads its own row, one
+// cache line per 16 positions, and the lines of a warp's 32 rows and five
+// fields outgrow L1 before they are used up: x loads ask L1 to keep their
+// lines (evict_last).  y and z sweeps read each line once per warp.  A cell is
+// read this way only before its own thread writes it.
 template <int DIR>
 __device__ __forceinline__ double ld_march(const double *p)
 {
@@ -1262,8 +1264,9 @@ struct Marcher {
         }
         // read-only (non-coherent) path: within one sweep a cell is read by the
         // thread of its own pencil before that thread writes it, never after
-        return prim<R, COUNT>(__ldg(a.U[0] + idx), __ldg(a.U[1 + DIR] + idx), __ldg(a.U[1 + A1] + idx),
-                              __ldg(a.U[1 + A2] + idx), __ldg(a.U[4] + idx), k, cnt);
+        return prim<R, COUNT>(ld_march<DIR>(a.U[0] + idx), ld_march<DIR>(a.U[1 + DIR] + idx),
+                              ld_march<DIR>(a.U[1 + A1] + idx), ld_march<DIR>(a.U[1 + A2] + idx),
+                              ld_march<DIR>(a.U[4] + idx), k, cnt);
     }
 
     // Zone at pencil position s with the dual-energy pressure choice, and its
@@ -1354,7 +1357,7 @@ struct Marcher {
         const int map[5] = {0, 1 + DIR, 1 + A1, 1 + A2, 4};
         _Pragma("unroll") for (int v = 0; v < 5; ++v)
         {
-            const double U = RING ? ring(s, v) : a.U[map[v]][idx];
+            const double U = RING ? ring(s, v) : ld_march<DIR>(a.U[map[v]] + idx);
             if (sizeof(R) == 8) u[v] = cell_update(U, dtdx64, (double)Fm[v], (double)Fp[v]);
             else u[v] = (U + Gm[v]) - Gp[v];
         }
