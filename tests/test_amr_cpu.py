@@ -143,3 +143,116 @@ def test_hierarchy_driver_rejects_bad_layouts_before_any_cuda_call():
     # level 1 must stay 3 root cells inside a periodic root (no ghosts to interpolate from)
     assert create([root, ([[8, 8, 8]], [[2, 12, 12]], [0])]) == -3
     assert L.enzo_hierarchy_destroy(None) == -1
+
+
+def _brute_plans(n, origin):
+    """Level plans by their definitions, every patch against every other."""
+    n, origin = np.asarray(n, dtype=np.int64), np.asarray(origin, dtype=np.int64)
+    lo, hi = origin, origin + n
+    sib, itp = [], []
+    for a in range(len(n)):
+        for b in range(len(n)):
+            if b == a:
+                continue
+            blo, bhi = np.maximum(lo[a] - 3, lo[b]), np.minimum(hi[a] + 3, hi[b])
+            if np.all(blo < bhi):
+                sib.append((a, b, tuple(blo), tuple(bhi)))
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if dx == dy == dz == 0:
+                        continue
+                    d = np.array([dx, dy, dz])
+                    rlo = np.where(d < 0, lo[a] - 3, np.where(d > 0, hi[a], lo[a]))
+                    rhi = np.where(d < 0, lo[a], np.where(d > 0, hi[a] + 3, hi[a]))
+                    if not any(np.all((lo[b] <= rlo) & (rhi <= hi[b])) for b in range(len(n))):
+                        itp.append((a, a, tuple(rlo), tuple(rhi)))
+    return sib, itp
+
+
+def _random_disjoint_layout(rng, count, extent=48):
+    """Disjoint boxes of even sizes at even origins (a rebuilt level's shape)."""
+    boxes = []
+    occ = np.zeros((extent,) * 3, dtype=bool)
+    tries = 0
+    while len(boxes) < count and tries < 2000:
+        tries += 1
+        size = 2 * rng.integers(1, 5, size=3)
+        o = 2 * rng.integers(0, (extent - size) // 2 + 1, size=3)
+        sl = tuple(slice(int(o[d]), int(o[d] + size[d])) for d in range(3))
+        if occ[sl[2], sl[1], sl[0]].any():
+            continue
+        occ[sl[2], sl[1], sl[0]] = True
+        boxes.append((size, o))
+    return np.array([b[0] for b in boxes]), np.array([b[1] for b in boxes])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_native_level_plans_equal_their_definition_on_random_layouts(seed):
+    """The library's bucket-indexed plans against every pair of patches: the
+    same sibling copy boxes in the same (dst, src) order, the same regions to
+    interpolate in the same (patch, direction) order."""
+    rng = np.random.default_rng(seed)
+    n, o = _random_disjoint_layout(rng, 40)
+    want_sib, want_itp = _brute_plans(n, o)
+    got_sib, got_itp = gh._level_plans(n, o)
+    as_t = lambda t: [(int(r["dst"]), int(r["src"]), tuple(int(v) for v in r["lo"]), tuple(int(v) for v in r["hi"]))
+                      for r in t]
+    assert as_t(got_sib) == want_sib
+    assert as_t(got_itp) == want_itp
+    assert len(want_sib) > 0 and len(want_itp) > 0
+
+
+def _brute_parts(fn, fo, cn, co):
+    """Flux-correction parts and waves by their definition (every pair)."""
+    fn, fo, cn, co = (np.asarray(a, dtype=np.int64) for a in (fn, fo, cn, co))
+    flo, fhi = fo // 2, (fo + fn) // 2
+    parts, cells = [], []
+    for i in range(len(fn)):
+        for d in range(3):
+            a1, a2 = (1 if d == 0 else 0), (1 if d == 2 else 2)
+            for side in (0, 1):
+                X = (fo[i, d] + (fn[i, d] if side else 0)) // 2
+                olo, ohi = flo[i].copy(), fhi[i].copy()
+                olo[d], ohi[d] = (X - 1, X) if side == 0 else (X, X + 1)
+                vol = int(np.prod(ohi - olo))
+                cov = sum(int(np.prod(np.clip(np.minimum(ohi, fhi[j]) - np.maximum(olo, flo[j]), 0, None)))
+                          for j in range(len(fn)))
+                if cov >= vol:
+                    continue
+                for t in range(len(cn)):
+                    tlo, thi = np.maximum(olo, co[t]), np.minimum(ohi, co[t] + cn[t])
+                    if np.all(tlo < thi):
+                        parts.append((i, d, side, t, (int(tlo[a1] - flo[i, a1]), int(tlo[a2] - flo[i, a2])),
+                                      (int(thi[a1] - flo[i, a1]), int(thi[a2] - flo[i, a2]))))
+                        cells.append((t, tlo, thi))
+    wave = []
+    for k in range(len(parts)):
+        w = 0
+        for q in range(k):
+            if cells[q][0] == cells[k][0] and np.all(np.maximum(cells[k][1], cells[q][1]) <
+                                                     np.minimum(cells[k][2], cells[q][2])):
+                w = max(w, wave[q] + 1)
+        wave.append(w)
+    return parts, wave
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_native_correction_parts_equal_their_definition_on_random_layouts(seed):
+    rng = np.random.default_rng(10 + seed)
+    # coarse level: the 24^3 domain cut into slabs along x and y
+    cx = sorted(set([0, 24] + list(rng.integers(4, 20, size=2))))
+    cy = sorted(set([0, 24] + list(rng.integers(4, 20, size=1))))
+    cn, co = [], []
+    for x0, x1 in zip(cx[:-1], cx[1:]):
+        for y0, y1 in zip(cy[:-1], cy[1:]):
+            cn.append((x1 - x0, y1 - y0, 24))
+            co.append((x0, y0, 0))
+    fn, fo = _random_disjoint_layout(rng, 25, extent=48)
+    want_parts, want_wave = _brute_parts(fn, fo, cn, co)
+    parts, wave = gh.correction_parts({"n": fn, "origin": fo}, {"n": np.array(cn), "origin": np.array(co)})
+    got = [(int(p["fine"]), int(p["dir"]), int(p["side"]), int(p["target"]), tuple(int(v) for v in p["lo"]),
+            tuple(int(v) for v in p["hi"])) for p in parts]
+    assert got == want_parts
+    assert list(wave) == want_wave
+    assert len(got) > 0
