@@ -87,14 +87,6 @@ def _lib():
     return L
 
 
-def _to_dev(arr, device):
-    import torch
-    raw = np.frombuffer(np.ascontiguousarray(arr).tobytes(), dtype=np.uint8).copy()
-    if raw.size == 0:
-        raw = np.zeros(16, dtype=np.uint8)
-    return torch.from_numpy(raw).to(device)
-
-
 class _Grid:
     """Patch lookup of a level: patches start at per-axis start positions, and a
     dense table over the start indices maps each start corner to its patch."""
