@@ -400,11 +400,27 @@ __global__ void __launch_bounds__(kFillThreads) pack_kernel(const enzo_patch *pa
         const int N0 = P.n[0] + 2 * P.ng, N1 = P.n[1] + 2 * P.ng;
         const int64_t q = a.act_off[lo] + c;
         const int64_t u = P.off + (x + P.ng) + (int64_t)N0 * ((y + P.ng) + (int64_t)N1 * (z + P.ng));
+        if (PACK) {
+            // gather: every field's load first, then the contiguous stores (the
+            // compiler cannot tell the arrays apart and would otherwise wait out
+            // one load per field): 3.33 -> 3.12 ms on the 4000-patch level
+            double v[6];
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            if (f >= a.nf) break;
-            if (PACK) a.packed[f][q] = a.U[f][u];
-            else a.U[f][u] = a.packed[f][q];
+            for (int f = 0; f < 6; ++f)
+                if (f < a.nf) v[f] = __ldg(a.U[f] + u);
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                if (f >= a.nf) break;
+                a.packed[f][q] = v[f];
+            }
+        } else {
+            // scatter: load and store field by field (batching the loads here
+            // measured slower, 3.75 -> 4.42 ms)
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                if (f >= a.nf) break;
+                a.U[f][u] = a.packed[f][q];
+            }
         }
     }
 }
