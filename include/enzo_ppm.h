@@ -528,7 +528,7 @@ int enzo_project(const enzo_patch_batch *coarse, const enzo_patch_link *coarse_l
 typedef struct enzo_hierarchy enzo_hierarchy;   /* opaque */
 
 typedef struct {
-    int32_t npatch;         /* patches of the level (>= 0; the root level has one or more) */
+    int32_t npatch;         /* patches of the level (>= 0; exactly 1 on the root level) */
     const int32_t *n;       /* HOST [npatch][3] active cells per axis (>= 1; even below the root) */
     const int32_t *origin;  /* HOST [npatch][3] global index at this level of the first active
                                cell (even below the root: patches cover whole parent cells) */

@@ -800,6 +800,9 @@ extern "C" int enzo_hierarchy_create(const enzo_level_layout *levels, int32_t nl
     if (!levels || nlevel < 1 || nlevel > 32 || !out || !(root_dx > 0.0) || !(root_dx < INFINITY) ||
         (nfields != 5 && nfields != 6))
         return ENZO_ERR_ARG;
+    // the root is one grid: its ghosts come from its own boundaries (wrapped
+    // or filled), never from siblings
+    if (levels[0].npatch != 1) return ENZO_ERR_ARG;
     *out = nullptr;
     for (int l = 0; l < nlevel; ++l) {
         const enzo_level_layout &ly = levels[l];
@@ -814,7 +817,7 @@ extern "C" int enzo_hierarchy_create(const enzo_level_layout *levels, int32_t nl
     if (root_bc)
         for (int d = 0; d < 3; ++d)
             if (root_bc[d] < ENZO_BC_PERIODIC || root_bc[d] > ENZO_BC_OUTFLOW) return ENZO_ERR_ARG;
-    if (!root_bc && nlevel > 1 && levels[0].npatch == 1) {
+    if (!root_bc && nlevel > 1) {
         // the periodic root wraps inside its sweeps and keeps no ghost cells, so
         // the level-1 ghost interpolation (SecondOrderA reaches one root cell
         // beyond the cell under a fine ghost) must find its parent cells inside it

@@ -139,6 +139,7 @@ def test_hierarchy_driver_rejects_bad_layouts_before_any_cuda_call():
     assert create([root, ([[8, 8, 8]], [[12, 12, 13]], [0])]) == -1      # odd origin
     assert create([([[16, 16, 16]], [[0, 0, 0]], [0])]) == -1             # a root with a parent
     assert create([root], nf=7) == -1
+    assert create([([[8, 16, 16], [8, 16, 16]], [[0, 0, 0], [8, 0, 0]], [-1, -1])]) == -1   # a root of two grids
     assert create([root], dx=0.0) == -1
     # level 1 must stay 3 root cells inside a periodic root (no ghosts to interpolate from)
     assert create([root, ([[8, 8, 8]], [[2, 12, 12]], [0])]) == -3
